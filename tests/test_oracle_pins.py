@@ -1,0 +1,458 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself:
+brute-force double sums, closed forms of the diffusion flow, invariants and
+hand-computed geometry. Each test names the passage of the paper it pins.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1802_07625_gb300 import synth
+
+PI = math.pi
+
+
+# --------------------------------------------------------------------------
+# brute force on tiny grids (pure Python, math.cos evaluated directly)
+# --------------------------------------------------------------------------
+
+def brute_forward(rho, blur):
+    """Main text Eq. rhotilde_mn with the integral as a midpoint sum, 4-fold loop."""
+    Ly, Lx = rho.shape
+    out = np.zeros((Ly, Lx))
+    for n in range(Ly):
+        for m in range(Lx):
+            s = 0.0
+            for j in range(Ly):
+                for i in range(Lx):
+                    s += rho[j, i] * math.cos(PI * m * (i + 0.5) / Lx) * math.cos(PI * n * (j + 0.5) / Ly)
+            w = 4.0 / ((1 + (m == 0)) * (1 + (n == 0)))
+            k2 = m * m / Lx ** 2 + n * n / Ly ** 2
+            out[n, m] = w * s * math.exp(-PI * PI * blur * blur * k2 / 2)
+    return out
+
+
+def brute_fields(spec, t):
+    """SI Eq. rhoxyt with f_mn = exp(-pi^2 (m^2/Lx^2 + n^2/Ly^2) t) and its x/y derivatives."""
+    Ly, Lx = spec.shape
+    rho = np.zeros((Ly, Lx))
+    gx = np.zeros((Ly, Lx))
+    gy = np.zeros((Ly, Lx))
+    for j in range(Ly):
+        y = j + 0.5
+        for i in range(Lx):
+            x = i + 0.5
+            r = a = b = 0.0
+            for n in range(Ly):
+                for m in range(Lx):
+                    c = spec[n, m] * math.exp(-PI * PI * (m * m / Lx ** 2 + n * n / Ly ** 2) * t)
+                    r += c * math.cos(PI * m * x / Lx) * math.cos(PI * n * y / Ly)
+                    a += c * (-PI * m / Lx) * math.sin(PI * m * x / Lx) * math.cos(PI * n * y / Ly)
+                    b += c * math.cos(PI * m * x / Lx) * (-PI * n / Ly) * math.sin(PI * n * y / Ly)
+            rho[j, i] = r / (Lx * Ly)
+            gx[j, i] = a / (Lx * Ly)
+            gy[j, i] = b / (Lx * Ly)
+    return rho, gx, gy
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (6, 8), (8, 6)])
+@pytest.mark.parametrize("blur", [0.0, 1.3])
+def test_forward_matches_brute_force(orc, shape, blur):
+    rng = np.random.default_rng(11)
+    rho = rng.uniform(0.2, 3.0, size=shape)
+    got = orc.forward(rho, blur)
+    ref = brute_forward(rho, blur)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (6, 8)])
+@pytest.mark.parametrize("t", [0.0, 0.37])
+def test_fields_match_brute_force(orc, shape, t):
+    rng = np.random.default_rng(12)
+    spec = rng.standard_normal(shape)
+    rho, gx, gy = orc.fields(spec, t)
+    r0, a0, b0 = brute_fields(spec, t)
+    for got, ref in ((rho, r0), (gx, a0), (gy, b0)):
+        assert np.max(np.abs(got - ref)) < 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("shape", [(16, 12), (64, 64), (10, 32)])
+def test_round_trip_is_identity(orc, shape):
+    # the inverse series of SI Eq. rhoxyt undoes the coefficients of Eq. rhotilde_mn
+    # exactly on the cell-centre grid (discrete orthogonality of the cosines)
+    rng = np.random.default_rng(13)
+    rho = rng.uniform(0.1, 5.0, size=shape)
+    back, _, _ = orc.fields(orc.forward(rho, 0.0), 0.0)
+    assert np.max(np.abs(back - rho)) < 1e-13 * np.max(rho)
+
+
+def test_single_mode_has_one_coefficient(orc):
+    Ly, Lx = 12, 16
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    rho = np.cos(2 * PI * x[None, :] / Lx) * np.cos(PI * y[:, None] / Ly)
+    spec = orc.forward(rho, 0.0)
+    expect = np.zeros((Ly, Lx))
+    expect[1, 2] = Lx * Ly  # 4 * (Lx/2) * (Ly/2)
+    assert np.max(np.abs(spec - expect)) < 1e-11
+
+
+def test_mean_coefficient_is_total_mass(orc):
+    # SI: rho~_00 = rho_bar Lx Ly
+    rng = np.random.default_rng(14)
+    rho = rng.uniform(0.1, 5.0, size=(20, 24))
+    spec = orc.forward(rho, 2.0)
+    assert abs(spec[0, 0] - rho.sum()) < 1e-11 * rho.sum()
+
+
+def test_blur_is_gaussian_of_width_sigma(orc):
+    # a Gaussian blur of standard deviation sigma multiplies the coefficient of
+    # wavenumber k = pi m / L by exp(-k^2 sigma^2 / 2)
+    Ly, Lx = 8, 32
+    x = np.arange(Lx) + 0.5
+    rho = 1.0 + 0.3 * np.cos(3 * PI * x / Lx)[None, :] * np.ones((Ly, 1))
+    s0 = orc.forward(rho, 0.0)
+    s1 = orc.forward(rho, 1.7)
+    k = 3 * PI / Lx
+    assert abs(s1[0, 3] / s0[0, 3] - math.exp(-k * k * 1.7 ** 2 / 2)) < 1e-13
+    assert abs(s1[0, 0] - s0[0, 0]) < 1e-12 * s0[0, 0]
+
+
+# --------------------------------------------------------------------------
+# closed form of the diffusion flow for one cosine mode
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("t", [0.0, 3.0, 40.0])
+def test_single_mode_decay_and_velocity(orc, t):
+    # rho0 = 1 + a cos(pi x / Lx): SI Eq. fmn_diff (D = 1 time) gives
+    # rho = 1 + a e^{-pi^2 t/Lx^2} cos(pi x/Lx), v_x = -d_x rho / rho, v_y = 0
+    Ly, Lx, a = 8, 32, 0.4
+    x = np.arange(Lx) + 0.5
+    rho0 = (1 + a * np.cos(PI * x / Lx))[None, :] * np.ones((Ly, 1))
+    spec = orc.forward(rho0, 0.0)
+    rho, gx, gy = orc.fields(spec, t)
+    decay = math.exp(-PI * PI * t / Lx ** 2)
+    rho_ref = 1 + a * decay * np.cos(PI * x / Lx)
+    gx_ref = -a * decay * (PI / Lx) * np.sin(PI * x / Lx)
+    assert np.max(np.abs(rho - rho_ref[None, :])) < 1e-13
+    assert np.max(np.abs(gx - gx_ref[None, :])) < 1e-13
+    assert np.max(np.abs(gy)) < 1e-13
+    vx, vy, vmax = orc.velocity(rho, gx, gy)
+    vx_ref = -gx_ref / rho_ref
+    assert np.max(np.abs(vx - vx_ref[None, :])) < 1e-13
+    assert np.max(np.abs(vy)) < 1e-13
+    assert abs(vmax - np.max(np.abs(vx_ref))) < 1e-13
+
+
+def test_two_dimensional_mode_decay_rate(orc):
+    # mode (m, n) = (2, 3) decays as exp(-pi^2 (4/Lx^2 + 9/Ly^2) t)
+    Ly, Lx, t = 12, 16, 2.5
+    spec = np.zeros((Ly, Lx))
+    spec[3, 2] = 5.0
+    rho, gx, gy = orc.fields(spec, t)
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    f = 5.0 * math.exp(-PI * PI * (4 / Lx ** 2 + 9 / Ly ** 2) * t) / (Lx * Ly)
+    cx, cy = np.cos(2 * PI * x / Lx), np.cos(3 * PI * y / Ly)
+    sx, sy = np.sin(2 * PI * x / Lx), np.sin(3 * PI * y / Ly)
+    assert np.max(np.abs(rho - f * cy[:, None] * cx[None, :])) < 1e-15
+    assert np.max(np.abs(gx - f * cy[:, None] * (-2 * PI / Lx) * sx[None, :])) < 1e-15
+    assert np.max(np.abs(gy - f * (-3 * PI / Ly) * sy[:, None] * cx[None, :])) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# interpolation and the no-flux walls
+# --------------------------------------------------------------------------
+
+def _linear_field(Lx, Ly, A, b):
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    X, Y = np.meshgrid(x, y)
+    vx = A[0][0] * X + A[0][1] * Y + b[0]
+    vy = A[1][0] * X + A[1][1] * Y + b[1]
+    return vx, vy
+
+
+def test_interp_reproduces_linear_fields_inside(orc):
+    Lx, Ly = 10, 7
+    A = [[0.3, -0.2], [0.15, 0.4]]
+    b = [0.7, -0.5]
+    vx, vy = _linear_field(Lx, Ly, A, b)
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x = rng.uniform(0.5, Lx - 0.5)
+        y = rng.uniform(0.5, Ly - 0.5)
+        ux, uy = orc.interp(vx, vy, x, y)
+        assert abs(ux - (A[0][0] * x + A[0][1] * y + b[0])) < 1e-13
+        assert abs(uy - (A[1][0] * x + A[1][1] * y + b[1])) < 1e-13
+
+
+def test_interp_at_grid_points_and_walls(orc):
+    Lx, Ly = 9, 6
+    rng = np.random.default_rng(4)
+    vx = rng.standard_normal((Ly, Lx))
+    vy = rng.standard_normal((Ly, Lx))
+    for j in range(Ly):
+        for i in range(Lx):
+            ux, uy = orc.interp(vx, vy, i + 0.5, j + 0.5)
+            assert ux == pytest.approx(vx[j, i], abs=1e-15)
+            assert uy == pytest.approx(vy[j, i], abs=1e-15)
+    for y in np.linspace(0, Ly, 13):
+        # no flux through the walls x = 0 and x = Lx (main text: no flow through the
+        # edges of the box)
+        assert orc.interp(vx, vy, 0.0, y)[0] == 0.0
+        assert orc.interp(vx, vy, float(Lx), y)[0] == 0.0
+    for x in np.linspace(0, Lx, 13):
+        assert orc.interp(vx, vy, x, 0.0)[1] == 0.0
+        assert orc.interp(vx, vy, x, float(Ly))[1] == 0.0
+    # tangential component on a wall equals the nearest grid point's
+    j = 2
+    assert orc.interp(vx, vy, 0.0, j + 0.5)[1] == pytest.approx(vy[j, 0], abs=1e-15)
+    assert orc.interp(vx, vy, float(Lx), j + 0.5)[1] == pytest.approx(vy[j, Lx - 1], abs=1e-15)
+    # halfway between the wall and the first grid point the normal component is halved
+    assert orc.interp(vx, vy, 0.25, j + 0.5)[0] == pytest.approx(0.5 * vx[j, 0], abs=1e-15)
+
+
+# --------------------------------------------------------------------------
+# predictor-corrector step
+# --------------------------------------------------------------------------
+
+def test_heun_step_closed_form_for_linear_fields(orc):
+    # For v0(r) = A r + b and v1(r) = c (A r + b), Heun's step is
+    #   r* = r + h (A r + b),  r' = r + h/2 ((A r + b) + c (A r* + b))
+    Lx, Ly = 40, 30
+    A = np.array([[0.02, -0.01], [0.015, -0.03]])
+    b = np.array([0.1, -0.05])
+    c = 1.7
+    v0x, v0y = _linear_field(Lx, Ly, A, b)
+    v1x, v1y = c * v0x, c * v0y
+    rng = np.random.default_rng(5)
+    pts = np.stack([rng.uniform(10, 30, 40), rng.uniform(8, 22, 40)], axis=1)
+    h = 0.8
+    xp, yp, xc, yc, err = orc.heun_step(v0x, v0y, v1x, v1y, pts[:, 0].copy(), pts[:, 1].copy(), h)
+    f0 = pts @ A.T + b
+    rstar = pts + h * f0
+    f1 = c * (rstar @ A.T + b)
+    rcorr = pts + 0.5 * h * (f0 + f1)
+    assert np.max(np.abs(np.stack([xp, yp], 1) - rstar)) < 1e-13
+    assert np.max(np.abs(np.stack([xc, yc], 1) - rcorr)) < 1e-13
+    assert err == pytest.approx(np.max(np.linalg.norm(rcorr - rstar, axis=1)), rel=1e-12)
+
+
+def test_heun_step_stays_in_box(orc):
+    Lx, Ly = 8, 8
+    vx = np.full((Ly, Lx), 5.0)
+    vy = np.full((Ly, Lx), -5.0)
+    x = np.array([7.6])
+    y = np.array([0.3])
+    _, _, xc, yc, _ = orc.heun_step(vx, vy, vx, vy, x, y, 1.0)
+    assert 0.0 <= xc[0] <= Lx and 0.0 <= yc[0] <= Ly
+
+
+# --------------------------------------------------------------------------
+# the integration
+# --------------------------------------------------------------------------
+
+def test_uniform_density_gives_identity(orc):
+    Ly, Lx = 16, 24
+    spec = orc.forward(np.full((Ly, Lx), 2.5), 1.0)
+    r = orc.integrate(spec)
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    assert r.accepted == 0 and r.status == 0
+    assert np.array_equal(r.X, np.broadcast_to(x[None, :], (Ly, Lx)))
+    assert np.array_equal(r.Y, np.broadcast_to(y[:, None], (Ly, Lx)))
+
+
+def test_x_only_density_gives_one_dimensional_equalising_map(orc):
+    # SI Eq. det in one dimension has the unique monotone solution
+    #   T_x(x) = (1/rho_bar) int_0^x rho0,  T_y = y.
+    # For rho0 = 1 + a cos(pi x / L): T_x = x + (a L / pi) sin(pi x / L).
+    Ly, Lx, a = 8, 64, 0.5
+    x = np.arange(Lx) + 0.5
+    rho0 = (1 + a * np.cos(PI * x / Lx))[None, :] * np.ones((Ly, 1))
+    spec = orc.forward(rho0, 0.0)
+    exact = x + a * Lx / PI * np.sin(PI * x / Lx)
+    errs = []
+    for atol in (4e-2, 1e-2, 2.5e-3):
+        r = orc.integrate(spec, atol=atol, rho_tol=1e-7)
+        assert r.status == 0
+        assert np.max(np.abs(r.Y - (np.arange(Ly) + 0.5)[:, None])) == 0.0
+        errs.append(np.max(np.abs(r.X - exact[None, :])))
+    # second-order scheme: the error falls with the step tolerance and is small
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 0.03
+
+
+def test_mirror_symmetry(orc):
+    rng = np.random.default_rng(6)
+    Ly, Lx = 12, 12
+    rho0 = rng.uniform(0.5, 2.0, (Ly, Lx))
+    r1 = orc.integrate(orc.forward(rho0, 1.0))
+    r2 = orc.integrate(orc.forward(rho0[:, ::-1].copy(), 1.0))
+    assert r1.accepted == r2.accepted
+    assert np.max(np.abs(r2.X[:, ::-1] - (Lx - r1.X))) < 1e-9
+    assert np.max(np.abs(r2.Y[:, ::-1] - r1.Y)) < 1e-9
+
+
+def test_transpose_symmetry(orc):
+    rng = np.random.default_rng(7)
+    L = 12
+    rho0 = rng.uniform(0.5, 2.0, (L, L))
+    r1 = orc.integrate(orc.forward(rho0, 1.0))
+    r2 = orc.integrate(orc.forward(rho0.T.copy(), 1.0))
+    assert np.max(np.abs(r2.X.T - r1.Y)) < 1e-9
+    assert np.max(np.abs(r2.Y.T - r1.X)) < 1e-9
+
+
+def test_projected_grid_has_positive_jacobian(orc):
+    m = synth.make_workload("voronoi16_64")
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    rho = orc.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
+    r = orc.integrate(orc.forward(rho, 1.0))
+    X, Y = r.X, r.Y
+    # signed area of every quad of projected cell centres (no fold-overs)
+    ax = X[:-1, 1:] - X[:-1, :-1]
+    ay = Y[:-1, 1:] - Y[:-1, :-1]
+    bx = X[1:, :-1] - X[:-1, :-1]
+    by = Y[1:, :-1] - Y[:-1, :-1]
+    assert np.min(ax * by - ay * bx) > 0.0
+
+
+# --------------------------------------------------------------------------
+# geometry: areas, rasterisation, point mapping
+# --------------------------------------------------------------------------
+
+def test_region_areas_and_orientation(orc):
+    sq = [[1, 1], [3, 1], [3, 3], [1, 3]]                 # CCW, area 4
+    hole = [[1.5, 1.5], [1.5, 2.0], [2.0, 2.0], [2.0, 1.5]]  # CW, area -0.25
+    tri = [[5, 5], [8, 5], [5, 9]]                         # CCW, area 6
+    xy = np.array(sq + hole + tri, dtype=float)
+    offs = np.array([0, 4, 8, 11])
+    reg = np.array([0, 0, 1], dtype=np.int32)
+    A = orc.region_areas(2, offs, reg, xy)
+    assert A[0] == pytest.approx(3.75, abs=1e-14)
+    assert A[1] == pytest.approx(6.0, abs=1e-14)
+    err, mx = orc.area_errors(np.array([1.0, 3.0]), A)
+    # targets: V_i * sum(A) / sum(V) = 9.75/4 * [1, 3]
+    assert err[0] == pytest.approx(3.75 / (9.75 / 4) - 1, abs=1e-14)
+    assert err[1] == pytest.approx(6.0 / (9.75 * 3 / 4) - 1, abs=1e-14)
+    assert mx == pytest.approx(max(abs(err[0]), abs(err[1])), abs=0)
+
+
+def _overlap(a0, a1, b0, b1):
+    return max(0.0, min(a1, b1) - max(a0, b0))
+
+
+def test_rasterize_rectangles_exact_coverage(orc):
+    Lx, Ly = 8, 6
+    r1 = (1.25, 0.5, 3.5, 4.75)
+    r2 = (4.0, 1.2, 7.3, 5.0)
+    ring1 = synth.rectangle_ring(*r1, spacing=0.7)
+    ring2 = synth.rectangle_ring(*r2, spacing=0.45)
+    xy = np.concatenate([ring1, ring2])
+    offs = np.array([0, len(ring1), len(ring1) + len(ring2)])
+    reg = np.array([0, 1], dtype=np.int32)
+    vals = np.array([2.0, 7.0])
+    A = orc.region_areas(2, offs, reg, xy)
+    a1 = (r1[2] - r1[0]) * (r1[3] - r1[1])
+    a2 = (r2[2] - r2[0]) * (r2[3] - r2[1])
+    assert A == pytest.approx([a1, a2], abs=1e-13)
+    rho = orc.rasterize(Lx, Ly, vals, A, offs, reg, xy)
+    d_out = vals.sum() / (a1 + a2)
+    for j in range(Ly):
+        for i in range(Lx):
+            c1 = _overlap(i, i + 1, r1[0], r1[2]) * _overlap(j, j + 1, r1[1], r1[3])
+            c2 = _overlap(i, i + 1, r2[0], r2[2]) * _overlap(j, j + 1, r2[1], r2[3])
+            ref = d_out + (vals[0] / a1 - d_out) * c1 + (vals[1] / a2 - d_out) * c2
+            assert rho[j, i] == pytest.approx(ref, abs=1e-13)
+    # the box's mean density is the map's mean density
+    assert rho.mean() == pytest.approx(d_out, rel=1e-13)
+
+
+def test_rasterize_triangle_and_hole(orc):
+    # right triangle (0,0),(4,0),(0,4): cells below the diagonal are full, cells the
+    # diagonal cuts through are half covered; a clockwise square ring removes area
+    Lx, Ly = 6, 6
+    tri = np.array([[0, 0], [4, 0], [0, 4]], dtype=float)
+    hole = np.array([[0.5, 0.5], [0.5, 1.5], [1.5, 1.5], [1.5, 0.5]], dtype=float)
+    other = synth.rectangle_ring(4.0, 4.0, 6.0, 6.0, 1.0)
+    xy = np.concatenate([tri, hole, other])
+    offs = np.array([0, 3, 7, 7 + len(other)])
+    reg = np.array([0, 0, 1], dtype=np.int32)
+    vals = np.array([3.0, 1.0])
+    A = orc.region_areas(2, offs, reg, xy)
+    assert A[0] == pytest.approx(8.0 - 1.0)
+    rho = orc.rasterize(Lx, Ly, vals, A, offs, reg, xy)
+    d_out = vals.sum() / A.sum()
+    w0 = vals[0] / A[0] - d_out
+    w1 = vals[1] / A[1] - d_out
+    for j in range(Ly):
+        for i in range(Lx):
+            cov = 1.0 if i + j + 2 <= 4 else (0.5 if i + j == 3 else 0.0)
+            cov -= _overlap(i, i + 1, 0.5, 1.5) * _overlap(j, j + 1, 0.5, 1.5)
+            cov1 = 1.0 if (i >= 4 and j >= 4) else 0.0
+            assert rho[j, i] == pytest.approx(d_out + w0 * cov + w1 * cov1, abs=1e-13)
+
+
+def test_rasterize_voronoi_total_mass(orc):
+    m = synth.make_workload("voronoi16_64")
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    rho = orc.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
+    d_out = m.values.sum() / A.sum()
+    # sum over cells of rho = d_out * box area (the margin carries the mean density)
+    assert rho.sum() == pytest.approx(d_out * m.Lx * m.Ly, rel=1e-12)
+    # the inset margin is exactly d_out
+    assert np.all(rho[:8, :] == d_out) and np.all(rho[:, :8] == d_out)
+    assert np.all(rho > 0)
+
+
+def test_map_points_identity_and_affine(orc):
+    Lx, Ly = 12, 9
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    X, Y = np.meshgrid(x, y)
+    rng = np.random.default_rng(8)
+    pts = np.stack([rng.uniform(0, Lx, 200), rng.uniform(0, Ly, 200)], axis=1)
+    out = orc.map_points(X, Y, pts)
+    assert np.max(np.abs(out - pts)) < 1e-13
+    # an affine projected grid maps every point affinely (bilinear reproduces affine maps,
+    # inside and in the extended half-cell band along the walls)
+    M = np.array([[1.1, 0.2], [-0.1, 0.9]])
+    c = np.array([0.3, -0.4])
+    Xa = M[0, 0] * X + M[0, 1] * Y + c[0]
+    Ya = M[1, 0] * X + M[1, 1] * Y + c[1]
+    out = orc.map_points(Xa, Ya, pts)
+    assert np.max(np.abs(out - (pts @ M.T + c))) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the whole method
+# --------------------------------------------------------------------------
+
+def test_strip_map_converges_to_one_dimensional_solution(orc):
+    # two vertical strips that tile the box: the density is x-only, so the converged
+    # cartogram moves the dividing line to x = Lx V0 / (V0 + V1) (SI Eq. det in 1-D)
+    Lx, Ly = 32, 16
+    V = [1.0, 3.0]
+    m = synth.strip_map(Lx, Ly, [0, 16, 32], V, spacing=1.0)
+    r = orc.cartogram(m, blur=0.0)
+    assert r.converged and r.status == 0
+    assert r.max_area_error < 0.01
+    xy = r.xy
+    mid = np.abs(m.xy[:, 0] - 16.0) < 1e-12
+    target = Lx * V[0] / sum(V)
+    assert np.max(np.abs(xy[mid, 0] - target)) < 0.01 * Lx
+    # nothing moves vertically in an x-only flow
+    assert np.max(np.abs(xy[:, 1] - m.xy[:, 1])) < 1e-12
+
+
+def test_voronoi_map_converges(orc):
+    m = synth.make_workload("voronoi16_64")
+    r = orc.cartogram(m, blur=1.0)
+    assert r.converged and r.max_area_error < 0.01
+    # every region's area is within 1% of its target; the sum of target areas is the
+    # sum of current areas by construction
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, r.xy)
+    err, mx = orc.area_errors(m.values, A)
+    assert mx == pytest.approx(r.max_area_error)
