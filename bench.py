@@ -1,0 +1,387 @@
+"""Benchmark: converged diffusion-flow cartograms on the GB300.
+
+One timed step = one whole converged cartogram of the workload (all outer
+iterations: rasterise, forward transform, integrate every grid point to
+equalisation, map vertices, areas) starting from the original map, which is resident
+in HBM (restored on the device by cartogram_reset). The headline metric is RK2
+grid-point updates per second: Lx*Ly x attempted predictor-corrector steps /
+device time, with the transforms of every attempted step included.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain C implementation written from
+the paper) on the host cores, on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica of the workload (a
+single cartogram has no data-parallel split worth a collective); value sums the
+updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "powerlaw3000_1024"
+METRIC = "RK2 grid-point updates/s (converged 1024^2 cartogram, mixed precision)"
+UNIT = "updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def launches_per_cartogram(iterations, attempted):
+    """Kernels the library launches for one cartogram_integrate call: initial areas (2);
+    per iteration rasterise (2), forward transform (2), integration init (3: state,
+    pass 1, pass 2, finish -> 4), one attempted step (3 each), finish (2), vertex map (1),
+    areas (2)."""
+    return 2 + iterations * (2 + 2 + 4 + 2 + 1 + 2) + 3 * attempted
+
+
+def bytes_per_point(esz):
+    """Algorithmic bytes per grid point per launch of each hot kernel class:
+    pass 1 reads the spectrum (1 value) and writes (A, B); pass 2 reads (A, B) and writes v;
+    the step reads and writes the displacement and gathers v(t) and v(t+h) once each."""
+    return {"inverse_rows": 3 * esz, "inverse_cols_velocity": 4 * esz, "heun_step": 8 * esz}
+
+
+def cpu_baseline(m, blur, n_steps, threads=None):
+    """The FP64 oracle (as it stands) on the host cores: n_steps attempted steps of the
+    workload's first integration (field at t+h by direct sums + Heun step of all points)."""
+    import oracle
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    A = oracle.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    rho = oracle.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
+    spec = oracle.forward(rho, blur)
+    rho_bar = spec[0, 0] / (m.Lx * m.Ly)
+    v0 = oracle.velocity(*oracle.fields(spec, 0.0))
+    X = (np.arange(m.Lx)[None, :] + 0.5) * np.ones((m.Ly, 1))
+    Y = (np.arange(m.Ly)[:, None] + 0.5) * np.ones((1, m.Lx))
+    h = 1e-2
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        v1 = oracle.velocity(*oracle.fields(spec, h))
+        oracle.heun_step(v0[0], v0[1], v1[0], v1[1], X.ravel(), Y.ravel(), h)
+    dt = time.perf_counter() - t0
+    del rho_bar
+    return {"value": n_steps * m.Lx * m.Ly / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d attempted steps (field by direct cosine/sine sums + Heun step of all %dx%d grid "
+                      "points) of the first integration of %s, %.1f s" % (n_steps, m.Lx, m.Ly, WORKLOAD, dt),
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1802_07625_gb300 import synth
+    m = synth.make_workload(WORKLOAD)
+    blur = synth.WORKLOADS[WORKLOAD]["blur"]
+    for _ in range(args.warmup):
+        cpu_baseline(m, blur, 1)
+    times = []
+    for _ in range(args.steps):
+        r = cpu_baseline(m, blur, 1)
+        times.append(r["seconds"])
+    total = sum(times)
+    value = args.steps * m.Lx * m.Ly / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": "%dx%d" % (m.Lx, m.Ly),
+                                            "sample": "one attempted step per timed step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": "one attempted step of the first integration per timed step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1802_07625_gb300 as P
+    from paper_1802_07625_gb300 import synth
+
+    P.load()
+    m = synth.make_workload(WORKLOAD)
+    w = synth.WORKLOADS[WORKLOAD]
+    blur = w["blur"]
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local)
+    # inputs resident in HBM
+    d_vals = torch.tensor(m.values, device=dev)
+    d_off = torch.tensor(m.ring_offsets, device=dev)
+    d_reg = torch.tensor(m.ring_region, device=dev)
+    d_xy = torch.tensor(m.xy, device=dev)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed")
+    c.set_stream(stream)
+    P.cartogram_set_regions(c.ctx, d_vals, d_off, d_reg, d_xy)
+    c._map = P._Map(m.n_regions, m.n_vertices)
+
+    def one():
+        c.reset()
+        return c.integrate()
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    with ClockSampler(local) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush between timed steps (256 MB > 126 MB L2)
+            ev[k][0].record(stream)
+            stats.append(one())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+    clocks = clk.summary()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    attempted = sum(s.steps_accepted + s.steps_rejected for s in stats)
+    updates = attempted * m.Lx * m.Ly
+    t_max = _max_over_ranks(world, total_ms / 1e3)
+    updates_all = _sum_over_ranks(world, float(updates))
+    value = updates_all / t_max
+    s_per_cartogram = total_ms / 1e3 / args.steps
+    last = stats[-1]
+
+    # live per-kernel timing for the roofline (same stream, CUDA events)
+    prof = c.profile(reps=20)
+    esz = 4
+    bpp = bytes_per_point(esz)
+    step_ms = {k: prof[k] for k in bpp}
+    dominant = max(step_ms, key=step_ms.get)
+    peaks, peak_kind = _peaks()
+    achieved = bpp[dominant] * m.Lx * m.Ly / (prof[dominant] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(dominant)
+        except Exception:
+            traffic = None
+
+    # end to end through the C-ABI with host buffers: pinned host -> set_regions ->
+    # integrate -> vertices back to pinned host
+    h_vals = torch.tensor(m.values).pin_memory()
+    h_off = torch.tensor(m.ring_offsets).pin_memory()
+    h_reg = torch.tensor(m.ring_region).pin_memory()
+    h_xy = torch.tensor(m.xy).pin_memory()
+    h_out = torch.empty_like(h_xy).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    e2e_updates = 0
+    for _ in range(e2e_steps):
+        P.cartogram_set_regions(c.ctx, h_vals, h_off, h_reg, h_xy)
+        s = c.integrate()
+        P.cartogram_get_vertices(c.ctx, h_out)
+        e2e_updates += (s.steps_accepted + s.steps_rejected) * m.Lx * m.Ly
+    e2e_dt = time.perf_counter() - t0
+    h2d = sum(t.numel() * t.element_size() for t in (h_vals, h_off, h_reg, h_xy))
+    d2h = h_out.numel() * h_out.element_size()
+    e2e_value = _sum_over_ranks(world, float(e2e_updates)) / _max_over_ranks(world, e2e_dt)
+
+    # the plain FP64 GPU path on the same workload (one converged cartogram)
+    fp64 = None
+    if args.fp64_steps > 0:
+        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64")
+        f.set_stream(stream)
+        P.cartogram_set_regions(f.ctx, d_vals, d_off, d_reg, d_xy)
+        f._map = P._Map(m.n_regions, m.n_vertices)
+        f.reset()
+        f.integrate()
+        torch.cuda.synchronize()
+        fms, fatt = 0.0, 0
+        for _ in range(args.fp64_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f.reset()
+            a.record(stream)
+            fs = f.integrate()
+            b.record(stream)
+            torch.cuda.synchronize()
+            fms += a.elapsed_time(b)
+            fatt += fs.steps_accepted + fs.steps_rejected
+        fp64 = {"updates_per_s": fatt * m.Lx * m.Ly / (fms / 1e3), "s_per_cartogram": fms / 1e3 / args.fp64_steps,
+                "iterations": fs.iterations, "attempted_steps": fs.steps_accepted + fs.steps_rejected,
+                "max_area_error": fs.max_area_error}
+        f.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m, blur, args.cpu_steps)
+        cpu.pop("seconds", None)
+
+    launches = sum(launches_per_cartogram(s.iterations, s.steps_accepted + s.steps_rejected) for s in stats)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "%dx%d" % (m.Lx, m.Ly), "regions": m.n_regions,
+                       "vertices": m.n_vertices, "precision": "mixed", "blur": blur,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "s_per_cartogram": s_per_cartogram,
+            "iterations": last.iterations, "attempted_steps_per_cartogram": last.steps_accepted + last.steps_rejected,
+            "accepted_steps_per_cartogram": last.steps_accepted, "max_area_error": last.max_area_error,
+            "accepted_updates_per_s": value * last.steps_accepted / max(1, last.steps_accepted + last.steps_rejected),
+            "fp64_gpu": fp64,
+            "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
+            "kernel_ms": prof,
+            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_kind": peak_kind + " (copy bandwidth)",
+                         "bytes_per_launch": bpp[dominant] * m.Lx * m.Ly},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * cartogram.h - C-ABI of the GB300 (sm_103a) diffusion-flow cartogram library.
+ *
+ * The library computes density-equalising map projections (cartograms) with the
+ * flow-based method of Gastner, Seguy & More, "Fast flow-based algorithm for
+ * creating density-equalizing map projections" (PNAS 2018, arXiv:1802.07625),
+ * integrating the diffusion flow (SI Appendix section 2, Eq. fmn_diff): the cosine
+ * spectrum of the blurred, rasterised density is damped in time, inverse cosine /
+ * sine transforms give rho and grad rho, v = -grad(rho)/rho, and all Lx*Ly grid
+ * points advance by an adaptive predictor-corrector step with bilinear
+ * interpolation (main text, section "Flow-based cartograms" and the paragraph on
+ * overlaying an Lx x Ly grid). Polygon vertices follow through the projected grid,
+ * and the integration repeats on its own output until every region's area is
+ * within the tolerance of its target (main text, section on benchmarking).
+ *
+ * Coordinates are grid units inside the box [0, Lx] x [0, Ly]. Grid points are the
+ * cell centres (i + 1/2, j + 1/2). Fields are row-major Lx*Ly arrays indexed
+ * [j*Lx + i]; spectra are indexed [n*Lx + m] (m: x wavenumber).
+ *
+ * Pointers: every array argument may be host memory or device memory of the
+ * context's GPU; the library detects which and copies accordingly. The caller owns
+ * every buffer it passes; the library copies inputs during the call and never keeps
+ * a caller pointer. All functions are synchronous with respect to the host unless
+ * stated otherwise; device work runs on the context's stream, which does not wait for
+ * other streams: device inputs produced on another stream must be complete (or that
+ * stream passed to cartogram_set_stream) before the call.
+ *
+ * Errors: functions return CG_OK (0) or a negative CG_E* code; a description of
+ * the last error is available from cartogram_last_error(). A context is not thread
+ * safe: use one context per host thread.
+ */
+#ifndef CARTOGRAM_H
+#define CARTOGRAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cg_ctx cg_ctx;
+
+enum {
+    CG_OK = 0,
+    CG_EINVAL = -1,        /* invalid argument (sizes, NaN/Inf, non-positive value, ...) */
+    CG_ENOMEM = -2,        /* device or host allocation failed */
+    CG_ECUDA = -3,         /* a CUDA runtime call failed */
+    CG_ENOCONVERGE = -4,   /* max_iter outer iterations did not reach area_tol */
+    CG_EFOLD = -5,         /* a projected grid folded over (non-positive quad area) */
+    CG_ESTEPFAIL = -6,     /* an integration used max_steps attempts, or its step collapsed */
+    CG_ESTATE = -8         /* call out of order (e.g. integrate before set_regions) */
+};
+
+enum {
+    CG_PRECISION_FP64 = 0,   /* every field, transform and position in FP64 */
+    CG_PRECISION_MIXED = 1   /* transforms, fields and displacements in FP32; rasterisation,
+                                forward transform, polygon areas, the convergence test and
+                                the step-control arithmetic in FP64 */
+};
+
+/* Tuning of the method. cartogram_default_options() fills the defaults noted here. */
+typedef struct cg_options {
+    int precision;      /* CG_PRECISION_FP64 (default) or CG_PRECISION_MIXED */
+    double dt0;         /* first trial step, diffusion time with D = 1 (1e-2) */
+    double atol;        /* accept a step when max ||r_corr - r_pred|| <= atol cells (1e-2) */
+    double grow;        /* step factor after an accepted step (1.2) */
+    double shrink;      /* step factor after a rejected step (0.5) */
+    double cfl;         /* step cap: h * max|v| <= cfl cells (1.0) */
+    double rho_tol;     /* an integration ends at the first accepted step with
+                           max |rho - rho_bar| / rho_bar <= rho_tol (1e-4) */
+    double area_tol;    /* outer iterations end when max |A_i/A^_i - 1| < area_tol (0.01) */
+    int max_steps;      /* attempted steps per integration before CG_ESTEPFAIL (4000) */
+    int max_iter;       /* outer iterations before CG_ENOCONVERGE (50) */
+    int use_graph;      /* 1: whole integration is one CUDA-graph launch with a device-side
+                           loop (default); 0: host-driven loop of the same kernels */
+} cg_options;
+
+typedef struct cg_stats {
+    int iterations;             /* outer iterations run by the last cartogram_integrate */
+    int converged;              /* 1 if max area error < area_tol */
+    long long steps_accepted;   /* summed over the iterations */
+    long long steps_rejected;
+    double max_area_error;      /* max_i |A_i / A^_i - 1| after the last iteration */
+    double t_end;               /* diffusion time reached by the last integration */
+    double seconds;             /* host wall time of the call */
+    double step_loop_ms;        /* device time of the integrations' step loops */
+} cg_stats;
+
+/* Fill *opt with the defaults listed in cg_options. Returns CG_OK or CG_EINVAL (NULL). */
+int cartogram_default_options(cg_options* opt);
+
+/* Create a context for an Lx x Ly grid (main text: "overlay the map with an Lx x Ly
+ * square grid"; Lx and Ly integers). This build supports powers of two from 8 to
+ * 1024 along each axis. blur_width is the standard deviation, in cells, of the
+ * Gaussian blur applied to the rasterised density before every integration (main
+ * text, section on benchmarking: "Gaussian blur of moderate width"); 0 disables
+ * it. opt may be NULL for the defaults. Allocates the device state on the current
+ * CUDA device. On success *out owns the context; free it with cartogram_destroy.
+ * Errors: CG_EINVAL (sizes, blur, options), CG_ENOMEM, CG_ECUDA. */
+int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_ctx** out);
+
+/* Run the context's device work on `cuda_stream` (a cudaStream_t, e.g. torch's current
+ * stream) from now on; NULL selects the context's own stream. */
+int cartogram_set_stream(cg_ctx* ctx, void* cuda_stream);
+
+/* Set the map: n_regions regions with target values (main text, problem statement:
+ * areas proportional to e.g. population; the density of a region is its value over
+ * its area, section on previous all-coordinates methods).
+ *   target_values [n_regions]      > 0 and finite
+ *   ring_offsets  [n_rings + 1]    int64, ring k owns vertices ring_offsets[k] ..
+ *                                  ring_offsets[k+1]-1; ring_offsets[0] = 0, increasing,
+ *                                  at least 3 vertices per ring
+ *   ring_region   [n_rings]        int32 in [0, n_regions)
+ *   xy            [ring_offsets[n_rings]][2]  vertices (x, y) inside [0,Lx]x[0,Ly];
+ *                                  rings are implicitly closed; counter-clockwise rings
+ *                                  are outer boundaries, clockwise rings are holes, and
+ *                                  a region's area is the signed sum over its rings.
+ * Regions must not overlap and each must have positive area. Resets the iteration
+ * history. Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
+int cartogram_set_regions(cg_ctx* ctx, int n_regions, const double* target_values,
+                          int64_t n_rings, const int64_t* ring_offsets,
+                          const int32_t* ring_region, const double* xy);
+
+/* Run the whole method (main text, section on benchmarking, "repeat the integration"):
+ * rasterise, blur and transform the density, integrate the flow of all grid points
+ * to equalisation, map the vertices through the projected grid, recompute the areas,
+ * and repeat until max_i |A_i/A^_i - 1| < area_tol (main text: a maximum relative
+ * area error below 1%), where A^_i = V_i * sum(A) / sum(V). Continues from the
+ * current vertices, so a second call after convergence runs no iteration. stats may
+ * be NULL. Returns CG_OK on convergence, CG_ENOCONVERGE after max_iter iterations
+ * (the vertices and history stay valid), CG_ESTEPFAIL, CG_ESTATE, CG_ECUDA. */
+int cartogram_integrate(cg_ctx* ctx, cg_stats* stats);
+
+/* Map n arbitrary points (x, y pairs, [n][2]) through every projected grid of the
+ * history in order (main text: the projection is defined for every point, e.g. the
+ * capitals or death cases of the case studies). xy_in and xy_out may alias. Errors:
+ * CG_EINVAL, CG_ECUDA. */
+int cartogram_project(cg_ctx* ctx, int64_t n, const double* xy_in, double* xy_out);
+
+/* Signed relative area errors A_i / A^_i - 1 of the current vertices, [n_regions]. */
+int cartogram_area_errors(cg_ctx* ctx, double* err);
+
+/* Current (mapped) vertices, same layout as set_regions' xy. */
+int cartogram_get_vertices(cg_ctx* ctx, double* xy_out);
+
+/* Restore the vertices given to the last cartogram_set_regions and clear the history,
+ * on the device (no host transfer). Errors: CG_ESTATE (no map). */
+int cartogram_reset(cg_ctx* ctx);
+
+/* Number of outer iterations in the history (projected grids stored). */
+int cartogram_history_length(const cg_ctx* ctx);
+
+/* Projected grid of history entry k: positions of the Lx*Ly cell centres after
+ * integration k, xy_out [Lx*Ly][2] FP64. Errors: CG_EINVAL (k out of range). */
+int cartogram_get_grid(cg_ctx* ctx, int k, double* xy_out);
+
+/* ---- step-level entry points (one stage of the method each) ---------------- */
+
+/* Rasterised density of the current vertices, normalised so that the box mean is 1
+ * (section on previous all-coordinates methods; the margin carries the mean density,
+ * section on benchmarking): rho[j*Lx+i] = rho0/rho_bar with exact cell coverage.
+ * rho_out [Lx*Ly] FP64. */
+int cartogram_density(cg_ctx* ctx, double* rho_out);
+
+/* Cosine spectrum (main text Eq. rhotilde_mn) of the normalised density of the
+ * current vertices, times the Gaussian blur factor exp(-pi^2 s^2 (m^2/Lx^2 +
+ * n^2/Ly^2)/2). spec_out [Ly][Lx] FP64, indexed [n*Lx + m]; spec[0] = Lx*Ly.
+ * Also makes this spectrum the context's current one. */
+int cartogram_spectrum(cg_ctx* ctx, double* spec_out);
+
+/* Density and velocity at diffusion time t from the current spectrum (SI Eq. rhoxyt
+ * with Eq. fmn_diff, D = 1; v = -grad(rho)/rho): rho_out [Lx*Ly] (normalised density,
+ * may be NULL), v_out [Lx*Ly][2] (vx, vy) at the cell centres. In mixed precision the
+ * values are computed in FP32 and widened. */
+int cartogram_velocity(cg_ctx* ctx, double t, double* rho_out, double* v_out);
+
+/* One predictor-corrector step of all grid points from displacements disp_in
+ * ([Lx*Ly][2], position = cell centre + displacement) with step h, using the fields
+ * at times t and t+h of the current spectrum (main text: predictor-corrector with
+ * bilinear interpolation). disp_out [Lx*Ly][2]; *err = max ||r_corr - r_pred||. */
+int cartogram_heun_step(cg_ctx* ctx, double t, double h, const double* disp_in,
+                        double* disp_out, double* err);
+
+/* One integration (the step loop from t = 0 to equalisation) of the current spectrum.
+ * grid_out [Lx*Ly][2] receives the projected cell centres (may be NULL); accepted and
+ * rejected (may be NULL) the step counts, t_end the final time. Returns CG_OK or
+ * CG_ESTEPFAIL. */
+int cartogram_integrate_once(cg_ctx* ctx, double* grid_out, long long* accepted,
+                             long long* rejected, double* t_end);
+
+/* Diagnostic timing of the hot kernel classes on the context's stream with CUDA events:
+ * each class is launched `reps` times on the current spectrum and the displacements
+ * of the last integration, and ms_out[k] receives the mean device time per launch of
+ *   0 inverse transform pass 1 (damping + rows), 1 inverse pass 2 (columns + velocity),
+ *   2 predictor-corrector step of all grid points, 3 rasterisation (clear + edges + scan),
+ *   4 forward transform (rows + columns), 5 vertex mapping + areas.
+ * ms_out has 6 entries. Errors: CG_ESTATE (no map or no spectrum), CG_EINVAL. */
+int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
+
+/* Description of the last error on this context ("" if none); valid until the next call. */
+const char* cartogram_last_error(const cg_ctx* ctx);
+
+/* Free the context and all its device memory. NULL is accepted. */
+void cartogram_destroy(cg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CARTOGRAM_H */

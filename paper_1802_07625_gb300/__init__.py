@@ -1,0 +1,374 @@
+"""GB300 (sm_103a) diffusion-flow cartogram library: Python binding of the C-ABI.
+
+Every function here marshals arguments for the call of the same name in
+include/cartogram.h and nothing else: all computation runs in the CUDA library
+(_build/libcartogram.so). Arrays may be numpy arrays (host) or torch tensors on the
+host or on the context's GPU; outputs are written into caller-provided arrays or
+freshly allocated numpy arrays. There is no CPU fallback: if the library is not
+built or CUDA is unusable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_ENOCONVERGE", "CG_EFOLD", "CG_ESTEPFAIL",
+    "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CartogramError", "Options", "Stats",
+    "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
+    "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_profile", "cartogram_history_length", "cartogram_get_grid", "cartogram_density",
+    "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
+    "cartogram_last_error", "cartogram_destroy", "Cartogram",
+]
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
+CG_ESTATE = -8
+CG_PRECISION_FP64, CG_PRECISION_MIXED = 0, 1
+
+_ERRNAMES = {0: "CG_OK", -1: "CG_EINVAL", -2: "CG_ENOMEM", -3: "CG_ECUDA", -4: "CG_ENOCONVERGE",
+             -5: "CG_EFOLD", -6: "CG_ESTEPFAIL", -8: "CG_ESTATE"}
+
+
+class CartogramError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_ERRNAMES.get(code, code), msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("dt0", ctypes.c_double), ("atol", ctypes.c_double),
+                ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("steps_accepted", ctypes.c_longlong), ("steps_rejected", ctypes.c_longlong),
+                ("max_area_error", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("step_loop_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library not built: %s (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "cartogram_default_options": (i, [ctypes.POINTER(Options)]),
+        "cartogram_init": (i, [i, i, d, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+        "cartogram_set_stream": (i, [_P, _P]),
+        "cartogram_set_regions": (i, [_P, i, _P, ll, _P, _P, _P]),
+        "cartogram_integrate": (i, [_P, ctypes.POINTER(Stats)]),
+        "cartogram_project": (i, [_P, ll, _P, _P]),
+        "cartogram_area_errors": (i, [_P, _P]),
+        "cartogram_get_vertices": (i, [_P, _P]),
+        "cartogram_history_length": (i, [_P]),
+        "cartogram_reset": (i, [_P]),
+        "cartogram_profile": (i, [_P, i, _P]),
+        "cartogram_get_grid": (i, [_P, i, _P]),
+        "cartogram_density": (i, [_P, _P]),
+        "cartogram_spectrum": (i, [_P, _P]),
+        "cartogram_velocity": (i, [_P, d, _P, _P]),
+        "cartogram_heun_step": (i, [_P, d, d, _P, _P, _P]),
+        "cartogram_integrate_once": (i, [_P, _P, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(d)]),
+        "cartogram_last_error": (ctypes.c_char_p, [_P]),
+        "cartogram_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, rc):
+    if rc != CG_OK:
+        msg = load().cartogram_last_error(ctx) if ctx else b""
+        raise CartogramError(rc, (msg or b"").decode())
+    return rc
+
+
+def _ptr(a, dtype, writable=False):
+    """Address of a contiguous numpy array or torch tensor of the given numpy dtype."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):  # torch tensor
+        import torch
+        want = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            if writable:
+                raise ValueError("output tensor must be contiguous %s" % want)
+            a = a.to(want).contiguous()
+        if a.is_cuda:
+            # the library's stream does not wait on torch's: make the data ready first
+            torch.cuda.current_stream(a.device).synchronize()
+        return a.data_ptr(), a
+    arr = np.asarray(a)
+    if arr.dtype != dtype or not arr.flags["C_CONTIGUOUS"]:
+        if writable:
+            raise ValueError("output array must be C-contiguous %s" % np.dtype(dtype))
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+    return arr.ctypes.data, arr
+
+
+# ---------------------------------------------------------------------------
+# one function per C entry point
+# ---------------------------------------------------------------------------
+
+def cartogram_default_options() -> Options:
+    o = Options()
+    _check(None, load().cartogram_default_options(ctypes.byref(o)))
+    return o
+
+
+def cartogram_init(Lx: int, Ly: int, blur_width: float, opt: Options | None = None) -> int:
+    ctx = _P()
+    rc = load().cartogram_init(int(Lx), int(Ly), float(blur_width),
+                               ctypes.byref(opt) if opt is not None else None, ctypes.byref(ctx))
+    if rc != CG_OK:
+        raise CartogramError(rc, "cartogram_init(%d, %d, %g) failed" % (Lx, Ly, blur_width))
+    return ctx.value
+
+
+def cartogram_set_stream(ctx, stream) -> None:
+    """`stream`: a torch.cuda.Stream, a raw cudaStream_t integer, or None (own stream)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(ctx, load().cartogram_set_stream(ctx, stream))
+
+
+def cartogram_set_regions(ctx, target_values, ring_offsets, ring_region, xy) -> None:
+    pv, v = _ptr(target_values, np.float64)
+    po, o = _ptr(ring_offsets, np.int64)
+    pr, r = _ptr(ring_region, np.int32)
+    px, x = _ptr(xy, np.float64)
+    n_regions = int(v.shape[0]) if hasattr(v, "shape") else len(v)
+    n_rings = int(r.shape[0]) if hasattr(r, "shape") else len(r)
+    _check(ctx, load().cartogram_set_regions(ctx, n_regions, pv, n_rings, po, pr, px))
+
+
+def cartogram_integrate(ctx) -> Stats:
+    s = Stats()
+    rc = load().cartogram_integrate(ctx, ctypes.byref(s))
+    if rc not in (CG_OK,):
+        err = CartogramError(rc, (load().cartogram_last_error(ctx) or b"").decode())
+        err.stats = s
+        raise err
+    return s
+
+
+def cartogram_project(ctx, xy_in, xy_out=None):
+    pi_, a = _ptr(xy_in, np.float64)
+    n = int(a.shape[0])
+    if xy_out is None:
+        xy_out = np.empty((n, 2), dtype=np.float64)
+    po, _ = _ptr(xy_out, np.float64, writable=True)
+    _check(ctx, load().cartogram_project(ctx, n, pi_, po))
+    return xy_out
+
+
+def cartogram_area_errors(ctx, out):
+    po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_area_errors(ctx, po))
+    return out
+
+
+def cartogram_get_vertices(ctx, out):
+    po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_get_vertices(ctx, po))
+    return out
+
+
+def cartogram_reset(ctx) -> None:
+    _check(ctx, load().cartogram_reset(ctx))
+
+
+PROFILE_CLASSES = ("inverse_rows", "inverse_cols_velocity", "heun_step", "rasterise", "forward",
+                   "map_and_areas")
+
+
+def cartogram_profile(ctx, reps: int = 20) -> dict:
+    out = np.zeros(len(PROFILE_CLASSES))
+    _check(ctx, load().cartogram_profile(ctx, int(reps), out.ctypes.data))
+    return dict(zip(PROFILE_CLASSES, out.tolist()))
+
+
+def cartogram_history_length(ctx) -> int:
+    return load().cartogram_history_length(ctx)
+
+
+def cartogram_get_grid(ctx, k, out):
+    po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_get_grid(ctx, int(k), po))
+    return out
+
+
+def cartogram_density(ctx, out):
+    po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_density(ctx, po))
+    return out
+
+
+def cartogram_spectrum(ctx, out=None):
+    po = None
+    if out is not None:
+        po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_spectrum(ctx, po))
+    return out
+
+
+def cartogram_velocity(ctx, t, rho_out=None, v_out=None):
+    pr = _ptr(rho_out, np.float64, writable=True)[0] if rho_out is not None else None
+    pv = _ptr(v_out, np.float64, writable=True)[0] if v_out is not None else None
+    _check(ctx, load().cartogram_velocity(ctx, float(t), pr, pv))
+    return rho_out, v_out
+
+
+def cartogram_heun_step(ctx, t, h, disp_in, disp_out):
+    pi_, _a = _ptr(disp_in, np.float64)
+    po, _ = _ptr(disp_out, np.float64, writable=True)
+    e = ctypes.c_double()
+    _check(ctx, load().cartogram_heun_step(ctx, float(t), float(h), pi_, po, ctypes.byref(e)))
+    return e.value
+
+
+def cartogram_integrate_once(ctx, grid_out=None):
+    pg = _ptr(grid_out, np.float64, writable=True)[0] if grid_out is not None else None
+    a, r, t = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, load().cartogram_integrate_once(ctx, pg, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t)))
+    return a.value, r.value, t.value
+
+
+def cartogram_last_error(ctx) -> str:
+    return (load().cartogram_last_error(ctx) or b"").decode()
+
+
+def cartogram_destroy(ctx) -> None:
+    if ctx:
+        load().cartogram_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience object owning a context
+# ---------------------------------------------------------------------------
+
+@dataclass
+class _Map:
+    n_regions: int
+    n_vertices: int
+
+
+class Cartogram:
+    """Owns one context; methods call the entry points above."""
+
+    def __init__(self, Lx, Ly, blur_width=0.0, precision="fp64", **options):
+        o = cartogram_default_options()
+        o.precision = CG_PRECISION_MIXED if precision == "mixed" else CG_PRECISION_FP64
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %s" % k)
+            setattr(o, k, v)
+        self.Lx, self.Ly = int(Lx), int(Ly)
+        self.options = o
+        self.ctx = cartogram_init(Lx, Ly, blur_width, o)
+        self._map = None
+
+    def close(self):
+        if self.ctx:
+            cartogram_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        cartogram_set_stream(self.ctx, stream)
+
+    def set_regions(self, values, ring_offsets, ring_region, xy):
+        cartogram_set_regions(self.ctx, values, ring_offsets, ring_region, xy)
+        self._map = _Map(len(values), int(np.asarray(ring_offsets)[-1]) if not hasattr(ring_offsets, "data_ptr")
+                         else int(ring_offsets[-1]))
+
+    def set_map(self, m):
+        self.set_regions(m.values, m.ring_offsets, m.ring_region, m.xy)
+
+    def integrate(self) -> Stats:
+        return cartogram_integrate(self.ctx)
+
+    def project(self, xy, out=None):
+        return cartogram_project(self.ctx, xy, out)
+
+    def area_errors(self):
+        return cartogram_area_errors(self.ctx, np.empty(self._map.n_regions))
+
+    def vertices(self):
+        return cartogram_get_vertices(self.ctx, np.empty((self._map.n_vertices, 2)))
+
+    def reset(self):
+        cartogram_reset(self.ctx)
+
+    def profile(self, reps=20):
+        return cartogram_profile(self.ctx, reps)
+
+    def history_length(self):
+        return cartogram_history_length(self.ctx)
+
+    def grid(self, k):
+        return cartogram_get_grid(self.ctx, k, np.empty((self.Ly, self.Lx, 2)))
+
+    def density(self):
+        return cartogram_density(self.ctx, np.empty((self.Ly, self.Lx)))
+
+    def spectrum(self):
+        return cartogram_spectrum(self.ctx, np.empty((self.Ly, self.Lx)))
+
+    def velocity(self, t):
+        rho = np.empty((self.Ly, self.Lx))
+        v = np.empty((self.Ly, self.Lx, 2))
+        cartogram_velocity(self.ctx, t, rho, v)
+        return rho, v
+
+    def heun_step(self, t, h, disp):
+        out = np.empty((self.Ly, self.Lx, 2))
+        err = cartogram_heun_step(self.ctx, t, h, disp, out)
+        return out, err
+
+    def integrate_once(self):
+        g = np.empty((self.Ly, self.Lx, 2))
+        a, r, t = cartogram_integrate_once(self.ctx, g)
+        return g, a, r, t

@@ -1,0 +1,188 @@
+// Advection of all Lx*Ly grid points by one predictor-corrector step (main text Eq.
+// rt_diff, integrated "using a predictor-corrector method that automatically adapts
+// the size of the next time step", with "interpolating between the grid points"),
+// and the device-side step controller.
+//
+// Positions are stored as displacements from the cell centres (i + 1/2, j + 1/2), so
+// in FP32 their rounding is relative to the displacement, not to the coordinate.
+// Interpolation lattice: the cell centres plus the walls x = 0, Lx and y = 0, Ly,
+// where the normal velocity vanishes (no flux through the box edges) and the
+// tangential velocity equals that of the nearest grid point. This is bilinear
+// interpolation with indices clamped to the grid, followed by a factor
+// min(1, 2x, 2(Lx - x)) on v_x (and likewise on v_y) inside the half-cell band.
+#pragma once
+
+#include "common.cuh"
+
+namespace cg {
+
+template <typename T>
+__device__ __forceinline__ V2<T> interp_v(const V2<T>* __restrict__ v, int Lx, int Ly, int i, int j,
+                                         T dx, T dy) {
+  // cell of the interpolation lattice; floors are clamped before the integer
+  // conversion and the indices clamped to the grid, so every load stays in bounds
+  const T flx = min(max(floor(dx), T(-2 - Lx)), T(Lx + 2));
+  const T fly = min(max(floor(dy), T(-2 - Ly)), T(Ly + 2));
+  const int ix = i + (int)flx, iy = j + (int)fly;
+  const T fx = dx - flx, fy = dy - fly;
+  const int i0 = min(max(ix, 0), Lx - 1), i1 = min(max(ix + 1, 0), Lx - 1);
+  const int j0 = min(max(iy, 0), Ly - 1), j1 = min(max(iy + 1, 0), Ly - 1);
+  const V2<T> a = v[(size_t)j0 * Lx + i0], b = v[(size_t)j0 * Lx + i1];
+  const V2<T> c = v[(size_t)j1 * Lx + i0], d = v[(size_t)j1 * Lx + i1];
+  const T gx = T(1) - fx, gy = T(1) - fy;
+  T ux = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
+  T uy = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
+  const T x = (T)i + T(0.5) + dx, y = (T)j + T(0.5) + dy;
+  if (ix < 0 || ix >= Lx - 1) ux *= min(T(1), min(T(2) * x, T(2) * ((T)Lx - x)));
+  if (iy < 0 || iy >= Ly - 1) uy *= min(T(1), min(T(2) * y, T(2) * ((T)Ly - y)));
+  return mk2<T>(ux, uy);
+}
+
+template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Accept / reject the attempt whose reductions are in st, update t, h, buffers and
+// status (one thread). The cap h * max|v| <= cfl uses the field at the accepted time.
+__device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
+                                             cudaGraphConditionalHandle handle, int use_cond) {
+  const double e = sqrt(__longlong_as_double((long long)st->err2_bits));
+  const double vmax_new = sqrt(__longlong_as_double((long long)st->vmax2_bits));
+  const double dev_new = __longlong_as_double((long long)st->dev_bits);
+  int status = kRunning;
+  double h = st->h;
+  if (st->bad) {
+    status = kStepFail;
+  } else if (e <= sp.atol) {
+    st->parity ^= 1;
+    st->t += h;
+    st->accepted += 1;
+    st->vmax = vmax_new;
+    if (dev_new <= sp.rho_tol) status = kDone;
+    else h *= sp.grow;
+  } else {
+    st->rejected += 1;
+    h *= sp.shrink;
+  }
+  if (status == kRunning) {
+    if (st->accepted + st->rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
+    else if (st->vmax > 0.0 && h * st->vmax > sp.cfl) h = sp.cfl / st->vmax;
+  }
+  st->h = h;
+  st->status = status;
+  st->err2_bits = 0;
+  st->vmax2_bits = 0;
+  st->dev_bits = 0;
+  st->ticket = 0;
+  st->bad = 0;
+  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+}
+
+// One Heun step of every grid point. Step mode: buffers by parity, h from the state,
+// and the last block to finish runs the controller. Fixed mode (single step on
+// explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0, dout = dbuf1, step h.
+template <typename T>
+__global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
+                                                    const V2<T>* vbuf0, const V2<T>* vbuf1,
+                                                    V2<T>* dbuf0, V2<T>* dbuf1, int Lx, int Ly,
+                                                    int log2Lx, int mode, double h_fixed,
+                                                    cudaGraphConditionalHandle handle, int use_cond) {
+  __shared__ T red[32];
+  __shared__ int last;
+  if (mode == kModeStep && st->status != kRunning) return;
+  const V2<T>* vcur = vbuf0;
+  const V2<T>* vnew = vbuf1;
+  const V2<T>* din = dbuf0;
+  V2<T>* dout = dbuf1;
+  double hd = h_fixed;
+  if (mode == kModeStep) {
+    const int par = st->parity;
+    vcur = par ? vbuf1 : vbuf0;
+    vnew = par ? vbuf0 : vbuf1;
+    din = par ? dbuf1 : dbuf0;
+    dout = par ? dbuf0 : dbuf1;
+    hd = st->h;
+  }
+  const T h = (T)hd, hh = (T)(0.5 * hd);
+  const int N = Lx * Ly;
+  T e2 = T(0);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    const int i = p & (Lx - 1), j = p >> log2Lx;
+    const V2<T> d = din[p];
+    const T lox = -((T)i + T(0.5)), hix = (T)(Lx - i) - T(0.5);
+    const T loy = -((T)j + T(0.5)), hiy = (T)(Ly - j) - T(0.5);
+    const V2<T> u0 = interp_v<T>(vcur, Lx, Ly, i, j, d.x, d.y);
+    const T px = clampT(d.x + h * u0.x, lox, hix);
+    const T py = clampT(d.y + h * u0.y, loy, hiy);
+    const V2<T> u1 = interp_v<T>(vnew, Lx, Ly, i, j, px, py);
+    const T cx = clampT(d.x + hh * (u0.x + u1.x), lox, hix);
+    const T cy = clampT(d.y + hh * (u0.y + u1.y), loy, hiy);
+    dout[p] = mk2<T>(cx, cy);
+    const T ex = cx - px, ey = cy - py;
+    e2 = max(e2, ex * ex + ey * ey);
+  }
+  e2 = block_max(e2, red);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&st->err2_bits, (double)e2);
+    if (mode == kModeStep) {
+      __threadfence();
+      const unsigned int t = atomicAdd(&st->ticket, 1u);
+      last = (t == gridDim.x - 1);
+    }
+  }
+  if (mode != kModeStep) return;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    control_step(st, sp, handle, use_cond);
+  }
+}
+
+// Reset the state for a new integration (t = 0, h = dt0, parity 0, counters 0).
+__global__ void init_state_kernel(DevState* st, StepParams sp) {
+  st->t = 0.0;
+  st->h = sp.dt0;
+  st->vmax = 0.0;
+  st->accepted = 0;
+  st->rejected = 0;
+  st->parity = 0;
+  st->status = kRunning;
+  st->err2_bits = 0;
+  st->vmax2_bits = 0;
+  st->dev_bits = 0;
+  st->ticket = 0;
+  st->bad = 0;
+  st->body_iters = 0;
+}
+
+// After the field at t = 0: stop at once if the density is already equal, else cap
+// the first step.
+__global__ void init_finish_kernel(DevState* st, StepParams sp, cudaGraphConditionalHandle handle,
+                                   int use_cond) {
+  const double vmax = sqrt(__longlong_as_double((long long)st->vmax2_bits));
+  const double dev = __longlong_as_double((long long)st->dev_bits);
+  int status = kRunning;
+  double h = sp.dt0;
+  if (st->bad) status = kStepFail;
+  else if (dev <= sp.rho_tol) status = kDone;
+  else if (vmax > 0.0 && h * vmax > sp.cfl) h = sp.cfl / vmax;
+  st->vmax = vmax;
+  st->h = h;
+  st->status = status;
+  st->err2_bits = 0;
+  st->vmax2_bits = 0;
+  st->dev_bits = 0;
+  st->ticket = 0;
+  st->bad = 0;
+  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+}
+
+// Copy the displacements of the current buffer (selected by parity) to `dst`.
+template <typename T>
+__global__ void snapshot_kernel(const DevState* st, const V2<T>* dbuf0, const V2<T>* dbuf1,
+                                V2<T>* dst, int N) {
+  const V2<T>* src = st->parity ? dbuf1 : dbuf0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) dst[p] = src[p];
+}
+
+}  // namespace cg

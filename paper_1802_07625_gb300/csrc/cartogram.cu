@@ -1,0 +1,894 @@
+// C-ABI of the cartogram library: context, validation, device memory, the CUDA graph
+// of one integration, and the outer iteration. Declarations and their contracts are
+// in include/cartogram.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cartogram.h"
+#include "kernels.h"
+
+using cg::DevState;
+using cg::IterInfo;
+using cg::StepParams;
+using cg::V2;
+
+struct cg_ctx {
+  int Lx = 0, Ly = 0, log2Lx = 0, log2Ly = 0;
+  double blur = 0.0;
+  cg_options opt{};
+  bool mixed = false;
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // transform tables: inverse roots and quarter-wave factors in the working type,
+  // forward (FP64) roots, quarter-wave factors and blur factors
+  void *Wx = nullptr, *Wy = nullptr, *Ex = nullptr, *Ey = nullptr;
+  double2 *Wfx = nullptr, *Wfy = nullptr, *Efx = nullptr, *Efy = nullptr;
+  double *bx = nullptr, *by = nullptr;
+
+  // fields
+  double* acc = nullptr;     // rasterised rho/rho_bar - 1 (FP64)
+  double* R = nullptr;       // forward transform along x
+  double* spec64 = nullptr;  // blurred cosine spectrum (FP64), (0,0) removed
+  void* specT = nullptr;     // spectrum in the working type (aliases spec64 in FP64)
+  void* AB = nullptr;        // pass-1 output
+  void* vbuf[2] = {nullptr, nullptr};
+  void* dbuf[2] = {nullptr, nullptr};
+  void* dres = nullptr;      // displacements of the last integration
+  void* rho_tmp = nullptr;   // density output of the field entry point
+  DevState* st = nullptr;
+  IterInfo* info = nullptr;
+  IterInfo* info_h = nullptr;  // pinned
+  bool have_spectrum = false;
+
+  // map
+  bool have_regions = false;
+  int R_n = 0;
+  long long n_rings = 0, n_vert = 0;
+  double* values = nullptr;
+  long long* ring_off = nullptr;
+  int* reg_off = nullptr;
+  int* reg_rings = nullptr;
+  int* next = nullptr;
+  int* vreg = nullptr;
+  double2* xy = nullptr;
+  double2* xy0 = nullptr;  // vertices as given to set_regions
+  double* ring_area = nullptr;
+  double* area = nullptr;
+  double* err_d = nullptr;
+  double* w = nullptr;
+  std::vector<void*> hist;
+  int hist_len = 0;
+  double2* pts = nullptr;
+  long long pts_cap = 0;
+
+  // graph of one integration
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int fail(cg_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CG_CUDA(ctx, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+  } while (0)
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+StepParams step_params(const cg_ctx* c) {
+  StepParams sp;
+  sp.dt0 = c->opt.dt0;
+  sp.atol = c->opt.atol;
+  sp.grow = c->opt.grow;
+  sp.shrink = c->opt.shrink;
+  sp.cfl = c->opt.cfl;
+  sp.rho_tol = c->opt.rho_tol;
+  sp.h_min = 0.0;
+  sp.max_steps = c->opt.max_steps;
+  return sp;
+}
+
+template <typename T>
+int upload_tables(cg_ctx* c, int N, void** Wd, void** Ed, double2** Wfd, double2** Efd) {
+  // roots W[p] = exp(+2 pi i p/N) and quarter-wave factors E[m] = exp(i pi m/(2N)),
+  // angles reduced exactly on the integers before the library cos/sin
+  std::vector<V2<T>> W(N), E(N);
+  std::vector<double2> Wf(N), Ef(N);
+  for (int p = 0; p < N; ++p) {
+    const double a = 2.0 * cg::kPi * (double)p / N;
+    const double cw = std::cos(a), sw = std::sin(a);
+    W[p].x = (T)cw;
+    W[p].y = (T)sw;
+    Wf[p] = make_double2(cw, -sw);
+    const double b = cg::kPi * (double)p / (2.0 * N);
+    const double ce = std::cos(b), se = std::sin(b);
+    E[p].x = (T)ce;
+    E[p].y = (T)se;
+    Ef[p] = make_double2(ce, se);
+  }
+  CG_CUDA(c, cudaMalloc(Wd, sizeof(V2<T>) * N));
+  CG_CUDA(c, cudaMalloc(Ed, sizeof(V2<T>) * N));
+  CG_CUDA(c, cudaMalloc((void**)Wfd, sizeof(double2) * N));
+  CG_CUDA(c, cudaMalloc((void**)Efd, sizeof(double2) * N));
+  CG_CUDA(c, cudaMemcpy(*Wd, W.data(), sizeof(V2<T>) * N, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(*Ed, E.data(), sizeof(V2<T>) * N, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(*Wfd, Wf.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(*Efd, Ef.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
+int upload_blur(cg_ctx* c, int N, double sigma, double** d) {
+  std::vector<double> b(N);
+  for (int m = 0; m < N; ++m) {
+    const double k = cg::kPi * m / N;
+    b[m] = std::exp(-0.5 * k * k * sigma * sigma);
+  }
+  CG_CUDA(c, cudaMalloc((void**)d, sizeof(double) * N));
+  CG_CUDA(c, cudaMemcpy(*d, b.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
+template <typename T>
+int alloc_fields(cg_ctx* c) {
+  const size_t N = (size_t)c->Lx * c->Ly;
+  int r = upload_tables<T>(c, c->Lx, &c->Wx, &c->Ex, &c->Wfx, &c->Efx);
+  if (r) return r;
+  r = upload_tables<T>(c, c->Ly, &c->Wy, &c->Ey, &c->Wfy, &c->Efy);
+  if (r) return r;
+  if ((r = upload_blur(c, c->Lx, c->blur, &c->bx))) return r;
+  if ((r = upload_blur(c, c->Ly, c->blur, &c->by))) return r;
+  CG_CUDA(c, cudaMalloc((void**)&c->acc, sizeof(double) * N));
+  CG_CUDA(c, cudaMalloc((void**)&c->R, sizeof(double) * N));
+  CG_CUDA(c, cudaMalloc((void**)&c->spec64, sizeof(double) * N));
+  if (sizeof(T) == 4) {
+    CG_CUDA(c, cudaMalloc(&c->specT, sizeof(T) * N));
+  } else {
+    c->specT = c->spec64;
+  }
+  CG_CUDA(c, cudaMalloc(&c->AB, sizeof(V2<T>) * N));
+  for (int k = 0; k < 2; ++k) {
+    CG_CUDA(c, cudaMalloc(&c->vbuf[k], sizeof(V2<T>) * N));
+    CG_CUDA(c, cudaMalloc(&c->dbuf[k], sizeof(V2<T>) * N));
+  }
+  CG_CUDA(c, cudaMalloc(&c->dres, sizeof(V2<T>) * N));
+  CG_CUDA(c, cudaMalloc(&c->rho_tmp, sizeof(T) * N));
+  CG_CUDA(c, cudaMalloc((void**)&c->st, sizeof(DevState)));
+  CG_CUDA(c, cudaMemset(c->st, 0, sizeof(DevState)));
+  CG_CUDA(c, cudaMalloc((void**)&c->info, sizeof(IterInfo)));
+  CG_CUDA(c, cudaMallocHost((void**)&c->info_h, sizeof(IterInfo)));
+  CG_CUDA(c, cudaMemset(c->spec64, 0, sizeof(double) * N));
+  if (sizeof(T) == 4) CG_CUDA(c, cudaMemset(c->specT, 0, sizeof(T) * N));
+  CG_CUDA(c, cg::prepare_spectral<T>(c->log2Lx, c->log2Ly));
+  CG_CUDA(c, cg::prepare_forward(c->log2Lx, c->log2Ly));
+  return CG_OK;
+}
+
+// ---- the kernels of one integration ------------------------------------------
+
+template <typename T>
+void enqueue_field(cg_ctx* c, int mode, double tau, V2<T>* out0, V2<T>* out1, T* rho_out,
+                   cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
+  cg::launch_inv_rows<T>(c->log2Lx, c->Ly, (const T*)c->specT, (V2<T>*)c->AB, (const V2<T>*)c->Wx,
+                         (const V2<T>*)c->Ex, c->st, mode, tau, h, use_cond,
+                         (unsigned int)c->opt.max_steps + 8u, s);
+  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, (const V2<T>*)c->AB, out0, out1, rho_out,
+                         (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, mode, s);
+}
+
+template <typename T>
+void enqueue_init(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const StepParams sp = step_params(c);
+  cg::launch_init_state(c->st, sp, s);
+  cudaMemsetAsync(c->dbuf[0], 0, sizeof(V2<T>) * (size_t)c->Lx * c->Ly, s);
+  enqueue_field<T>(c, cg::kModeInit, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s);
+  cg::launch_init_finish(c->st, sp, h, use_cond, s);
+}
+
+template <typename T>
+void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const StepParams sp = step_params(c);
+  enqueue_field<T>(c, cg::kModeStep, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s, h,
+                   use_cond);
+  cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
+                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeStep, 0.0, h,
+                     use_cond, s);
+}
+
+template <typename T>
+void enqueue_finish(cg_ctx* c, cudaStream_t s) {
+  cg::launch_snapshot<T>(c->st, (const V2<T>*)c->dbuf[0], (const V2<T>*)c->dbuf[1], (V2<T>*)c->dres,
+                         c->Lx * c->Ly, s);
+  cg::launch_collect(c->st, c->info, s);
+}
+
+// One integration as a graph: init kernels, then a WHILE node whose body is one
+// attempted step (field at t+h, Heun step + controller); the controller clears the
+// condition when the integration ends.
+template <typename T>
+int build_graph(cg_ctx* c) {
+  cudaStream_t cs = nullptr, bs = nullptr;
+  CG_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CG_CUDA(c, cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  int rc = CG_OK;
+  do {
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "begin capture: %s", cudaGetErrorString(e)); break; }
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg_graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg_graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(cs, &g);
+      rc = fail(c, CG_ECUDA, "conditional handle: %s", cudaGetErrorString(e));
+      break;
+    }
+    enqueue_init<T>(c, h, 1, cs);
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg_graph, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaGraph_t body = cp.conditional.phGraph_out ? cp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      enqueue_body<T>(c, h, 1, bs);
+      cudaGraph_t bg = nullptr;
+      e = cudaStreamEndCapture(bs, &bg);
+    }
+    if (e == cudaSuccess) enqueue_finish<T>(c, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "graph capture: %s", cudaGetErrorString(e)); break; }
+    e = cudaGraphInstantiate(&c->exec, g, 0);
+    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); break; }
+    c->graph = g;
+    c->cond = h;
+    g = nullptr;
+  } while (0);
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  cudaStreamDestroy(cs);
+  cudaStreamDestroy(bs);
+  return rc;
+}
+
+// Run one integration of the current spectrum; the projected grid ends in dres and
+// the outcome in info (device). Records the step-loop time between ev0 and ev1.
+template <typename T>
+int run_integration(cg_ctx* c) {
+  cudaStream_t s = c->stream;
+  if (c->opt.use_graph) {
+    if (!c->exec) {
+      int r = build_graph<T>(c);
+      if (r) return r;
+    }
+    CG_CUDA(c, cudaEventRecord(c->ev0, s));
+    CG_CUDA(c, cudaGraphLaunch(c->exec, s));
+    CG_CUDA(c, cudaEventRecord(c->ev1, s));
+    return CG_OK;
+  }
+  // host-driven loop: the same kernels; the kernels return at once after the end
+  CG_CUDA(c, cudaEventRecord(c->ev0, s));
+  enqueue_init<T>(c, 0, 0, s);
+  const int chunk = 8;
+  for (long long done = 0; done < (long long)c->opt.max_steps + chunk; done += chunk) {
+    for (int k = 0; k < chunk; ++k) enqueue_body<T>(c, 0, 0, s);
+    cg::launch_collect(c->st, c->info, s);
+    CG_CUDA(c, cudaMemcpyAsync(c->info_h, c->info, sizeof(IterInfo), cudaMemcpyDeviceToHost, s));
+    CG_CUDA(c, cudaStreamSynchronize(s));
+    if (c->info_h->status != cg::kRunning) break;
+  }
+  enqueue_finish<T>(c, s);
+  CG_CUDA(c, cudaEventRecord(c->ev1, s));
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+template <typename T>
+int run_forward(cg_ctx* c) {
+  cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
+                    sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy, c->bx,
+                    c->by, c->stream);
+  c->have_spectrum = true;
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int run_raster(cg_ctx* c) {
+  CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->Lx * c->Ly, c->stream));
+  cg::launch_raster(c->xy, c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, (int)c->n_vert, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int run_areas(cg_ctx* c) {
+  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings,
+                   c->values, c->R_n, c->area, c->err_d, c->w, c->info, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int read_info(cg_ctx* c) {
+  CG_CUDA(c, cudaMemcpyAsync(c->info_h, c->info, sizeof(IterInfo), cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+template <typename T>
+int do_integrate(cg_ctx* c, cg_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cg_stats s;
+  memset(&s, 0, sizeof s);
+  int r;
+  if ((r = run_areas(c)) || (r = read_info(c))) return r;
+  double max_err = c->info_h->max_err;
+  int status = CG_OK;
+  const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
+  int it = 0;
+  while (!(max_err < c->opt.area_tol)) {
+    if (it >= c->opt.max_iter) {
+      status = fail(c, CG_ENOCONVERGE, "no convergence after %d iterations (max error %g)", it, max_err);
+      break;
+    }
+    if ((r = run_raster(c)) || (r = run_forward<T>(c)) || (r = run_integration<T>(c)) ||
+        (r = read_info(c)))
+      return r;
+    const IterInfo inf = *c->info_h;
+    float ms = 0.f;
+    CG_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    s.step_loop_ms += ms;
+    s.steps_accepted += inf.accepted;
+    s.steps_rejected += inf.rejected;
+    s.t_end = inf.t_end;
+    if (inf.status != cg::kDone) {
+      status = fail(c, CG_ESTEPFAIL, "integration %d ended with status %d after %lld/%lld steps", it + 1,
+                    inf.status, inf.accepted, inf.rejected);
+      break;
+    }
+    if ((int)c->hist.size() <= c->hist_len) {
+      void* p = nullptr;
+      CG_CUDA(c, cudaMalloc(&p, fbytes));
+      c->hist.push_back(p);
+    }
+    void* grid = c->hist[c->hist_len];
+    CG_CUDA(c, cudaMemcpyAsync(grid, c->dres, fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)grid, c->Lx, c->Ly, c->stream);
+    if ((r = run_areas(c)) || (r = read_info(c))) return r;
+    max_err = c->info_h->max_err;
+    ++it;
+    ++c->hist_len;
+  }
+  s.iterations = it;
+  s.converged = max_err < c->opt.area_tol;
+  s.max_area_error = max_err;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = s;
+  return status;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+int check_ctx(cg_ctx* c, bool need_regions) {
+  if (!c) return CG_EINVAL;
+  c->err.clear();
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, CG_ECUDA, "cudaSetDevice failed");
+  if (need_regions && !c->have_regions) return fail(c, CG_ESTATE, "no map: call cartogram_set_regions first");
+  return CG_OK;
+}
+
+template <typename T>
+int copy_field_out(cg_ctx* c, const void* src, double* dst, int comps) {
+  // widen T -> double on the host (entry points for inspection, not the hot path)
+  const size_t n = (size_t)c->Lx * c->Ly * comps;
+  std::vector<T> h(n);
+  CG_CUDA(c, cudaMemcpyAsync(h.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> o(h.begin(), h.end());
+  CG_CUDA(c, cudaMemcpy(dst, o.data(), sizeof(double) * n, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+template <typename T>
+int copy_field_in(cg_ctx* c, const double* src, void* dst, int comps) {
+  const size_t n = (size_t)c->Lx * c->Ly * comps;
+  std::vector<double> h(n);
+  CG_CUDA(c, cudaMemcpy(h.data(), src, sizeof(double) * n, cudaMemcpyDefault));
+  std::vector<T> t(h.begin(), h.end());
+  CG_CUDA(c, cudaMemcpyAsync(dst, t.data(), sizeof(T) * n, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+template <typename T>
+int do_velocity(cg_ctx* c, double t, double* rho_out, double* v_out) {
+  CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  enqueue_field<T>(c, cg::kModeFixed, t, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], (T*)c->rho_tmp,
+                   c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  int r;
+  if (rho_out && (r = copy_field_out<T>(c, c->rho_tmp, rho_out, 1))) return r;
+  if (v_out && (r = copy_field_out<T>(c, c->vbuf[0], v_out, 2))) return r;
+  return CG_OK;
+}
+
+template <typename T>
+int do_heun(cg_ctx* c, double t, double h, const double* din, double* dout, double* err) {
+  CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  enqueue_field<T>(c, cg::kModeFixed, t, (V2<T>*)c->vbuf[0], nullptr, nullptr, c->stream);
+  enqueue_field<T>(c, cg::kModeFixed, t + h, (V2<T>*)c->vbuf[1], nullptr, nullptr, c->stream);
+  int r = copy_field_in<T>(c, din, c->dbuf[0], 2);
+  if (r) return r;
+  CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
+                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0,
+                     c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  if ((r = copy_field_out<T>(c, c->dbuf[1], dout, 2))) return r;
+  DevState hs;
+  CG_CUDA(c, cudaMemcpy(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost));
+  if (err) {
+    double e2;
+    memcpy(&e2, &hs.err2_bits, sizeof e2);
+    *err = std::sqrt(e2);
+  }
+  return CG_OK;
+}
+
+template <typename T>
+int grid_out(cg_ctx* c, const void* disp, double* out) {
+  const size_t N = (size_t)c->Lx * c->Ly;
+  std::vector<T> h(2 * N);
+  CG_CUDA(c, cudaMemcpyAsync(h.data(), disp, sizeof(T) * 2 * N, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> o(2 * N);
+  for (int j = 0; j < c->Ly; ++j)
+    for (int i = 0; i < c->Lx; ++i) {
+      const size_t p = (size_t)j * c->Lx + i;
+      o[2 * p] = i + 0.5 + (double)h[2 * p];
+      o[2 * p + 1] = j + 0.5 + (double)h[2 * p + 1];
+    }
+  CG_CUDA(c, cudaMemcpy(out, o.data(), sizeof(double) * 2 * N, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+template <typename T>
+int do_integrate_once(cg_ctx* c, double* grid, long long* acc, long long* rej, double* t_end) {
+  int r = run_integration<T>(c);
+  if (r) return r;
+  if ((r = read_info(c))) return r;
+  const IterInfo inf = *c->info_h;
+  if (acc) *acc = inf.accepted;
+  if (rej) *rej = inf.rejected;
+  if (t_end) *t_end = inf.t_end;
+  if (grid && (r = grid_out<T>(c, c->dres, grid))) return r;
+  if (inf.status != cg::kDone) return fail(c, CG_ESTEPFAIL, "integration ended with status %d", inf.status);
+  return CG_OK;
+}
+
+int ensure_pts(cg_ctx* c, long long n) {
+  if (n > c->pts_cap) {
+    if (c->pts) cudaFree(c->pts);
+    c->pts = nullptr;
+    c->pts_cap = 0;
+    CG_CUDA(c, cudaMalloc((void**)&c->pts, sizeof(double2) * n));
+    c->pts_cap = n;
+  }
+  return CG_OK;
+}
+
+template <typename T>
+int do_project(cg_ctx* c, int64_t n, const double* in, double* out) {
+  if (n == 0) return CG_OK;
+  int r = ensure_pts(c, n);
+  if (r) return r;
+  CG_CUDA(c, cudaMemcpyAsync(c->pts, in, sizeof(double2) * n, cudaMemcpyDefault, c->stream));
+  for (int k = 0; k < c->hist_len; ++k)
+    cg::launch_map_points<T>(c->pts, c->pts, n, (const V2<T>*)c->hist[k], c->Lx, c->Ly, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  CG_CUDA(c, cudaMemcpyAsync(out, c->pts, sizeof(double2) * n, cudaMemcpyDefault, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+template <typename T>
+int do_profile(cg_ctx* c, int reps, double* ms_out) {
+  cudaStream_t s = c->stream;
+  cudaEvent_t a, b;
+  CG_CUDA(c, cudaEventCreate(&a));
+  CG_CUDA(c, cudaEventCreate(&b));
+  const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
+  double out[6] = {0, 0, 0, 0, 0, 0};
+  CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  CG_CUDA(c, cudaMemcpyAsync(c->dbuf[0], c->dres, fbytes, cudaMemcpyDeviceToDevice, s));
+  int r0 = ensure_pts(c, c->n_vert);
+  if (r0) return r0;
+  const double t = 1.0, h = 0.5;
+  enqueue_field<T>(c, cg::kModeFixed, t, (V2<T>*)c->vbuf[0], nullptr, nullptr, s);
+  enqueue_field<T>(c, cg::kModeFixed, t + h, (V2<T>*)c->vbuf[1], nullptr, nullptr, s);
+  for (int k = 0; k < 6; ++k) {
+    CG_CUDA(c, cudaEventRecord(a, s));
+    for (int r = 0; r < reps; ++r) {
+      switch (k) {
+        case 0:
+          cg::launch_inv_rows<T>(c->log2Lx, c->Ly, (const T*)c->specT, (V2<T>*)c->AB, (const V2<T>*)c->Wx,
+                                 (const V2<T>*)c->Ex, c->st, cg::kModeFixed, t + h, 0, 0, 0u, s);
+          break;
+        case 1:
+          cg::launch_inv_cols<T>(c->log2Ly, c->Lx, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr, nullptr,
+                                 (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
+          break;
+        case 2:
+          cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
+                             (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0, s);
+          break;
+        case 3:
+          run_raster(c);
+          break;
+        case 4:
+          cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
+                            sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                            c->bx, c->by, s);
+          break;
+        default:
+          cg::launch_map_points<T>(c->xy0, c->pts, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s);
+          cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings,
+                           c->values, c->R_n, c->area, c->err_d, c->w, c->info, s);
+          break;
+      }
+    }
+    CG_CUDA(c, cudaEventRecord(b, s));
+    CG_CUDA(c, cudaEventSynchronize(b));
+    float ms = 0.f;
+    CG_CUDA(c, cudaEventElapsedTime(&ms, a, b));
+    out[k] = ms / reps;
+  }
+  CG_CUDA(c, cudaGetLastError());
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CG_CUDA(c, cudaMemcpy(ms_out, out, sizeof out, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+void free_regions(cg_ctx* c) {
+  void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
+                c->xy, c->xy0, c->ring_area, c->area, c->err_d, c->w};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  c->values = nullptr; c->ring_off = nullptr; c->reg_off = nullptr; c->reg_rings = nullptr;
+  c->next = nullptr; c->vreg = nullptr; c->xy = nullptr; c->xy0 = nullptr;
+  c->ring_area = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
+  c->have_regions = false;
+}
+
+}  // namespace
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+
+extern "C" {
+
+int cartogram_default_options(cg_options* o) {
+  if (!o) return CG_EINVAL;
+  o->precision = CG_PRECISION_FP64;
+  o->dt0 = 1e-2;
+  o->atol = 1e-2;
+  o->grow = 1.2;
+  o->shrink = 0.5;
+  o->cfl = 1.0;
+  o->rho_tol = 1e-4;
+  o->area_tol = 0.01;
+  o->max_steps = 4000;
+  o->max_iter = 50;
+  o->use_graph = 1;
+  return CG_OK;
+}
+
+int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_ctx** out) {
+  if (!out) return CG_EINVAL;
+  *out = nullptr;
+  if (!pow2_in_range(Lx) || !pow2_in_range(Ly)) return CG_EINVAL;
+  if (!is_finite(blur_width) || blur_width < 0.0) return CG_EINVAL;
+  cg_options o;
+  cartogram_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED) return CG_EINVAL;
+  if (!(o.dt0 > 0) || !(o.atol > 0) || !(o.grow >= 1.0) || !(o.shrink > 0 && o.shrink < 1) ||
+      !(o.cfl > 0) || !(o.rho_tol > 0) || !(o.area_tol > 0) || o.max_steps < 1 || o.max_iter < 0 ||
+      !is_finite(o.dt0) || !is_finite(o.atol) || !is_finite(o.grow) || !is_finite(o.cfl) || !is_finite(o.rho_tol) ||
+      !is_finite(o.area_tol))
+    return CG_EINVAL;
+  cg_ctx* c = new cg_ctx();
+  c->Lx = Lx;
+  c->Ly = Ly;
+  c->log2Lx = ilog2(Lx);
+  c->log2Ly = ilog2(Ly);
+  c->blur = blur_width;
+  c->opt = o;
+  c->mixed = o.precision == CG_PRECISION_MIXED;
+  int r = CG_OK;
+  if (cudaGetDevice(&c->device) != cudaSuccess) r = CG_ECUDA;
+  if (!r && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) r = CG_ECUDA;
+  c->stream = c->own_stream;
+  if (!r && (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)) r = CG_ECUDA;
+  if (!r) r = c->mixed ? alloc_fields<float>(c) : alloc_fields<double>(c);
+  if (r) {
+    cudaGetLastError();
+    cartogram_destroy(c);
+    return r;
+  }
+  *out = c;
+  return CG_OK;
+}
+
+int cartogram_set_stream(cg_ctx* c, void* stream) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return CG_OK;
+}
+
+int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values, int64_t n_rings,
+                          const int64_t* ring_offsets, const int32_t* ring_region,
+                          const double* xy) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (n_regions < 1 || n_rings < 1 || !target_values || !ring_offsets || !ring_region || !xy)
+    return fail(c, CG_EINVAL, "empty map or NULL array");
+  if (n_rings > (1LL << 30)) return fail(c, CG_EINVAL, "too many rings");
+  // inputs may live on the host or the device: bring them to the host to validate
+  std::vector<double> vals(n_regions);
+  std::vector<long long> off(n_rings + 1);
+  std::vector<int> reg(n_rings);
+  CG_CUDA(c, cudaMemcpy(vals.data(), target_values, sizeof(double) * n_regions, cudaMemcpyDefault));
+  CG_CUDA(c, cudaMemcpy(off.data(), ring_offsets, sizeof(long long) * (n_rings + 1), cudaMemcpyDefault));
+  CG_CUDA(c, cudaMemcpy(reg.data(), ring_region, sizeof(int) * n_rings, cudaMemcpyDefault));
+  for (int k = 0; k < n_regions; ++k)
+    if (!is_finite(vals[k]) || !(vals[k] > 0.0)) return fail(c, CG_EINVAL, "target value %d is not positive and finite", k);
+  if (off[0] != 0) return fail(c, CG_EINVAL, "ring_offsets[0] must be 0");
+  for (long long k = 0; k < n_rings; ++k) {
+    if (off[k + 1] - off[k] < 3) return fail(c, CG_EINVAL, "ring %lld has fewer than 3 vertices", k);
+    if (reg[k] < 0 || reg[k] >= n_regions) return fail(c, CG_EINVAL, "ring %lld has region %d out of range", k, reg[k]);
+  }
+  const long long nv = off[n_rings];
+  if (nv >= (1LL << 31)) return fail(c, CG_EINVAL, "too many vertices");
+  std::vector<double> pts(2 * (size_t)nv);
+  CG_CUDA(c, cudaMemcpy(pts.data(), xy, sizeof(double) * 2 * nv, cudaMemcpyDefault));
+  for (long long k = 0; k < nv; ++k) {
+    const double x = pts[2 * k], y = pts[2 * k + 1];
+    if (!is_finite(x) || !is_finite(y) || x < 0.0 || x > c->Lx || y < 0.0 || y > c->Ly)
+      return fail(c, CG_EINVAL, "vertex %lld (%g, %g) is outside the box [0,%d]x[0,%d]", k, x, y, c->Lx, c->Ly);
+  }
+  // per-vertex successor and region, region -> rings index
+  std::vector<int> next(nv), vreg(nv), reg_off(n_regions + 1, 0), reg_rings(n_rings);
+  for (long long k = 0; k < n_rings; ++k) {
+    for (long long v = off[k]; v < off[k + 1]; ++v) {
+      next[v] = (int)(v + 1 < off[k + 1] ? v + 1 : off[k]);
+      vreg[v] = reg[k];
+    }
+    reg_off[reg[k] + 1]++;
+  }
+  for (int k = 0; k < n_regions; ++k) reg_off[k + 1] += reg_off[k];
+  {
+    std::vector<int> fill(reg_off.begin(), reg_off.end() - 1);
+    for (long long k = 0; k < n_rings; ++k) reg_rings[fill[reg[k]]++] = (int)k;
+  }
+  free_regions(c);
+  c->R_n = n_regions;
+  c->n_rings = n_rings;
+  c->n_vert = nv;
+  CG_CUDA(c, cudaMalloc((void**)&c->values, sizeof(double) * n_regions));
+  CG_CUDA(c, cudaMalloc((void**)&c->ring_off, sizeof(long long) * (n_rings + 1)));
+  CG_CUDA(c, cudaMalloc((void**)&c->reg_off, sizeof(int) * (n_regions + 1)));
+  CG_CUDA(c, cudaMalloc((void**)&c->reg_rings, sizeof(int) * n_rings));
+  CG_CUDA(c, cudaMalloc((void**)&c->next, sizeof(int) * nv));
+  CG_CUDA(c, cudaMalloc((void**)&c->vreg, sizeof(int) * nv));
+  CG_CUDA(c, cudaMalloc((void**)&c->xy, sizeof(double2) * nv));
+  CG_CUDA(c, cudaMalloc((void**)&c->xy0, sizeof(double2) * nv));
+  CG_CUDA(c, cudaMalloc((void**)&c->ring_area, sizeof(double) * n_rings));
+  CG_CUDA(c, cudaMalloc((void**)&c->area, sizeof(double) * n_regions));
+  CG_CUDA(c, cudaMalloc((void**)&c->err_d, sizeof(double) * n_regions));
+  CG_CUDA(c, cudaMalloc((void**)&c->w, sizeof(double) * n_regions));
+  CG_CUDA(c, cudaMemcpy(c->values, vals.data(), sizeof(double) * n_regions, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->ring_off, off.data(), sizeof(long long) * (n_rings + 1), cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->reg_off, reg_off.data(), sizeof(int) * (n_regions + 1), cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->reg_rings, reg_rings.data(), sizeof(int) * n_rings, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->next, next.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->vreg, vreg.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->xy, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->xy0, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
+  c->have_regions = true;
+  c->hist_len = 0;
+  c->have_spectrum = false;
+  // every region needs a positive area
+  if ((r = run_areas(c)) || (r = read_info(c))) return r;
+  std::vector<double> area(n_regions);
+  CG_CUDA(c, cudaMemcpy(area.data(), c->area, sizeof(double) * n_regions, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n_regions; ++k)
+    if (!(area[k] > 0.0)) {
+      free_regions(c);
+      return fail(c, CG_EINVAL, "region %d has non-positive area %g", k, area[k]);
+    }
+  return CG_OK;
+}
+
+int cartogram_integrate(cg_ctx* c, cg_stats* stats) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  return c->mixed ? do_integrate<float>(c, stats) : do_integrate<double>(c, stats);
+}
+
+int cartogram_project(cg_ctx* c, int64_t n, const double* xy_in, double* xy_out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (n < 0 || (n > 0 && (!xy_in || !xy_out))) return fail(c, CG_EINVAL, "bad point array");
+  return c->mixed ? do_project<float>(c, n, xy_in, xy_out) : do_project<double>(c, n, xy_in, xy_out);
+}
+
+int cartogram_area_errors(cg_ctx* c, double* err) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!err) return fail(c, CG_EINVAL, "NULL output");
+  if ((r = run_areas(c)) || (r = read_info(c))) return r;
+  CG_CUDA(c, cudaMemcpy(err, c->err_d, sizeof(double) * c->R_n, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+int cartogram_get_vertices(cg_ctx* c, double* xy_out) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!xy_out) return fail(c, CG_EINVAL, "NULL output");
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  CG_CUDA(c, cudaMemcpy(xy_out, c->xy, sizeof(double2) * c->n_vert, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+int cartogram_reset(cg_ctx* c) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  CG_CUDA(c, cudaMemcpyAsync(c->xy, c->xy0, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToDevice, c->stream));
+  c->hist_len = 0;
+  return CG_OK;
+}
+
+int cartogram_profile(cg_ctx* c, int reps, double* ms_out) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!c->have_spectrum) return fail(c, CG_ESTATE, "no spectrum: run an integration first");
+  if (reps < 1 || !ms_out) return fail(c, CG_EINVAL, "bad profile arguments");
+  return c->mixed ? do_profile<float>(c, reps, ms_out) : do_profile<double>(c, reps, ms_out);
+}
+
+int cartogram_history_length(const cg_ctx* c) { return c ? c->hist_len : 0; }
+
+int cartogram_get_grid(cg_ctx* c, int k, double* xy_out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (k < 0 || k >= c->hist_len || !xy_out) return fail(c, CG_EINVAL, "history entry %d out of range", k);
+  return c->mixed ? grid_out<float>(c, c->hist[k], xy_out) : grid_out<double>(c, c->hist[k], xy_out);
+}
+
+int cartogram_density(cg_ctx* c, double* rho_out) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!rho_out) return fail(c, CG_EINVAL, "NULL output");
+  if ((r = run_areas(c)) || (r = run_raster(c))) return r;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  std::vector<double> h(N);
+  CG_CUDA(c, cudaMemcpyAsync(h.data(), c->acc, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (double& v : h) v += 1.0;
+  CG_CUDA(c, cudaMemcpy(rho_out, h.data(), sizeof(double) * N, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+int cartogram_spectrum(cg_ctx* c, double* spec_out) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if ((r = run_areas(c)) || (r = run_raster(c))) return r;
+  r = c->mixed ? run_forward<float>(c) : run_forward<double>(c);
+  if (r) return r;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (spec_out) {
+    const size_t N = (size_t)c->Lx * c->Ly;
+    std::vector<double> h(N);
+    CG_CUDA(c, cudaMemcpy(h.data(), c->spec64, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    h[0] = (double)c->Lx * c->Ly;
+    CG_CUDA(c, cudaMemcpy(spec_out, h.data(), sizeof(double) * N, cudaMemcpyDefault));
+  }
+  return CG_OK;
+}
+
+int cartogram_velocity(cg_ctx* c, double t, double* rho_out, double* v_out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (!c->have_spectrum) return fail(c, CG_ESTATE, "no spectrum: call cartogram_spectrum first");
+  if (!is_finite(t) || t < 0.0) return fail(c, CG_EINVAL, "bad time %g", t);
+  return c->mixed ? do_velocity<float>(c, t, rho_out, v_out) : do_velocity<double>(c, t, rho_out, v_out);
+}
+
+int cartogram_heun_step(cg_ctx* c, double t, double h, const double* disp_in, double* disp_out,
+                        double* err) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (!c->have_spectrum) return fail(c, CG_ESTATE, "no spectrum: call cartogram_spectrum first");
+  if (!is_finite(t) || t < 0.0 || !is_finite(h) || !(h > 0.0) || !disp_in || !disp_out)
+    return fail(c, CG_EINVAL, "bad step arguments");
+  return c->mixed ? do_heun<float>(c, t, h, disp_in, disp_out, err)
+                  : do_heun<double>(c, t, h, disp_in, disp_out, err);
+}
+
+int cartogram_integrate_once(cg_ctx* c, double* grid_out, long long* accepted, long long* rejected,
+                             double* t_end) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (!c->have_spectrum) return fail(c, CG_ESTATE, "no spectrum: call cartogram_spectrum first");
+  return c->mixed ? do_integrate_once<float>(c, grid_out, accepted, rejected, t_end)
+                  : do_integrate_once<double>(c, grid_out, accepted, rejected, t_end);
+}
+
+const char* cartogram_last_error(const cg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+void cartogram_destroy(cg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  free_regions(c);
+  void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
+                c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
+                c->dres, c->rho_tmp, c->st, c->info, c->pts};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (c->specT && c->specT != c->spec64) cudaFree(c->specT);
+  for (void* p : c->hist) cudaFree(p);
+  if (c->info_h) cudaFreeHost(c->info_h);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Shared device helpers of the cartogram kernels: complex arithmetic on float2 /
+// double2, order-preserving atomic max of non-negative values, block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cg {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using V2 = typename vec2<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ V2<T> mk2(T x, T y) {
+  V2<T> r; r.x = x; r.y = y; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Device-resident state of one integration (written by the step controller).
+struct DevState {
+  double t;          // accepted diffusion time
+  double h;          // step to attempt next (already capped)
+  double vmax;       // max |v| of the field at t
+  long long accepted;
+  long long rejected;
+  int parity;        // current buffers: v[parity], disp[parity]
+  int status;        // kRunning, kDone, or a negative error code
+  // reductions of the attempt in flight (bit patterns of non-negative doubles)
+  unsigned long long err2_bits;   // max ||r_corr - r_pred||^2
+  unsigned long long vmax2_bits;  // max |v|^2 of the new field
+  unsigned long long dev_bits;    // max |rho/rho_bar - 1| of the new field
+  unsigned int ticket;            // blocks of the step kernel that have finished
+  int bad;                        // a field had a non-positive or non-finite density
+  unsigned int body_iters;        // step-loop iterations started (termination guard)
+  unsigned int pad;
+};
+// What a field or step kernel works on: the field at t (start of an integration),
+// the attempt at t + h inside the step loop, or explicit buffers and times.
+enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2 };
+
+constexpr int kRunning = 0;
+constexpr int kDone = 1;
+constexpr int kStepFail = -6;
+
+// Per-iteration results read back by the host in one copy.
+struct IterInfo {
+  double max_err;       // max_i |A_i / A^_i - 1|
+  double t_end;         // diffusion time reached by the integration
+  long long accepted;
+  long long rejected;
+  int status;           // DevState status after the integration
+  int pad;
+};
+
+// Step-control constants passed by value to the kernels that need them.
+struct StepParams {
+  double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
+  long long max_steps;
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Max over the block; the result is valid in thread 0. `red` holds >= 32 values.
+template <typename T> __device__ __forceinline__ T block_max(T v, T* red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? red[lane] : T(0);
+    v = warp_max(v);
+  }
+  return v;
+}
+
+}  // namespace cg

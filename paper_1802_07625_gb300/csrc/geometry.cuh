@@ -1,0 +1,218 @@
+// Geometry kernels: exact-coverage rasterisation of the regions, ring and region
+// areas with the relative area errors, and mapping points through a projected grid.
+#pragma once
+
+#include "common.cuh"
+
+namespace cg {
+
+// ---------------------------------------------------------------------------
+// Rasterisation: rho'[j][i] = sum_regions w_r * area(region_r intersect cell_ij),
+// w_r = (V_r / A_r) / (sum V / sum A) - 1 (the density relative to the map mean,
+// minus one; the margin of the box, covered by no region, gets 0).
+//
+// A ring's coverage of cell (i, j) is sum over its edges of -dy * clamp(i+1 - x(y), 0, 1)
+// integrated along the edge (the winding number of a leftward ray). Every edge is cut
+// at the grid lines into pieces inside one cell; a piece in cell (i, j) with vertical
+// extent dy and mean abscissa x_m adds -w dy (i+1 - x_m) to D[j][i] and -w dy (x_m - i)
+// to D[j][i+1]; the prefix sum of D along each row is the coverage-weighted density.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void raster_piece(double ax, double ay, double bx, double by, double wt,
+                                             double* __restrict__ acc, int Lx, int Ly) {
+  const double pdy = by - ay;
+  if (pdy == 0.0) return;
+  const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
+  const int j = (int)floor(my);
+  if (j < 0 || j >= Ly) return;
+  const int i = (int)floor(mx);
+  const double c = -wt * pdy;
+  double* row = acc + (size_t)j * Lx;
+  if (i < 0) {
+    atomicAdd(row, c);
+  } else if (i < Lx) {
+    atomicAdd(row + i, c * ((double)(i + 1) - mx));
+    if (i + 1 < Lx) atomicAdd(row + i + 1, c * (mx - (double)i));
+  }
+}
+
+__global__ void raster_edges_kernel(const double2* __restrict__ xy, const int* __restrict__ next,
+                                    const int* __restrict__ vreg, const double* __restrict__ w,
+                                    double* __restrict__ acc, int Lx, int Ly, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double wt = w[vreg[v]];
+    const double2 P = xy[v], Q = xy[next[v]];
+    const double dx = Q.x - P.x, dy = Q.y - P.y;
+    if (wt == 0.0 || dy == 0.0) continue;
+    // next grid line crossed along x and along y, as edge parameters in (0, 1]
+    double gx = 0.0, gy = 0.0, sx = 2.0, sy = 2.0;
+    const double stx = dx > 0.0 ? 1.0 : -1.0, sty = dy > 0.0 ? 1.0 : -1.0;
+    if (dx != 0.0) {
+      gx = dx > 0.0 ? floor(P.x) + 1.0 : ceil(P.x) - 1.0;
+      sx = (gx - P.x) / dx;
+    }
+    gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
+    sy = (gy - P.y) / dy;
+    double ax = P.x, ay = P.y;
+    const int guard = Lx + Ly + 4;
+    for (int it = 0; it < guard; ++it) {
+      const double s1 = fmin(fmin(sx, sy), 1.0);
+      double bx, by;
+      if (s1 >= 1.0) {
+        bx = Q.x;
+        by = Q.y;
+      } else {
+        bx = P.x + s1 * dx;
+        by = P.y + s1 * dy;
+      }
+      raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly);
+      if (s1 >= 1.0) break;
+      if (sx <= s1) {
+        gx += stx;
+        sx = (gx - P.x) / dx;
+      }
+      if (sy <= s1) {
+        gy += sty;
+        sy = (gy - P.y) / dy;
+      }
+      ax = bx;
+      ay = by;
+    }
+  }
+}
+
+// In-place inclusive prefix sum of every row (one block per row, deterministic order).
+__global__ void row_scan_kernel(double* __restrict__ acc, int Lx) {
+  __shared__ double wsum[32];
+  double* row = acc + (size_t)blockIdx.x * Lx;
+  const int nt = blockDim.x;
+  const int chunk = Lx / nt;  // Lx is a multiple of blockDim.x
+  const int b = threadIdx.x * chunk;
+  double s = 0.0;
+  for (int k = 0; k < chunk; ++k) s += row[b + k];
+  // exclusive scan of the chunk sums across the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31 || threadIdx.x == nt - 1) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (nt + 31) >> 5;
+    double v = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (lane < nw) wsum[lane] = v;
+  }
+  __syncthreads();
+  double run = incl - s + (warp > 0 ? wsum[warp - 1] : 0.0);
+  for (int k = 0; k < chunk; ++k) {
+    run += row[b + k];
+    row[b + k] = run;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Areas: shoelace formula per ring (relative to the ring's first vertex), one warp
+// per ring; then per region the signed sum over its rings, the relative errors
+// err_r = A_r / A^_r - 1 with A^_r = V_r sum(A) / sum(V), and the rasterisation
+// weights w_r = A^_r / A_r - 1. One block.
+// ---------------------------------------------------------------------------
+__global__ void ring_area_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
+                                 double* __restrict__ ring_area, long long n_rings) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rings) return;
+  const long long a = off[r], b = off[r + 1];
+  const double2 o = xy[a];
+  double s = 0.0;
+  for (long long k = a + lane; k < b; k += 32) {
+    const double2 p = xy[k];
+    const double2 q = xy[k + 1 < b ? k + 1 : a];
+    s += (p.x - o.x) * (q.y - o.y) - (q.x - o.x) * (p.y - o.y);
+  }
+  s = warp_sum(s);
+  if (lane == 0) ring_area[r] = 0.5 * s;
+}
+
+__device__ __forceinline__ double block_sum_det(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = lane < nw ? red[lane] : 0.0;
+  t = warp_sum(t);  // every warp computes the same total in the same order
+  return t;
+}
+
+__global__ void region_kernel(const double* __restrict__ ring_area, const int* __restrict__ reg_off,
+                              const int* __restrict__ reg_rings, const double* __restrict__ values,
+                              int R, double* __restrict__ area, double* __restrict__ err,
+                              double* __restrict__ w, IterInfo* info) {
+  __shared__ double red[32];
+  double sa = 0.0, sv = 0.0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double A = 0.0;
+    for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) A += ring_area[reg_rings[k]];
+    area[r] = A;
+    sa += A;
+    sv += values[r];
+  }
+  sa = block_sum_det(sa, red);
+  sv = block_sum_det(sv, red);
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double target = values[r] * sa / sv;
+    const double A = area[r];
+    const double e = A / target - 1.0;
+    err[r] = e;
+    w[r] = target / A - 1.0;
+    mx = fmax(mx, fabs(e));
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) info->max_err = mx;
+}
+
+// Copy the integration's outcome into the per-iteration record.
+__global__ void collect_kernel(const DevState* st, IterInfo* info) {
+  info->t_end = st->t;
+  info->accepted = st->accepted;
+  info->rejected = st->rejected;
+  info->status = st->status;
+}
+
+// ---------------------------------------------------------------------------
+// Points through a projected grid: T(p) = p + bilinear interpolation of the grid
+// points' displacements over the quad of cell centres containing p (the nearest quad
+// is extended linearly in the half-cell band along the walls). Equal to bilinear
+// interpolation of the projected positions, since bilinear interpolation of the cell
+// centres themselves reproduces p.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void map_points_kernel(const double2* in, double2* out, long long n,
+                                  const V2<T>* __restrict__ disp, int Lx, int Ly) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double2 q = in[p];
+    const double u = q.x - 0.5, v = q.y - 0.5;
+    int i0 = (int)floor(u), j0 = (int)floor(v);
+    i0 = i0 < 0 ? 0 : (i0 > Lx - 2 ? Lx - 2 : i0);
+    j0 = j0 < 0 ? 0 : (j0 > Ly - 2 ? Ly - 2 : j0);
+    const double fx = u - i0, fy = v - j0;
+    const size_t k = (size_t)j0 * Lx + i0;
+    const V2<T> a = disp[k], b = disp[k + 1], c = disp[k + Lx], d = disp[k + Lx + 1];
+    const double gx = 1.0 - fx, gy = 1.0 - fy;
+    const double dx = gy * (gx * (double)a.x + fx * (double)b.x) + fy * (gx * (double)c.x + fx * (double)d.x);
+    const double dy = gy * (gx * (double)a.y + fx * (double)b.y) + fy * (gx * (double)c.y + fx * (double)d.y);
+    out[p] = make_double2(q.x + dx, q.y + dy);
+  }
+}
+
+}  // namespace cg

@@ -1,0 +1,120 @@
+// Host-side launchers of the cartogram kernels (defined in spectral_*.cu, step.cu,
+// geometry.cu). All launches are asynchronous on the given stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace cg {
+
+struct LaunchCfg {
+  int per_block;  // lines (rows or columns) per block
+  int threads;
+  size_t smem;
+  int grid;
+};
+
+inline int fft_n1(int log2n) { return 1 << ((log2n + 1) / 2); }
+inline int fft_stride(int log2n) {
+  const int N = 1 << log2n;
+  return N + N / fft_n1(log2n);
+}
+
+// pass 1 of the inverse transform: S spectral rows per block
+inline LaunchCfg inv_rows_cfg(int log2Lx, int Ly, size_t esz) {
+  const int N = 1 << log2Lx, N1 = fft_n1(log2Lx);
+  int S = 128 / N1;
+  if (S < 1) S = 1;
+  if (S > Ly) S = Ly;
+  LaunchCfg c;
+  c.per_block = S;
+  c.threads = S * N1;
+  c.smem = (size_t)N * 2 * esz + (size_t)S * fft_stride(log2Lx) * 2 * esz + (size_t)(N + S) * esz;
+  c.grid = Ly / S;
+  return c;
+}
+
+// pass 2 of the inverse transform: Wc columns per block
+inline LaunchCfg inv_cols_cfg(int log2Ly, int Lx, size_t esz) {
+  const int N = 1 << log2Ly, N1 = fft_n1(log2Ly);
+  int Wc = (esz == 4 && Lx >= 1024) ? 4 : 2;
+  if (Wc > Lx) Wc = Lx;
+  const int S = Wc + Wc / 2;
+  LaunchCfg c;
+  c.per_block = Wc;
+  c.threads = S * N1;
+  c.smem = (size_t)N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz + 64 * esz;
+  c.grid = Lx / Wc;
+  return c;
+}
+
+// forward transform, rows (pairs of rows per complex signal)
+inline LaunchCfg fwd_rows_cfg(int log2Lx, int Ly) {
+  const int N = 1 << log2Lx, N1 = fft_n1(log2Lx);
+  int S = 2 * (128 / N1);
+  if (S < 2) S = 2;
+  if (S > Ly) S = Ly;
+  LaunchCfg c;
+  c.per_block = S;
+  c.threads = (S / 2) * N1;
+  c.smem = (size_t)N * 16 + (size_t)(S / 2) * fft_stride(log2Lx) * 16;
+  c.grid = Ly / S;
+  return c;
+}
+
+// forward transform, columns (pairs of columns per complex signal)
+inline LaunchCfg fwd_cols_cfg(int log2Ly, int Lx) {
+  const int N = 1 << log2Ly, N1 = fft_n1(log2Ly);
+  int Wc = 4;
+  if (Wc > Lx) Wc = Lx;
+  LaunchCfg c;
+  c.per_block = Wc;
+  c.threads = (Wc / 2) * N1;
+  c.smem = (size_t)N * 16 + (size_t)(Wc / 2) * fft_stride(log2Ly) * 16;
+  c.grid = Lx / Wc;
+  return c;
+}
+
+// Allow the dynamic shared memory the spectral kernels of this grid need.
+template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);
+cudaError_t prepare_forward(int log2Lx, int log2Ly);
+
+template <typename T>
+void launch_inv_rows(int log2Lx, int Ly, const T* spec, V2<T>* AB, const V2<T>* W, const V2<T>* E,
+                     DevState* st, int mode, double tau, cudaGraphConditionalHandle handle,
+                     int use_cond, unsigned int max_body, cudaStream_t s);
+template <typename T>
+void launch_inv_cols(int log2Ly, int Lx, const V2<T>* AB, V2<T>* v0, V2<T>* v1, T* rho_out,
+                     const V2<T>* W, const V2<T>* E, DevState* st, int mode, cudaStream_t s);
+void launch_fwd_rows(int log2Lx, int log2Ly, const double* rho, double* R, const double2* Wx,
+                     const double2* Ex, cudaStream_t s);
+template <typename T>
+void launch_fwd(int log2Lx, int log2Ly, const double* rho, double* R, double* spec64, T* specT,
+                const double2* Wx, const double2* Ex, const double2* Wy, const double2* Ey,
+                const double* bx, const double* by, cudaStream_t s);
+
+template <typename T>
+void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
+                 V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
+                 int use_cond, cudaStream_t s);
+void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s);
+void launch_init_finish(DevState* st, const StepParams& sp, cudaGraphConditionalHandle handle,
+                        int use_cond, cudaStream_t s);
+template <typename T>
+void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>* dst, int N,
+                     cudaStream_t s);
+template <typename T>
+void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,
+                       int Ly, cudaStream_t s);
+
+void launch_raster(const double2* xy, const int* next, const int* vreg, const double* w,
+                   double* acc, int Lx, int Ly, int n_vert, cudaStream_t s);
+void launch_areas(const double2* xy, const long long* ring_off, double* ring_area,
+                  long long n_rings, const int* reg_off, const int* reg_rings,
+                  const double* values, int R, double* area, double* err, double* w,
+                  IterInfo* info, cudaStream_t s);
+void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s);
+
+}  // namespace cg

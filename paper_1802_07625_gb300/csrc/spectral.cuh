@@ -1,0 +1,293 @@
+// Spectral kernels of the diffusion flow.
+//
+// Forward: the cosine transform of the normalised, mean-subtracted density with the
+// blur factor (main text Eq. rhotilde_mn; SI Eq. rhoxyt's coefficients), computed as
+// a DCT-II along x then along y, each through one complex FFT per pair of real lines.
+//
+// Inverse (every attempted step): SI Eq. rhoxyt with f_mn = exp(-pi^2 (m^2/Lx^2 +
+// n^2/Ly^2) t) (Eq. fmn_diff, D = 1) and its x and y derivatives. The damping is
+// separable, exp(-pi^2 m^2 t/Lx^2) exp(-pi^2 n^2 t/Ly^2), so each block evaluates
+// Lx + (rows) exponentials instead of one per coefficient.
+//   pass 1 (rows n, along x):  A[n][i] = sum_m a_nm cos(pi m x_i/Lx)
+//                              B[n][i] = sum_m a_nm (-pi m/Lx) sin(pi m x_i/Lx)
+//   pass 2 (columns i, along y): rho' = sum_n A cos,  d_y rho = sum_n A (-pi n/Ly) sin,
+//                              d_x rho = sum_n B cos;  v = -grad rho / (1 + rho')
+// A length-N cosine sum y_i = sum_m c_m cos(pi m (i+1/2)/N) is one complex inverse DFT
+// of U_m = e^{i pi m/(2N)} (c_m - i c_{N-m})/2 (U_0 = c_0) read back in the order
+// y_{2k} = u_k, y_{2k+1} = u_{N-1-k}; a sine sum is the cosine sum of the reversed
+// coefficients times (-1)^i. Two real sums share one complex DFT (real and imaginary
+// parts).
+#pragma once
+
+#include "fft.cuh"
+
+namespace cg {
+
+__device__ __forceinline__ float texp(float x) { return expf(x); }
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+
+// Output index i of a cosine sum -> index of the complex DFT output that holds it.
+__device__ __forceinline__ int dct3_src(int i, int N) { return (i & 1) ? (N - 1 - (i >> 1)) : (i >> 1); }
+
+// ---------------------------------------------------------------------------
+// pass 1: damped spectrum rows -> (A, B) rows.  blockDim = S * N1, grid = Ly / S.
+// shared: W[N] (C), buf[S*STRIDE] (C), fx[N] (T), fy[S] (T)
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ AB,
+                                const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+                                int Ly, int S, DevState* st, int mode, double tau_fixed,
+                                cudaGraphConditionalHandle handle, int use_cond,
+                                unsigned int max_body) {
+  using C = V2<T>;
+  using F = FFTShape<LOG2N>;
+  constexpr int N = F::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* W = reinterpret_cast<C*>(smem_raw);
+  C* buf = W + N;
+  T* fx = reinterpret_cast<T*>(buf + S * F::STRIDE);
+  T* fyS = fx + N;
+
+  double tau = tau_fixed;
+  if (mode == kModeStep && blockIdx.x == 0 && threadIdx.x == 0) {
+    // first kernel of a loop iteration: end the loop if the integration is over or
+    // has run more iterations than the controller allows
+    const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
+    if (st->status == kRunning && it > max_body) st->status = kStepFail;
+    if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+  }
+  if (mode != kModeFixed) {
+    if (st->status != kRunning) return;
+    tau = (mode == kModeInit) ? st->t : st->t + st->h;
+  }
+  const int n0 = blockIdx.x * S;
+  const T kx = (T)(kPi * kPi * tau / ((double)N * N));
+  const T ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    W[i] = Wg[i];
+    fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
+  }
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const T n = (T)(n0 + s);
+    fyS[s] = texp(-ky * n * n) / (T)Ly;
+  }
+  __syncthreads();
+
+  const T kd = (T)(kPi / N);
+  const int P = N / 2 + 1;
+  for (int task = threadIdx.x; task < S * P; task += blockDim.x) {
+    const int s = task / P, m = task - s * P;
+    const T* row = spec + (size_t)(n0 + s) * N;
+    C* x = buf + s * F::STRIDE;
+    const T f = fyS[s];
+    const T am = row[m] * fx[m] * f;
+    if (m == 0) {
+      x[F::pidx(0)] = mk2<T>(am, T(0));
+      continue;
+    }
+    const T bm = -kd * (T)m * am;
+    const int q = N - m;
+    const T aq = row[q] * fx[q] * f;
+    const T bq = -kd * (T)q * aq;
+    x[F::pidx(m)] = cmul(Eg[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
+    if (q != m) x[F::pidx(q)] = cmul(Eg[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+  }
+  __syncthreads();
+  block_fft<T, LOG2N>(buf, S, W);
+  for (int task = threadIdx.x; task < S * N; task += blockDim.x) {
+    const int s = task >> LOG2N, i = task & (N - 1);
+    const C u = buf[s * F::STRIDE + F::out_slot(dct3_src(i, N))];
+    AB[(size_t)(n0 + s) * N + i] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: (A, B) columns -> velocity. Wc columns per block (even): Wc signals for
+// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs.
+// blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc.
+// shared: W[N] (C), buf[(Wc + Wc/2) * STRIDE] (C), red[64] (T)
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__global__ void inv_cols_kernel(const V2<T>* __restrict__ AB, V2<T>* vbuf0, V2<T>* vbuf1,
+                                T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
+                                const V2<T>* __restrict__ Eg, int Lx, int Wc, DevState* st,
+                                int mode) {
+  using C = V2<T>;
+  using F = FFTShape<LOG2N>;
+  constexpr int N = F::N;  // = Ly
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* W = reinterpret_cast<C*>(smem_raw);
+  C* buf = W + N;
+  T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::STRIDE);
+
+  if (mode != kModeFixed && st->status != kRunning) return;
+  V2<T>* out = vbuf0;
+  if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
+  else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
+  const int c0 = blockIdx.x * Wc;
+  const int Wp = Wc / 2;
+  const int P = N / 2 + 1;
+  const T kd = (T)(kPi / N);
+  for (int task = threadIdx.x; task < P * Wp; task += blockDim.x) {
+    const int m = task / Wp, p = task - m * Wp;
+    const int c = c0 + 2 * p;
+    const C Am0 = AB[(size_t)m * Lx + c], Am1 = AB[(size_t)m * Lx + c + 1];
+    C* x0 = buf + (2 * p) * F::STRIDE;
+    C* x1 = buf + (2 * p + 1) * F::STRIDE;
+    C* x2 = buf + (Wc + p) * F::STRIDE;
+    if (m == 0) {
+      x0[F::pidx(0)] = mk2<T>(Am0.x, T(0));
+      x1[F::pidx(0)] = mk2<T>(Am1.x, T(0));
+      x2[F::pidx(0)] = mk2<T>(Am0.y, Am1.y);
+      continue;
+    }
+    const int q = N - m;
+    const C Aq0 = AB[(size_t)q * Lx + c], Aq1 = AB[(size_t)q * Lx + c + 1];
+    const C em = Eg[m], eq = Eg[q];
+    {  // (rho', d_y rho) of column c
+      const T am = Am0.x, aq = Aq0.x, bm = -kd * (T)m * am, bq = -kd * (T)q * aq;
+      x0[F::pidx(m)] = cmul(em, mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
+      if (q != m) x0[F::pidx(q)] = cmul(eq, mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+    }
+    {  // (rho', d_y rho) of column c + 1
+      const T am = Am1.x, aq = Aq1.x, bm = -kd * (T)m * am, bq = -kd * (T)q * aq;
+      x1[F::pidx(m)] = cmul(em, mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
+      if (q != m) x1[F::pidx(q)] = cmul(eq, mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+    }
+    {  // d_x rho of columns c (real part) and c + 1 (imaginary part)
+      const T bem = Am0.y, gam = Am1.y, beq = Aq0.y, gaq = Aq1.y;
+      x2[F::pidx(m)] = cmul(em, mk2<T>((bem + gaq) * T(0.5), (gam - beq) * T(0.5)));
+      if (q != m) x2[F::pidx(q)] = cmul(eq, mk2<T>((beq + gam) * T(0.5), (gaq - bem) * T(0.5)));
+    }
+  }
+  __syncthreads();
+  block_fft<T, LOG2N>(buf, Wc + Wp, W);
+
+  T dev = T(0), v2max = T(0);
+  bool bad = false;
+  for (int task = threadIdx.x; task < N * Wc; task += blockDim.x) {
+    const int j = task / Wc, cc = task - j * Wc;
+    const int slot = F::out_slot(dct3_src(j, N));
+    const C u1 = buf[cc * F::STRIDE + slot];
+    const C u2 = buf[(Wc + (cc >> 1)) * F::STRIDE + slot];
+    const T rp = u1.x;
+    const T gy = (j & 1) ? -u1.y : u1.y;
+    const T gx = (cc & 1) ? u2.y : u2.x;
+    const T rho = T(1) + rp;
+    bad |= !(rho > T(0));
+    const T inv = T(1) / rho;
+    const T vx = -gx * inv, vy = -gy * inv;
+    const size_t o = (size_t)j * Lx + c0 + cc;
+    out[o] = mk2<T>(vx, vy);
+    if (rho_out) rho_out[o] = rho;
+    dev = max(dev, fabs(rp));
+    v2max = max(v2max, vx * vx + vy * vy);
+  }
+  bad = __syncthreads_or(bad);
+  dev = block_max(dev, red);
+  v2max = block_max(v2max, red + 32);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&st->dev_bits, (double)dev);
+    atomic_max_nonneg(&st->vmax2_bits, (double)v2max);
+    if (bad) st->bad = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward pass 1: DCT-II along x of row pairs. S rows per block (even),
+// blockDim = (S/2) * N1, grid = Ly / S. R[j][m] = sum_i rho[j][i] cos(pi m x_i/Lx).
+// shared: W[N] (C, forward roots), buf[(S/2) * STRIDE] (C)
+// ---------------------------------------------------------------------------
+template <int LOG2N>
+__global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restrict__ R,
+                                const double2* __restrict__ Wg, const double2* __restrict__ Eg,
+                                int S) {
+  using C = double2;
+  using F = FFTShape<LOG2N>;
+  constexpr int N = F::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* W = reinterpret_cast<C*>(smem_raw);
+  C* buf = W + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
+  const int r0 = blockIdx.x * S;
+  const int S2 = S / 2;
+  for (int task = threadIdx.x; task < S2 * (N / 2); task += blockDim.x) {
+    const int s = task / (N / 2), k = task - s * (N / 2);
+    const double2 e = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s) * N + 2 * k);
+    const double2 o = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s + 1) * N + 2 * k);
+    C* x = buf + s * F::STRIDE;
+    x[F::pidx(k)] = mk2<double>(e.x, o.x);
+    x[F::pidx(N - 1 - k)] = mk2<double>(e.y, o.y);
+  }
+  __syncthreads();
+  block_fft<double, LOG2N>(buf, S2, W);
+  for (int task = threadIdx.x; task < S2 * N; task += blockDim.x) {
+    const int s = task >> LOG2N, m = task & (N - 1);
+    const C* x = buf + s * F::STRIDE;
+    const C Vm = x[F::out_slot(m)];
+    const C Vq = x[F::out_slot((N - m) & (N - 1))];
+    const C em = Eg[m];
+    // V1 = (Vm + conj Vq)/2, V2 = (Vm - conj Vq)/(2i); X = Re(conj(e) V)
+    const C V1 = mk2<double>(0.5 * (Vm.x + Vq.x), 0.5 * (Vm.y - Vq.y));
+    const C V2 = mk2<double>(0.5 * (Vm.y + Vq.y), -0.5 * (Vm.x - Vq.x));
+    R[(size_t)(r0 + 2 * s) * N + m] = em.x * V1.x + em.y * V1.y;
+    R[(size_t)(r0 + 2 * s + 1) * N + m] = em.x * V2.x + em.y * V2.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward pass 2: DCT-II along y of column pairs, times the coefficient weights
+// 4/((1+d_m0)(1+d_n0)) and the separable blur factors; the (0,0) coefficient (the
+// mean, which the velocity handles separately) is set to zero.
+// Wc columns per block (even), blockDim = (Wc/2) * N1, grid = Lx / Wc.
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict__ spec64,
+                                T* __restrict__ specT, const double2* __restrict__ Wg,
+                                const double2* __restrict__ Eg, const double* __restrict__ bx,
+                                const double* __restrict__ by, int Lx, int Wc) {
+  using C = double2;
+  using F = FFTShape<LOG2N>;
+  constexpr int N = F::N;  // = Ly
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* W = reinterpret_cast<C*>(smem_raw);
+  C* buf = W + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
+  const int c0 = blockIdx.x * Wc;
+  const int Wp = Wc / 2;
+  for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
+    const int k = task / Wp, p = task - k * Wp;
+    const double2 e = *reinterpret_cast<const double2*>(R + (size_t)(2 * k) * Lx + c0 + 2 * p);
+    const double2 o = *reinterpret_cast<const double2*>(R + (size_t)(2 * k + 1) * Lx + c0 + 2 * p);
+    C* x = buf + p * F::STRIDE;
+    x[F::pidx(k)] = e;
+    x[F::pidx(N - 1 - k)] = o;
+  }
+  __syncthreads();
+  block_fft<double, LOG2N>(buf, Wp, W);
+  for (int task = threadIdx.x; task < N * Wp; task += blockDim.x) {
+    const int n = task / Wp, p = task - n * Wp;
+    const C* x = buf + p * F::STRIDE;
+    const C Vn = x[F::out_slot(n)];
+    const C Vq = x[F::out_slot((N - n) & (N - 1))];
+    const C en = Eg[n];
+    const C V1 = mk2<double>(0.5 * (Vn.x + Vq.x), 0.5 * (Vn.y - Vq.y));
+    const C V2 = mk2<double>(0.5 * (Vn.y + Vq.y), -0.5 * (Vn.x - Vq.x));
+    const int m = c0 + 2 * p;
+    const double wn = (n == 0 ? 1.0 : 2.0) * by[n];
+    double s0 = (en.x * V1.x + en.y * V1.y) * wn * (m == 0 ? 1.0 : 2.0) * bx[m];
+    double s1 = (en.x * V2.x + en.y * V2.y) * wn * 2.0 * bx[m + 1];
+    if (m == 0 && n == 0) s0 = 0.0;
+    const size_t o = (size_t)n * Lx + m;
+    spec64[o] = s0;
+    spec64[o + 1] = s1;
+    if (specT) {
+      specT[o] = (T)s0;
+      specT[o + 1] = (T)s1;
+    }
+  }
+}
+
+}  // namespace cg

@@ -1,0 +1,81 @@
+// Instantiation of the advection, step-control and geometry kernels.
+#include "advect.cuh"
+#include "geometry.cuh"
+#include "kernels.h"
+
+namespace cg {
+
+static inline int blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+template <typename T>
+void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
+                 V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
+                 int use_cond, cudaStream_t s) {
+  int log2Lx = 0;
+  while ((1 << log2Lx) < Lx) ++log2Lx;
+  const int N = Lx * Ly;
+  heun_kernel<T><<<blocks_for(N, 256, 1 << 20), 256, 0, s>>>(st, sp, v0, v1, d0, d1, Lx, Ly, log2Lx,
+                                                             mode, h, handle, use_cond);
+}
+
+void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st, sp);
+}
+
+void launch_init_finish(DevState* st, const StepParams& sp, cudaGraphConditionalHandle handle,
+                        int use_cond, cudaStream_t s) {
+  init_finish_kernel<<<1, 1, 0, s>>>(st, sp, handle, use_cond);
+}
+
+template <typename T>
+void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>* dst, int N,
+                     cudaStream_t s) {
+  snapshot_kernel<T><<<blocks_for(N, 256, 4096), 256, 0, s>>>(st, d0, d1, dst, N);
+}
+
+template <typename T>
+void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,
+                       int Ly, cudaStream_t s) {
+  if (n <= 0) return;
+  map_points_kernel<T><<<blocks_for(n, 256, 1 << 16), 256, 0, s>>>(in, out, n, disp, Lx, Ly);
+}
+
+void launch_raster(const double2* xy, const int* next, const int* vreg, const double* w,
+                   double* acc, int Lx, int Ly, int n_vert, cudaStream_t s) {
+  if (n_vert > 0)
+    raster_edges_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy, next, vreg, w, acc, Lx,
+                                                                          Ly, n_vert);
+  const int t = Lx < 256 ? Lx : 256;
+  row_scan_kernel<<<Ly, t, 0, s>>>(acc, Lx);
+}
+
+void launch_areas(const double2* xy, const long long* ring_off, double* ring_area,
+                  long long n_rings, const int* reg_off, const int* reg_rings,
+                  const double* values, int R, double* area, double* err, double* w,
+                  IterInfo* info, cudaStream_t s) {
+  ring_area_kernel<<<blocks_for(n_rings * 32, 256, 1 << 20), 256, 0, s>>>(xy, ring_off, ring_area,
+                                                                          n_rings);
+  region_kernel<<<1, 1024, 0, s>>>(ring_area, reg_off, reg_rings, values, R, area, err, w, info);
+}
+
+void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s) {
+  collect_kernel<<<1, 1, 0, s>>>(st, info);
+}
+
+#define CG_INSTANTIATE_STEP(T)                                                                      \
+  template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
+                               V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int,      \
+                               cudaStream_t);                                                       \
+  template void launch_snapshot<T>(const DevState*, const V2<T>*, const V2<T>*, V2<T>*, int,        \
+                                   cudaStream_t);                                                   \
+  template void launch_map_points<T>(const double2*, double2*, long long, const V2<T>*, int, int,   \
+                                     cudaStream_t);
+CG_INSTANTIATE_STEP(float)
+CG_INSTANTIATE_STEP(double)
+
+}  // namespace cg

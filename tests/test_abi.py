@@ -1,0 +1,69 @@
+"""Host-side checks that need no GPU: the C-ABI library builds, loads and exports every
+entry point that include/cartogram.h declares, and the Python binding covers them."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cartogram.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cartogram_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_method_calls():
+    names = _declared()
+    for n in ("cartogram_init", "cartogram_set_regions", "cartogram_integrate", "cartogram_project",
+              "cartogram_area_errors", "cartogram_destroy", "cartogram_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+
+    import paper_1802_07625_gb300 as P
+    P.load()
+    lib = ctypes.CDLL(P.library_path())
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_has_a_function_per_entry_point():
+    import paper_1802_07625_gb300 as P
+    for n in _declared():
+        assert callable(getattr(P, n)), n
+
+
+def test_default_options_without_gpu():
+    import paper_1802_07625_gb300 as P
+    o = P.cartogram_default_options()
+    assert o.precision == P.CG_PRECISION_FP64
+    assert o.dt0 == 1e-2 and o.atol == 1e-2 and o.grow == 1.2 and o.shrink == 0.5
+    assert o.cfl == 1.0 and o.rho_tol == 1e-4 and o.area_tol == 0.01
+    assert o.max_steps == 4000 and o.max_iter == 50 and o.use_graph == 1
+
+
+def test_init_rejects_bad_sizes_before_touching_the_gpu():
+    import paper_1802_07625_gb300 as P
+    for Lx, Ly in ((0, 64), (64, 48), (2048, 64), (4, 4)):
+        with pytest.raises(P.CartogramError) as e:
+            P.cartogram_init(Lx, Ly, 1.0)
+        assert e.value.code == P.CG_EINVAL
+    with pytest.raises(P.CartogramError) as e:
+        P.cartogram_init(64, 64, -1.0)
+    assert e.value.code == P.CG_EINVAL
+
+
+def test_oracle_and_library_share_no_source():
+    # the oracle is independent of the CUDA path: no include, import or file in common
+    orc = open(os.path.join(ROOT, "oracle", "cartogram_oracle.c")).read()
+    assert "#include \"" not in orc
+    csrc = os.path.join(ROOT, "paper_1802_07625_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "oracle" not in open(os.path.join(csrc, f)).read().lower(), f
+    for f in ("__init__.py", "build.py", "synth.py"):
+        txt = open(os.path.join(ROOT, "paper_1802_07625_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt, f

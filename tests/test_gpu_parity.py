@@ -1,0 +1,258 @@
+"""GPU path vs the FP64 CPU oracle, element by element, through the C-ABI.
+
+Tolerances:
+  FP64 path   1e-9 grid units on positions (the accuracy target of the method's
+              FP64 implementation); fields 1e-10 relative to their scale.
+  mixed path  1e-3 grid units on positions; fields 2e-5 relative (FP32 transforms
+              of length <= 1024 accumulate ~log2(N) roundings of 6e-8).
+  areas       relative area errors within 1e-4 of the oracle's.
+Step counts must agree exactly: both sides take the accept/reject decisions in FP64
+(FP64 path), and a decision flip would show up as a count difference.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1802_07625_gb300 as P
+from paper_1802_07625_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_POS_TOL = 1e-9
+MIXED_POS_TOL = 1e-3
+AREA_TOL = 1e-4
+
+
+def _oracle_density(orc, m):
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    rho = orc.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
+    return rho / (m.values.sum() / A.sum())
+
+
+def _small_map(L=64, n=16, name="voronoi16_64"):
+    return synth.make_workload(name, L=L, n=n)
+
+
+def _ctx(m, blur, precision, **kw):
+    c = P.Cartogram(m.Lx, m.Ly, blur, precision=precision, **kw)
+    c.set_map(m)
+    return c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("L", [64, 128])
+def test_density_matches_oracle(orc, precision, L):
+    m = _small_map(L=L, n=16 if L == 64 else 40)
+    with _ctx(m, 1.0, precision) as c:
+        got = c.density()
+    ref = _oracle_density(orc, m)
+    # exact coverage by two different algorithms (edge accumulation vs polygon clipping)
+    assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-11)])
+@pytest.mark.parametrize("shape", [(64, 64), (32, 64), (64, 16), (8, 8)])
+def test_spectrum_matches_oracle(orc, precision, tol, shape):
+    Ly, Lx = shape
+    ring = synth.rectangle_ring(0.3 * Lx, 0.2 * Ly, 0.71 * Lx, 0.9 * Ly, 0.7)
+    one = synth.RegionMap(Lx, Ly, np.array([2.0]), np.array([0, len(ring)]),
+                          np.array([0], dtype=np.int32), ring)
+    strips = synth.strip_map(Lx, Ly, [0, Lx // 4, Lx // 2, Lx], [1.0, 3.0, 0.5], spacing=0.6)
+    for mm in (one, strips):
+        with _ctx(mm, 1.3, precision) as c:
+            got = c.spectrum()
+        ref = orc.forward(_oracle_density(orc, mm), 1.3)
+        assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+@pytest.mark.parametrize("shape", [(64, 64), (16, 64), (128, 32)])
+@pytest.mark.parametrize("t", [0.0, 0.7, 25.0])
+def test_velocity_matches_oracle(orc, precision, tol, shape, t):
+    Ly, Lx = shape
+    m = synth.strip_map(Lx, Ly, [0, Lx // 4, Lx // 2, Lx], [1.0, 3.0, 0.5], spacing=0.6) \
+        if Lx != Ly else _small_map(L=Lx)
+    with _ctx(m, 1.0, precision) as c:
+        c.spectrum()
+        rho, v = c.velocity(t)
+    spec = orc.forward(_oracle_density(orc, m), 1.0)
+    r0, gx, gy = orc.fields(spec, t)
+    vx, vy, _ = orc.velocity(r0, gx, gy)
+    assert np.max(np.abs(rho - r0)) < tol * np.max(np.abs(r0))
+    scale = max(np.max(np.hypot(vx, vy)), 1e-30)
+    assert np.max(np.abs(v[..., 0] - vx)) < tol * scale * 4
+    assert np.max(np.abs(v[..., 1] - vy)) < tol * scale * 4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_heun_step_matches_oracle(orc, precision, tol):
+    m = _small_map()
+    Lx, Ly = m.Lx, m.Ly
+    rng = np.random.default_rng(5)
+    disp = rng.uniform(-3, 3, (Ly, Lx, 2))
+    # keep every point inside the box, some on and near the walls
+    xc = np.arange(Lx)[None, :] + 0.5
+    yc = np.arange(Ly)[:, None] + 0.5
+    disp[..., 0] = np.clip(xc + disp[..., 0], 0, Lx) - xc
+    disp[..., 1] = np.clip(yc + disp[..., 1], 0, Ly) - yc
+    t, h = 0.3, 0.45
+    with _ctx(m, 1.0, precision) as c:
+        c.spectrum()
+        out, err = c.heun_step(t, h, disp)
+    spec = orc.forward(_oracle_density(orc, m), 1.0)
+    v0 = orc.velocity(*orc.fields(spec, t))
+    v1 = orc.velocity(*orc.fields(spec, t + h))
+    x = (xc + disp[..., 0]).ravel()
+    y = (yc + disp[..., 1]).ravel()
+    _, _, xcor, ycor, e = orc.heun_step(v0[0], v0[1], v1[0], v1[1], x, y, h)
+    got_x = (xc + out[..., 0]).ravel()
+    got_y = (yc + out[..., 1]).ravel()
+    assert np.max(np.abs(got_x - xcor)) < tol * 10
+    assert np.max(np.abs(got_y - ycor)) < tol * 10
+    assert abs(err - e) < tol * 10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("L", [64, 128])
+def test_integration_matches_oracle(orc, precision, L):
+    m = _small_map(L=L, n=16 if L == 64 else 40)
+    with _ctx(m, 1.0, precision) as c:
+        c.spectrum()
+        grid, acc, rej, t_end = c.integrate_once()
+    spec = orc.forward(_oracle_density(orc, m), 1.0)
+    r = orc.integrate(spec)
+    assert r.status == 0
+    tol = FP64_POS_TOL if precision == "fp64" else MIXED_POS_TOL
+    if precision == "fp64":
+        assert (acc, rej) == (r.accepted, r.rejected)
+        assert t_end == pytest.approx(r.t_end, rel=1e-12)
+    assert np.max(np.abs(grid[..., 0] - r.X)) < tol
+    assert np.max(np.abs(grid[..., 1] - r.Y)) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_cartogram_matches_oracle(orc, precision):
+    m = synth.make_workload("voronoi16_64")
+    with _ctx(m, 1.0, precision) as c:
+        st = c.integrate()
+        xy = c.vertices()
+        err = c.area_errors()
+        nhist = c.history_length()
+    r = orc.cartogram(m, blur=1.0)
+    assert r.converged and st.converged
+    assert st.iterations == r.iterations == nhist
+    tol = FP64_POS_TOL if precision == "fp64" else MIXED_POS_TOL
+    assert np.max(np.abs(xy - r.xy)) < tol
+    assert np.max(np.abs(err - r.err)) < AREA_TOL
+    assert st.max_area_error < 0.01
+    if precision == "fp64":
+        assert st.steps_accepted == r.steps_accepted and st.steps_rejected == r.steps_rejected
+
+
+def test_graph_and_host_loop_agree():
+    m = _small_map()
+    with _ctx(m, 1.0, "fp64", use_graph=1) as a, _ctx(m, 1.0, "fp64", use_graph=0) as b:
+        sa, sb = a.integrate(), b.integrate()
+        assert sa.iterations == sb.iterations
+        assert sa.steps_accepted == sb.steps_accepted
+        assert np.max(np.abs(a.vertices() - b.vertices())) < 1e-12
+
+
+def test_project_reproduces_vertices_and_accepts_device_arrays():
+    import torch
+    m = _small_map()
+    with _ctx(m, 1.0, "mixed") as c:
+        c.integrate()
+        xy = c.vertices()
+        got = c.project(m.xy)
+        assert np.max(np.abs(got - xy)) < 1e-12
+        dev_in = torch.tensor(m.xy, device="cuda")
+        dev_out = torch.empty_like(dev_in)
+        P.cartogram_project(c.ctx, dev_in, dev_out)
+        assert np.max(np.abs(dev_out.cpu().numpy() - xy)) < 1e-12
+        assert c.project(np.zeros((0, 2))).shape == (0, 2)
+
+
+def test_project_matches_oracle_composition(orc):
+    m = _small_map()
+    rng = np.random.default_rng(9)
+    pts = np.stack([rng.uniform(0, m.Lx, 500), rng.uniform(0, m.Ly, 500)], axis=1)
+    with _ctx(m, 1.0, "fp64") as c:
+        c.integrate()
+        got = c.project(pts)
+        grids = [c.grid(k) for k in range(c.history_length())]
+    r = orc.cartogram(m, blur=1.0)
+    ref = pts.copy()
+    for g in r.grids:
+        ref = orc.map_points(g[0], g[1], ref)
+    assert np.max(np.abs(got - ref)) < FP64_POS_TOL
+    for g, go in zip(grids, r.grids):
+        assert np.max(np.abs(g[..., 0] - go[0])) < FP64_POS_TOL
+        assert np.max(np.abs(g[..., 1] - go[1])) < FP64_POS_TOL
+
+
+def test_uniform_density_is_identity():
+    # all regions at their target areas: no iteration, the map is unchanged
+    m = synth.strip_map(32, 32, [0, 8, 16, 32], [8.0, 8.0, 16.0], spacing=1.0)
+    with _ctx(m, 1.0, "fp64") as c:
+        st = c.integrate()
+        assert st.iterations == 0 and st.converged
+        assert np.array_equal(c.vertices(), m.xy)
+
+
+def test_strip_map_reaches_one_dimensional_solution():
+    Lx, Ly = 64, 16
+    V = [1.0, 3.0]
+    m = synth.strip_map(Lx, Ly, [0, 32, 64], V, spacing=1.0)
+    with _ctx(m, 0.0, "mixed") as c:
+        st = c.integrate()
+        xy = c.vertices()
+    assert st.converged
+    mid = np.abs(m.xy[:, 0] - 32.0) < 1e-12
+    assert np.max(np.abs(xy[mid, 0] - Lx * V[0] / sum(V))) < 0.01 * Lx
+    assert np.max(np.abs(xy[:, 1] - m.xy[:, 1])) < 1e-5
+
+
+def test_invalid_inputs_are_rejected():
+    m = _small_map()
+    with P.Cartogram(64, 64, 1.0) as c:
+        bad = m.values.copy()
+        bad[3] = float("nan")
+        for vals, off, reg, xy in (
+            (bad, m.ring_offsets, m.ring_region, m.xy),
+            (-m.values, m.ring_offsets, m.ring_region, m.xy),
+            (m.values, m.ring_offsets, m.ring_region, m.xy + 60.0),
+            (m.values, np.array([0, 2], dtype=np.int64), np.array([0], dtype=np.int32), m.xy[:2]),
+            (m.values[:1], m.ring_offsets, m.ring_region, m.xy),
+        ):
+            with pytest.raises(P.CartogramError) as e:
+                c.set_regions(vals, off, reg, xy)
+            assert e.value.code == P.CG_EINVAL
+        with pytest.raises(P.CartogramError) as e:
+            c.integrate()
+        assert e.value.code == P.CG_ESTATE
+        # a clockwise-only region has negative area
+        ring = synth.rectangle_ring(10, 10, 20, 20, 1.0)[::-1].copy()
+        with pytest.raises(P.CartogramError) as e:
+            c.set_regions(np.array([1.0]), np.array([0, len(ring)]), np.array([0], dtype=np.int32), ring)
+        assert e.value.code == P.CG_EINVAL
+
+
+def test_step_budget_exhaustion_reports_stepfail():
+    m = _small_map()
+    with _ctx(m, 1.0, "fp64", max_steps=3) as c:
+        with pytest.raises(P.CartogramError) as e:
+            c.integrate()
+        assert e.value.code == P.CG_ESTEPFAIL
+        # the map was left as it was
+        assert np.array_equal(c.vertices(), m.xy)
+
+
+def test_iteration_budget_reports_noconverge():
+    m = _small_map()
+    with _ctx(m, 1.0, "mixed", max_iter=2) as c:
+        with pytest.raises(P.CartogramError) as e:
+            c.integrate()
+        assert e.value.code == P.CG_ENOCONVERGE
+        assert c.history_length() == 2
