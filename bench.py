@@ -231,7 +231,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed")
+    c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed", max_iter=100)
     c.set_stream(stream)
     P.cartogram_set_regions(c.ctx, d_vals, d_off, d_reg, d_xy)
     c._map = P._Map(m.n_regions, m.n_vertices)
@@ -266,6 +266,14 @@ def run_ours(args):
     value = updates_all / t_max
     s_per_cartogram = total_ms / 1e3 / args.steps
     last = stats[-1]
+
+    if args.no_extras:
+        # only the timed cartograms (for profiler captures of this command)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "s_per_cartogram": s_per_cartogram,
+                              "note": "timed cartograms only; no roofline, e2e, fp64 or cpu legs"}), flush=True)
+        c.close()
+        return 0
 
     # live per-kernel timing for the roofline (same stream, CUDA events)
     prof = c.profile(reps=20)
@@ -306,7 +314,7 @@ def run_ours(args):
     # the plain FP64 GPU path on the same workload (one converged cartogram)
     fp64 = None
     if args.fp64_steps > 0:
-        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64")
+        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64", max_iter=100)
         f.set_stream(stream)
         P.cartogram_set_regions(f.ctx, d_vals, d_off, d_reg, d_xy)
         f._map = P._Map(m.n_regions, m.n_vertices)
@@ -377,6 +385,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="run only the warm-up and timed cartograms (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -73,6 +73,9 @@ typedef struct cg_options {
     int max_iter;       /* outer iterations before CG_ENOCONVERGE (50) */
     int use_graph;      /* 1: whole integration is one CUDA-graph launch with a device-side
                            loop (default); 0: host-driven loop of the same kernels */
+    double blur_decay;  /* blur width of outer iteration k (counted from set_regions/reset) is
+                           blur_width * blur_decay^k (0.5); 1: the same blur in every
+                           iteration, 0: only the first integration is blurred */
 } cg_options;
 
 typedef struct cg_stats {

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("blur", ctypes.c_double),
                 ("dt0", ctypes.c_double), ("atol", ctypes.c_double), ("grow", ctypes.c_double),
                 ("shrink", ctypes.c_double), ("cfl", ctypes.c_double), ("rho_tol", ctypes.c_double),
-                ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("max_iter", ctypes.c_int)]
+                ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("blur_decay", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -56,14 +57,14 @@ class Stats(ctypes.Structure):
 # independently of the CUDA library's defaults; the parity tests pass the same
 # values to both sides explicitly.
 DEFAULTS = dict(dt0=1e-2, atol=1e-2, grow=1.2, shrink=0.5, cfl=1.0, rho_tol=1e-4,
-                area_tol=0.01, max_steps=4000, max_iter=50)
+                area_tol=0.01, max_steps=4000, max_iter=50, blur_decay=0.5)
 
 
 def params(Lx, Ly, blur, **kw) -> Params:
     d = dict(DEFAULTS)
     d.update(kw)
     return Params(Lx, Ly, blur, d["dt0"], d["atol"], d["grow"], d["shrink"], d["cfl"],
-                  d["rho_tol"], d["area_tol"], d["max_steps"], d["max_iter"])
+                  d["rho_tol"], d["area_tol"], d["max_steps"], d["max_iter"], d["blur_decay"])
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -57,6 +57,7 @@ typedef struct {
     double area_tol;   /* outer loop stops once max relative area error < area_tol */
     int max_steps;     /* per integration (accepted + rejected) */
     int max_iter;      /* outer iterations */
+    double blur_decay; /* iteration k blurs with width blur * blur_decay^k */
 } orc_params;
 
 typedef struct {
@@ -528,6 +529,7 @@ void orc_map_points(int Lx, int Ly, const double* X, const double* Y, long long 
  *   areas <- shoelace(xy); stop if max|err| < area_tol
  *   repeat up to max_iter times:
  *     rho <- rasterize(xy); spec <- forward(rho, blur); (X,Y) <- integrate(spec)
+ *     (iteration it blurs with width blur * blur_decay^it)
  *     xy <- map(X, Y, xy); areas <- shoelace(xy); stop if max|err| < area_tol
  * xy (n_vertices*2) is updated in place. If grids is non-NULL it receives the
  * projected grid of every iteration, [iter][2][Ly][Lx] (X then Y), up to max_iter.
@@ -552,7 +554,7 @@ int orc_cartogram(const orc_params* P, int n_regions, const double* values,
     while (mx >= P->area_tol) {
         if (it >= P->max_iter) { status = -4; break; }
         orc_rasterize(Lx, Ly, n_regions, values, areas, n_rings, ring_offsets, ring_region, xy, rho);
-        orc_forward(Lx, Ly, rho, P->blur, spec);
+        orc_forward(Lx, Ly, rho, P->blur * pow(P->blur_decay, (double)it), spec);
         long long a, r;
         double tend;
         int s = orc_integrate(P, spec, X, Y, &a, &r, &tend, NULL, NULL, 0);

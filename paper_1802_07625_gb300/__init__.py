@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("dt0", ctypes.c_double), ("atol", ctypes.c_double),
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -34,7 +34,9 @@ struct cg_ctx {
   // forward (FP64) roots, quarter-wave factors and blur factors
   void *Wx = nullptr, *Wy = nullptr, *Ex = nullptr, *Ey = nullptr;
   double2 *Wfx = nullptr, *Wfy = nullptr, *Efx = nullptr, *Efy = nullptr;
-  double *bx = nullptr, *by = nullptr;
+  double *bx = nullptr, *by = nullptr;  // blur factors for width blur_tab_sigma
+  double* blur_h = nullptr;              // pinned staging of the blur factors
+  double blur_tab_sigma = -1.0;
 
   // fields
   double* acc = nullptr;     // rasterised rho/rho_bar - 1 (FP64)
@@ -150,14 +152,23 @@ int upload_tables(cg_ctx* c, int N, void** Wd, void** Ed, double2** Wfd, double2
   return CG_OK;
 }
 
-int upload_blur(cg_ctx* c, int N, double sigma, double** d) {
-  std::vector<double> b(N);
-  for (int m = 0; m < N; ++m) {
-    const double k = cg::kPi * m / N;
-    b[m] = std::exp(-0.5 * k * k * sigma * sigma);
+// Separable blur factors exp(-(pi m / L)^2 sigma^2 / 2) of both axes, staged through
+// pinned memory (the stream is synchronised once per outer iteration, before the
+// staging buffer is written again).
+int set_blur_tables(cg_ctx* c, double sigma) {
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  double* h = c->blur_h;
+  for (int m = 0; m < c->Lx; ++m) {
+    const double k = cg::kPi * m / c->Lx;
+    h[m] = std::exp(-0.5 * k * k * sigma * sigma);
   }
-  CG_CUDA(c, cudaMalloc((void**)d, sizeof(double) * N));
-  CG_CUDA(c, cudaMemcpy(*d, b.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  for (int n = 0; n < c->Ly; ++n) {
+    const double k = cg::kPi * n / c->Ly;
+    h[c->Lx + n] = std::exp(-0.5 * k * k * sigma * sigma);
+  }
+  CG_CUDA(c, cudaMemcpyAsync(c->bx, h, sizeof(double) * c->Lx, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(c, cudaMemcpyAsync(c->by, h + c->Lx, sizeof(double) * c->Ly, cudaMemcpyHostToDevice, c->stream));
+  c->blur_tab_sigma = sigma;
   return CG_OK;
 }
 
@@ -168,8 +179,10 @@ int alloc_fields(cg_ctx* c) {
   if (r) return r;
   r = upload_tables<T>(c, c->Ly, &c->Wy, &c->Ey, &c->Wfy, &c->Efy);
   if (r) return r;
-  if ((r = upload_blur(c, c->Lx, c->blur, &c->bx))) return r;
-  if ((r = upload_blur(c, c->Ly, c->blur, &c->by))) return r;
+  CG_CUDA(c, cudaMalloc((void**)&c->bx, sizeof(double) * c->Lx));
+  CG_CUDA(c, cudaMalloc((void**)&c->by, sizeof(double) * c->Ly));
+  CG_CUDA(c, cudaMallocHost((void**)&c->blur_h, sizeof(double) * (c->Lx + c->Ly)));
+  if (c->blur > 0.0 && (r = set_blur_tables(c, c->blur))) return r;
   CG_CUDA(c, cudaMalloc((void**)&c->acc, sizeof(double) * N));
   CG_CUDA(c, cudaMalloc((void**)&c->R, sizeof(double) * N));
   CG_CUDA(c, cudaMalloc((void**)&c->spec64, sizeof(double) * N));
@@ -326,9 +339,16 @@ int run_integration(cg_ctx* c) {
 
 template <typename T>
 int run_forward(cg_ctx* c) {
+  // blur width of this outer iteration: blur * decay^k
+  const double sigma = c->blur * std::pow(c->opt.blur_decay, (double)c->hist_len);
+  const bool blur = sigma > 0.0;
+  if (blur && sigma != c->blur_tab_sigma) {
+    int r = set_blur_tables(c, sigma);
+    if (r) return r;
+  }
   cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
-                    sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy, c->bx,
-                    c->by, c->stream);
+                    sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                    blur ? c->bx : nullptr, blur ? c->by : nullptr, c->stream);
   c->have_spectrum = true;
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;
@@ -567,7 +587,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
         case 4:
           cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
                             sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
-                            c->bx, c->by, s);
+                            c->bx, c->by, s);  // timing only
           break;
         default:
           cg::launch_map_points<T>(c->xy0, c->pts, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s);
@@ -621,6 +641,7 @@ int cartogram_default_options(cg_options* o) {
   o->max_steps = 4000;
   o->max_iter = 50;
   o->use_graph = 1;
+  o->blur_decay = 0.5;
   return CG_OK;
 }
 
@@ -884,6 +905,7 @@ void cartogram_destroy(cg_ctx* c) {
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);
   for (void* p : c->hist) cudaFree(p);
   if (c->info_h) cudaFreeHost(c->info_h);
+  if (c->blur_h) cudaFreeHost(c->blur_h);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

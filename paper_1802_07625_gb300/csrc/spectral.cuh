@@ -276,9 +276,9 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
     const C V1 = mk2<double>(0.5 * (Vn.x + Vq.x), 0.5 * (Vn.y - Vq.y));
     const C V2 = mk2<double>(0.5 * (Vn.y + Vq.y), -0.5 * (Vn.x - Vq.x));
     const int m = c0 + 2 * p;
-    const double wn = (n == 0 ? 1.0 : 2.0) * by[n];
-    double s0 = (en.x * V1.x + en.y * V1.y) * wn * (m == 0 ? 1.0 : 2.0) * bx[m];
-    double s1 = (en.x * V2.x + en.y * V2.y) * wn * 2.0 * bx[m + 1];
+    const double wn = (n == 0 ? 1.0 : 2.0) * (by ? by[n] : 1.0);
+    double s0 = (en.x * V1.x + en.y * V1.y) * wn * (m == 0 ? 1.0 : 2.0) * (bx ? bx[m] : 1.0);
+    double s1 = (en.x * V2.x + en.y * V2.y) * wn * 2.0 * (bx ? bx[m + 1] : 1.0);
     if (m == 0 && n == 0) s0 = 0.0;
     const size_t o = (size_t)n * Lx + m;
     spec64[o] = s0;
