@@ -152,28 +152,34 @@ def bytes_per_point(esz):
     return {"inverse_rows": 3 * esz, "inverse_cols_velocity": 4 * esz, "heun_step": 8 * esz}
 
 
-def cpu_baseline(m, blur, n_steps, threads=None):
-    """The FP64 oracle (as it stands) on the host cores: n_steps attempted steps of the
-    workload's first integration (field at t+h by direct sums + Heun step of all points)."""
-    import oracle
-    oracle.build()
-    if threads:
-        oracle.set_threads(threads)
-    A = oracle.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
-    rho = oracle.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
-    spec = oracle.forward(rho, blur)
-    rho_bar = spec[0, 0] / (m.Lx * m.Ly)
-    v0 = oracle.velocity(*oracle.fields(spec, 0.0))
-    X = (np.arange(m.Lx)[None, :] + 0.5) * np.ones((m.Ly, 1))
-    Y = (np.arange(m.Ly)[:, None] + 0.5) * np.ones((1, m.Lx))
-    h = 1e-2
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        v1 = oracle.velocity(*oracle.fields(spec, h))
-        oracle.heun_step(v0[0], v0[1], v1[0], v1[1], X.ravel(), Y.ravel(), h)
-    dt = time.perf_counter() - t0
-    del rho_bar
-    return {"value": n_steps * m.Lx * m.Ly / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+class OracleSample:
+    """The FP64 oracle (as it stands) on the host cores, set up once on the workload's
+    first integration; step() times one attempted step (field at t+h by direct
+    cosine/sine sums + Heun step of all grid points)."""
+
+    def __init__(self, m, blur):
+        import oracle
+        oracle.build()
+        self.o = oracle
+        self.m = m
+        A = oracle.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+        rho = oracle.rasterize(m.Lx, m.Ly, m.values, A, m.ring_offsets, m.ring_region, m.xy)
+        self.spec = oracle.forward(rho, blur)
+        self.v0 = oracle.velocity(*oracle.fields(self.spec, 0.0))
+        self.X = ((np.arange(m.Lx)[None, :] + 0.5) * np.ones((m.Ly, 1))).ravel()
+        self.Y = ((np.arange(m.Ly)[:, None] + 0.5) * np.ones((1, m.Lx))).ravel()
+
+    def step(self, h=1e-2):
+        t0 = time.perf_counter()
+        v1 = self.o.velocity(*self.o.fields(self.spec, h))
+        self.o.heun_step(self.v0[0], self.v0[1], v1[0], v1[1], self.X, self.Y, h)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(m, blur, n_steps):
+    s = OracleSample(m, blur)
+    dt = sum(s.step() for _ in range(n_steps))
+    return {"value": n_steps * m.Lx * m.Ly / dt, "unit": UNIT, "cores": s.o.num_threads(), "kind": "oracle",
             "sample": "%d attempted steps (field by direct cosine/sine sums + Heun step of all %dx%d grid "
                       "points) of the first integration of %s, %.1f s" % (n_steps, m.Lx, m.Ly, WORKLOAD, dt),
             "seconds": dt}
@@ -186,21 +192,22 @@ def run_reference(args):
     from paper_1802_07625_gb300 import synth
     m = synth.make_workload(WORKLOAD)
     blur = synth.WORKLOADS[WORKLOAD]["blur"]
+    sample = OracleSample(m, blur)
+    per = args.ref_attempts
     for _ in range(args.warmup):
-        cpu_baseline(m, blur, 1)
-    times = []
-    for _ in range(args.steps):
-        r = cpu_baseline(m, blur, 1)
-        times.append(r["seconds"])
+        sample.step()
+    times = [sum(sample.step() for _ in range(per)) for _ in range(args.steps)]
     total = sum(times)
-    value = args.steps * m.Lx * m.Ly / total
+    r = {"cores": sample.o.num_threads()}
+    value = args.steps * per * m.Lx * m.Ly / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "grid": "%dx%d" % (m.Lx, m.Ly),
-                                            "sample": "one attempted step per timed step"},
+                                            "sample": "%d attempted steps per timed step" % per},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": "one attempted step of the first integration per timed step"},
+                             "sample": "%d attempted steps (field by direct sums + Heun step of all "
+                                       "grid points) of the first integration per timed step" % per},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -231,10 +238,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed", max_iter=100)
+    c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed", max_iter=100,
+                    use_graph=0 if args.host_loop else 1)
     c.set_stream(stream)
     P.cartogram_set_regions(c.ctx, d_vals, d_off, d_reg, d_xy)
     c._map = P._Map(m.n_regions, m.n_vertices)
+
+    tune = c.autotune(reps=10)
 
     def one():
         c.reset()
@@ -358,6 +368,7 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
             "kernel_ms": prof,
+            "launch_shapes": tune,
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "peak_kind": peak_kind + " (copy bandwidth)",
@@ -383,8 +394,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--ref-attempts", type=int, default=20,
+                    help="oracle attempted steps per timed step of --impl reference")
+    ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the step kernels from the host instead of the conditional CUDA graph "
+                         "(profilers cannot capture kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="run only the warm-up and timed cartograms (for profiler captures)")
     args = ap.parse_args()

@@ -76,6 +76,8 @@ typedef struct cg_options {
     double blur_decay;  /* blur width of outer iteration k (counted from set_regions/reset) is
                            blur_width * blur_decay^k (0.5); 1: the same blur in every
                            iteration, 0: only the first integration is blurred */
+    int autotune;       /* 1: time the candidate launch shapes of the step kernels on first
+                           use and keep the fastest (default); 0: heuristic shapes */
 } cg_options;
 
 typedef struct cg_stats {
@@ -199,6 +201,14 @@ int cartogram_integrate_once(cg_ctx* ctx, double* grid_out, long long* accepted,
  *   4 forward transform (rows + columns), 5 vertex mapping + areas.
  * ms_out has 6 entries. Errors: CG_ESTATE (no map or no spectrum), CG_EINVAL. */
 int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
+
+/* Pick the launch shapes of the three step kernels (spectral rows per block of the
+ * first inverse pass, columns per block of the second, resident blocks per SM of the
+ * predictor-corrector step) by timing each candidate `reps` times with CUDA events on
+ * the context's stream. shapes_out[3] and ms_out[3] (may be NULL) receive the chosen
+ * shapes and their mean times per launch. cartogram_integrate runs this once by
+ * itself when the autotune option is set. Errors: CG_EINVAL, CG_ECUDA. */
+int cartogram_autotune(cg_ctx* ctx, int reps, int* shapes_out, double* ms_out);
 
 /* Description of the last error on this context ("" if none); valid until the next call. */
 const char* cartogram_last_error(const cg_ctx* ctx);

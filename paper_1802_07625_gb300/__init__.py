@@ -22,7 +22,7 @@ __all__ = [
     "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_profile", "cartogram_history_length", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_last_error", "cartogram_destroy", "Cartogram",
 ]
@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("dt0", ctypes.c_double), ("atol", ctypes.c_double),
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double)]
+                ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
         "cartogram_get_vertices": (i, [_P, _P]),
         "cartogram_history_length": (i, [_P]),
         "cartogram_reset": (i, [_P]),
+        "cartogram_autotune": (i, [_P, i, _P, _P]),
         "cartogram_profile": (i, [_P, i, _P]),
         "cartogram_get_grid": (i, [_P, i, _P]),
         "cartogram_density": (i, [_P, _P]),
@@ -219,6 +221,14 @@ def cartogram_profile(ctx, reps: int = 20) -> dict:
     return dict(zip(PROFILE_CLASSES, out.tolist()))
 
 
+def cartogram_autotune(ctx, reps: int = 10) -> dict:
+    shapes = np.zeros(3, dtype=np.int32)
+    ms = np.zeros(3)
+    _check(ctx, load().cartogram_autotune(ctx, int(reps), shapes.ctypes.data, ms.ctypes.data))
+    return {"rows_per_block": int(shapes[0]), "cols_per_block": int(shapes[1]),
+            "heun_blocks_per_sm": int(shapes[2]), "ms": ms.tolist()}
+
+
 def cartogram_history_length(ctx) -> int:
     return load().cartogram_history_length(ctx)
 
@@ -341,6 +351,9 @@ class Cartogram:
 
     def reset(self):
         cartogram_reset(self.ctx)
+
+    def autotune(self, reps=10):
+        return cartogram_autotune(self.ctx, reps)
 
     def profile(self, reps=20):
         return cartogram_profile(self.ctx, reps)

@@ -38,6 +38,24 @@ __device__ __forceinline__ V2<T> interp_v(const V2<T>* __restrict__ v, int Lx, i
   return mk2<T>(ux, uy);
 }
 
+// Two consecutive 2-vectors with one 16-byte access (FP32) or two (FP64).
+__device__ __forceinline__ void load_pair(const float2* p, float2 (&d)[2]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  d[0] = make_float2(v.x, v.y);
+  d[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double2* p, double2 (&d)[2]) {
+  d[0] = p[0];
+  d[1] = p[1];
+}
+__device__ __forceinline__ void store_pair(float2* p, const float2 (&d)[2]) {
+  *reinterpret_cast<float4*>(p) = make_float4(d[0].x, d[0].y, d[1].x, d[1].y);
+}
+__device__ __forceinline__ void store_pair(double2* p, const double2 (&d)[2]) {
+  p[0] = d[0];
+  p[1] = d[1];
+}
+
 template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
@@ -104,22 +122,31 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
     hd = st->h;
   }
   const T h = (T)hd, hh = (T)(0.5 * hd);
-  const int N = Lx * Ly;
+  const int npairs = (Lx * Ly) >> 1;
   T e2 = T(0);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+  // two horizontally adjacent points per thread (Lx is even), one vector load/store
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+    const int p = 2 * q;
     const int i = p & (Lx - 1), j = p >> log2Lx;
-    const V2<T> d = din[p];
-    const T lox = -((T)i + T(0.5)), hix = (T)(Lx - i) - T(0.5);
-    const T loy = -((T)j + T(0.5)), hiy = (T)(Ly - j) - T(0.5);
-    const V2<T> u0 = interp_v<T>(vcur, Lx, Ly, i, j, d.x, d.y);
-    const T px = clampT(d.x + h * u0.x, lox, hix);
-    const T py = clampT(d.y + h * u0.y, loy, hiy);
-    const V2<T> u1 = interp_v<T>(vnew, Lx, Ly, i, j, px, py);
-    const T cx = clampT(d.x + hh * (u0.x + u1.x), lox, hix);
-    const T cy = clampT(d.y + hh * (u0.y + u1.y), loy, hiy);
-    dout[p] = mk2<T>(cx, cy);
-    const T ex = cx - px, ey = cy - py;
-    e2 = max(e2, ex * ex + ey * ey);
+    V2<T> d[2];
+    load_pair(din + p, d);
+    V2<T> o[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int ik = i + k;
+      const T lox = -((T)ik + T(0.5)), hix = (T)(Lx - ik) - T(0.5);
+      const T loy = -((T)j + T(0.5)), hiy = (T)(Ly - j) - T(0.5);
+      const V2<T> u0 = interp_v<T>(vcur, Lx, Ly, ik, j, d[k].x, d[k].y);
+      const T px = clampT(d[k].x + h * u0.x, lox, hix);
+      const T py = clampT(d[k].y + h * u0.y, loy, hiy);
+      const V2<T> u1 = interp_v<T>(vnew, Lx, Ly, ik, j, px, py);
+      const T cx = clampT(d[k].x + hh * (u0.x + u1.x), lox, hix);
+      const T cy = clampT(d[k].y + hh * (u0.y + u1.y), loy, hiy);
+      o[k] = mk2<T>(cx, cy);
+      const T ex = cx - px, ey = cy - py;
+      e2 = max(e2, ex * ex + ey * ey);
+    }
+    store_pair(dout + p, o);
   }
   e2 = block_max(e2, red);
   if (threadIdx.x == 0) {

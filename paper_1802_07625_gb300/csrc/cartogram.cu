@@ -74,6 +74,11 @@ struct cg_ctx {
   double2* pts = nullptr;
   long long pts_cap = 0;
 
+  // launch shapes of the step kernels
+  cg::Tune tune;
+  bool tuned = false;
+  double tune_ms[3] = {0, 0, 0};
+
   // graph of one integration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -197,6 +202,7 @@ int alloc_fields(cg_ctx* c) {
     CG_CUDA(c, cudaMalloc(&c->dbuf[k], sizeof(V2<T>) * N));
   }
   CG_CUDA(c, cudaMalloc(&c->dres, sizeof(V2<T>) * N));
+  CG_CUDA(c, cudaMemset(c->dres, 0, sizeof(V2<T>) * N));
   CG_CUDA(c, cudaMalloc(&c->rho_tmp, sizeof(T) * N));
   CG_CUDA(c, cudaMalloc((void**)&c->st, sizeof(DevState)));
   CG_CUDA(c, cudaMemset(c->st, 0, sizeof(DevState)));
@@ -214,10 +220,10 @@ int alloc_fields(cg_ctx* c) {
 template <typename T>
 void enqueue_field(cg_ctx* c, int mode, double tau, V2<T>* out0, V2<T>* out1, T* rho_out,
                    cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
-  cg::launch_inv_rows<T>(c->log2Lx, c->Ly, (const T*)c->specT, (V2<T>*)c->AB, (const V2<T>*)c->Wx,
-                         (const V2<T>*)c->Ex, c->st, mode, tau, h, use_cond,
+  cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->specT, (V2<T>*)c->AB,
+                         (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, mode, tau, h, use_cond,
                          (unsigned int)c->opt.max_steps + 8u, s);
-  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, (const V2<T>*)c->AB, out0, out1, rho_out,
+  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, out0, out1, rho_out,
                          (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, mode, s);
 }
 
@@ -237,7 +243,7 @@ void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStr
                    use_cond);
   cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
                      (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeStep, 0.0, h,
-                     use_cond, s);
+                     use_cond, c->tune.heun_bps, s);
 }
 
 template <typename T>
@@ -245,6 +251,83 @@ void enqueue_finish(cg_ctx* c, cudaStream_t s) {
   cg::launch_snapshot<T>(c->st, (const V2<T>*)c->dbuf[0], (const V2<T>*)c->dbuf[1], (V2<T>*)c->dres,
                          c->Lx * c->Ly, s);
   cg::launch_collect(c->st, c->info, s);
+}
+
+// Time the candidate launch shapes of the three step kernels with CUDA events on the
+// context's stream (fields of the current spectrum at fixed times, the displacements of
+// the last integration) and keep the fastest of each.
+template <typename T>
+int do_autotune(cg_ctx* c, int reps) {
+  cudaStream_t s = c->stream;
+  const size_t esz = sizeof(T);
+  cudaEvent_t a, b;
+  CG_CUDA(c, cudaEventCreate(&a));
+  CG_CUDA(c, cudaEventCreate(&b));
+  CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  CG_CUDA(c, cudaMemcpyAsync(c->dbuf[0], c->dres, sizeof(V2<T>) * (size_t)c->Lx * c->Ly,
+                             cudaMemcpyDeviceToDevice, s));
+  const double t = 1.0, h = 0.5;
+  enqueue_field<T>(c, cg::kModeFixed, t, (V2<T>*)c->vbuf[0], nullptr, nullptr, s);
+  enqueue_field<T>(c, cg::kModeFixed, t + h, (V2<T>*)c->vbuf[1], nullptr, nullptr, s);
+  auto timeit = [&](auto&& launch, double* ms) -> int {
+    launch();
+    CG_CUDA(c, cudaEventRecord(a, s));
+    for (int r = 0; r < reps; ++r) launch();
+    CG_CUDA(c, cudaEventRecord(b, s));
+    CG_CUDA(c, cudaEventSynchronize(b));
+    float f = 0.f;
+    CG_CUDA(c, cudaEventElapsedTime(&f, a, b));
+    *ms = f / reps;
+    return CG_OK;
+  };
+  cg::Tune best = c->tune;
+  double best_ms[3] = {1e30, 1e30, 1e30};
+  int r;
+  for (int S = 1; S <= 16 && S <= c->Ly; S *= 2) {
+    const cg::LaunchCfg k = cg::inv_rows_cfg(c->log2Lx, c->Ly, esz, S);
+    if (k.smem > 227 * 1024 || k.threads > 1024) continue;
+    double ms;
+    if ((r = timeit([&] {
+           cg::launch_inv_rows<T>(c->log2Lx, c->Ly, S, (const T*)c->specT, (V2<T>*)c->AB,
+                                  (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFixed,
+                                  t + h, 0, 0, 0u, s);
+         }, &ms)))
+      return r;
+    if (ms < best_ms[0]) { best_ms[0] = ms; best.rows = S; }
+  }
+  for (int W = 2; W <= 16 && W <= c->Lx; W *= 2) {
+    const cg::LaunchCfg k = cg::inv_cols_cfg(c->log2Ly, c->Lx, esz, W);
+    if (k.smem > 227 * 1024 || k.threads > 1024) continue;
+    double ms;
+    if ((r = timeit([&] {
+           cg::launch_inv_cols<T>(c->log2Ly, c->Lx, W, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr,
+                                  nullptr, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st,
+                                  cg::kModeFixed, s);
+         }, &ms)))
+      return r;
+    if (ms < best_ms[1]) { best_ms[1] = ms; best.cols = W; }
+  }
+  const StepParams sp = step_params(c);
+  for (int bps = 2; bps <= 32; bps *= 2) {
+    double ms;
+    if ((r = timeit([&] {
+           cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
+                              (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h,
+                              0, 0, bps, s);
+         }, &ms)))
+      return r;
+    if (ms < best_ms[2]) { best_ms[2] = ms; best.heun_bps = bps; }
+  }
+  CG_CUDA(c, cudaGetLastError());
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->tune = best;
+  for (int k = 0; k < 3; ++k) c->tune_ms[k] = best_ms[k];
+  c->tuned = true;
+  // a graph captured with other shapes is rebuilt on next use
+  if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  return CG_OK;
 }
 
 // One integration as a graph: init kernels, then a WHILE node whose body is one
@@ -310,6 +393,10 @@ int build_graph(cg_ctx* c) {
 template <typename T>
 int run_integration(cg_ctx* c) {
   cudaStream_t s = c->stream;
+  if (c->opt.autotune && !c->tuned) {
+    int r = do_autotune<T>(c, 10);
+    if (r) return r;
+  }
   if (c->opt.use_graph) {
     if (!c->exec) {
       int r = build_graph<T>(c);
@@ -481,7 +568,7 @@ int do_heun(cg_ctx* c, double t, double h, const double* din, double* dout, doub
   CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
   cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
                      (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0,
-                     c->stream);
+                     c->tune.heun_bps, c->stream);
   CG_CUDA(c, cudaGetLastError());
   if ((r = copy_field_out<T>(c, c->dbuf[1], dout, 2))) return r;
   DevState hs;
@@ -570,16 +657,19 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
     for (int r = 0; r < reps; ++r) {
       switch (k) {
         case 0:
-          cg::launch_inv_rows<T>(c->log2Lx, c->Ly, (const T*)c->specT, (V2<T>*)c->AB, (const V2<T>*)c->Wx,
-                                 (const V2<T>*)c->Ex, c->st, cg::kModeFixed, t + h, 0, 0, 0u, s);
+          cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->specT, (V2<T>*)c->AB,
+                                 (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFixed, t + h,
+                                 0, 0, 0u, s);
           break;
         case 1:
-          cg::launch_inv_cols<T>(c->log2Ly, c->Lx, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr, nullptr,
+          cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1],
+                                 nullptr, nullptr,
                                  (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
           break;
         case 2:
           cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                             (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0, s);
+                             (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0,
+                             c->tune.heun_bps, s);
           break;
         case 3:
           run_raster(c);
@@ -642,6 +732,7 @@ int cartogram_default_options(cg_options* o) {
   o->max_iter = 50;
   o->use_graph = 1;
   o->blur_decay = 0.5;
+  o->autotune = 1;
   return CG_OK;
 }
 
@@ -818,6 +909,18 @@ int cartogram_profile(cg_ctx* c, int reps, double* ms_out) {
   if (!c->have_spectrum) return fail(c, CG_ESTATE, "no spectrum: run an integration first");
   if (reps < 1 || !ms_out) return fail(c, CG_EINVAL, "bad profile arguments");
   return c->mixed ? do_profile<float>(c, reps, ms_out) : do_profile<double>(c, reps, ms_out);
+}
+
+int cartogram_autotune(cg_ctx* c, int reps, int* shapes_out, double* ms_out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (reps < 1) return fail(c, CG_EINVAL, "reps must be positive");
+  r = c->mixed ? do_autotune<float>(c, reps) : do_autotune<double>(c, reps);
+  if (r) return r;
+  const int shp[3] = {c->tune.rows, c->tune.cols, c->tune.heun_bps};
+  if (shapes_out) CG_CUDA(c, cudaMemcpy(shapes_out, shp, sizeof shp, cudaMemcpyDefault));
+  if (ms_out) CG_CUDA(c, cudaMemcpy(ms_out, c->tune_ms, sizeof c->tune_ms, cudaMemcpyDefault));
+  return CG_OK;
 }
 
 int cartogram_history_length(const cg_ctx* c) { return c ? c->hist_len : 0; }

@@ -61,6 +61,7 @@ struct FFTShape {
   static constexpr int N1 = 1 << L1;   // length of the step-B DFTs (rows)
   static constexpr int N2 = 1 << L2;   // length of the step-A DFTs (columns)
   static constexpr int STRIDE = N + N / N1;  // padded length of one signal in shared memory
+  static constexpr int SSTRIDE = STRIDE + 1; // distance between signals (shifts their banks)
   __device__ static __forceinline__ int pidx(int p) { return p + (p >> L1); }
   // shared-memory slot of output X[k] once block_fft has run
   __device__ static __forceinline__ int out_slot(int k) {
@@ -68,7 +69,7 @@ struct FFTShape {
   }
 };
 
-// In-place DFT of S signals stored at buf[s*STRIDE + pidx(p)], p in [0, N), with root
+// In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N), with root
 // table W (shared memory, N entries). Unnormalised. Ends with __syncthreads().
 template <typename T, int LOG2N>
 __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ W) {
@@ -76,7 +77,7 @@ __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __rest
   using F = FFTShape<LOG2N>;
   for (int task = threadIdx.x; task < S * F::N1; task += blockDim.x) {
     const int s = task >> F::L1, n1 = task & (F::N1 - 1);
-    C* x = buf + s * F::STRIDE;
+    C* x = buf + s * F::SSTRIDE;
     C a[F::N2];
 #pragma unroll
     for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
@@ -89,7 +90,7 @@ __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __rest
   __syncthreads();
   for (int task = threadIdx.x; task < S * F::N2; task += blockDim.x) {
     const int s = task >> F::L2, k2 = task & (F::N2 - 1);
-    C* x = buf + s * F::STRIDE;
+    C* x = buf + s * F::SSTRIDE;
     C a[F::N1];
 #pragma unroll
     for (int n1 = 0; n1 < F::N1; ++n1) a[n1] = x[F::pidx(n1 + F::N1 * k2)];

@@ -19,33 +19,53 @@ struct LaunchCfg {
 inline int fft_n1(int log2n) { return 1 << ((log2n + 1) / 2); }
 inline int fft_stride(int log2n) {
   const int N = 1 << log2n;
-  return N + N / fft_n1(log2n);
+  return N + N / fft_n1(log2n) + 1;  // padded signal length + one element between signals
+}
+
+// Launch shapes of the step kernels, chosen per context (heuristic defaults, or by the
+// autotuner): spectral rows per block of pass 1, columns per block of pass 2 (even),
+// and resident blocks per SM of the predictor-corrector kernel.
+struct Tune {
+  int rows = 0;
+  int cols = 0;
+  int heun_bps = 0;
+};
+
+inline int default_rows(int log2Lx, int Ly) {
+  int S = 128 / fft_n1(log2Lx);
+  if (S < 1) S = 1;
+  if (S > Ly) S = Ly;
+  return S;
+}
+inline int default_cols(int Lx, size_t esz) {
+  int Wc = (esz == 4 && Lx >= 1024) ? 4 : 2;
+  if (Wc > Lx) Wc = Lx;
+  return Wc;
 }
 
 // pass 1 of the inverse transform: S spectral rows per block
-inline LaunchCfg inv_rows_cfg(int log2Lx, int Ly, size_t esz) {
+inline LaunchCfg inv_rows_cfg(int log2Lx, int Ly, size_t esz, int S) {
   const int N = 1 << log2Lx, N1 = fft_n1(log2Lx);
-  int S = 128 / N1;
-  if (S < 1) S = 1;
-  if (S > Ly) S = Ly;
+  if (S <= 0) S = default_rows(log2Lx, Ly);
   LaunchCfg c;
   c.per_block = S;
   c.threads = S * N1;
-  c.smem = (size_t)N * 2 * esz + (size_t)S * fft_stride(log2Lx) * 2 * esz + (size_t)(N + S) * esz;
+  c.smem = (size_t)N * 4 * esz + (size_t)S * N * esz + (size_t)S * fft_stride(log2Lx) * 2 * esz +
+           (size_t)(N + S) * esz;
   c.grid = Ly / S;
   return c;
 }
 
 // pass 2 of the inverse transform: Wc columns per block
-inline LaunchCfg inv_cols_cfg(int log2Ly, int Lx, size_t esz) {
+inline LaunchCfg inv_cols_cfg(int log2Ly, int Lx, size_t esz, int Wc) {
   const int N = 1 << log2Ly, N1 = fft_n1(log2Ly);
-  int Wc = (esz == 4 && Lx >= 1024) ? 4 : 2;
-  if (Wc > Lx) Wc = Lx;
+  if (Wc <= 0) Wc = default_cols(Lx, esz);
   const int S = Wc + Wc / 2;
   LaunchCfg c;
   c.per_block = Wc;
   c.threads = S * N1;
-  c.smem = (size_t)N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz + 64 * esz;
+  c.smem = (size_t)N * 4 * esz + (size_t)Wc * N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz +
+           64 * esz;
   c.grid = Lx / Wc;
   return c;
 }
@@ -82,12 +102,14 @@ template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);
 cudaError_t prepare_forward(int log2Lx, int log2Ly);
 
 template <typename T>
-void launch_inv_rows(int log2Lx, int Ly, const T* spec, V2<T>* AB, const V2<T>* W, const V2<T>* E,
-                     DevState* st, int mode, double tau, cudaGraphConditionalHandle handle,
-                     int use_cond, unsigned int max_body, cudaStream_t s);
+void launch_inv_rows(int log2Lx, int Ly, int S, const T* spec, V2<T>* AB, const V2<T>* W,
+                     const V2<T>* E, DevState* st, int mode, double tau,
+                     cudaGraphConditionalHandle handle, int use_cond, unsigned int max_body,
+                     cudaStream_t s);
 template <typename T>
-void launch_inv_cols(int log2Ly, int Lx, const V2<T>* AB, V2<T>* v0, V2<T>* v1, T* rho_out,
-                     const V2<T>* W, const V2<T>* E, DevState* st, int mode, cudaStream_t s);
+void launch_inv_cols(int log2Ly, int Lx, int Wc, const V2<T>* AB, V2<T>* v0, V2<T>* v1,
+                     T* rho_out, const V2<T>* W, const V2<T>* E, DevState* st, int mode,
+                     cudaStream_t s);
 void launch_fwd_rows(int log2Lx, int log2Ly, const double* rho, double* R, const double2* Wx,
                      const double2* Ex, cudaStream_t s);
 template <typename T>
@@ -98,7 +120,8 @@ void launch_fwd(int log2Lx, int log2Ly, const double* rho, double* R, double* sp
 template <typename T>
 void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
                  V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
-                 int use_cond, cudaStream_t s);
+                 int use_cond, int blocks_per_sm, cudaStream_t s);
+int sm_count();
 void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s);
 void launch_init_finish(DevState* st, const StepParams& sp, cudaGraphConditionalHandle handle,
                         int use_cond, cudaStream_t s);

@@ -20,6 +20,7 @@
 #pragma once
 
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace cg {
 
@@ -30,11 +31,13 @@ __device__ __forceinline__ double texp(double x) { return exp(x); }
 __device__ __forceinline__ int dct3_src(int i, int N) { return (i & 1) ? (N - 1 - (i >> 1)) : (i >> 1); }
 
 // ---------------------------------------------------------------------------
-// pass 1: damped spectrum rows -> (A, B) rows.  blockDim = S * N1, grid = Ly / S.
-// shared: W[N] (C), buf[S*STRIDE] (C), fx[N] (T), fy[S] (T)
+// pass 1: damped spectrum rows -> (A, B), written transposed: ABt[i][n].
+// blockDim = S * N1, grid = Ly / S. The S spectral rows are staged in shared memory
+// by bulk asynchronous copies while the tables are loaded.
+// shared: W[N] E[N] (C), stage[S*N] (T), buf[S*SSTRIDE] (C), fx[N] fy[S] (T)
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
-__global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ AB,
+__global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
                                 const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
                                 int Ly, int S, DevState* st, int mode, double tau_fixed,
                                 cudaGraphConditionalHandle handle, int use_cond,
@@ -42,10 +45,13 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;
+  __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* W = reinterpret_cast<C*>(smem_raw);
-  C* buf = W + N;
-  T* fx = reinterpret_cast<T*>(buf + S * F::STRIDE);
+  C* E = W + N;
+  T* stage = reinterpret_cast<T*>(E + N);
+  C* buf = reinterpret_cast<C*>(stage + S * N);
+  T* fx = reinterpret_cast<T*>(buf + S * F::SSTRIDE);
   T* fyS = fx + N;
 
   double tau = tau_fixed;
@@ -61,10 +67,16 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     tau = (mode == kModeInit) ? st->t : st->t + st->h;
   }
   const int n0 = blockIdx.x * S;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, (uint32_t)(S * N * sizeof(T)));
+    for (int s = 0; s < S; ++s) bulk_g2s(stage + s * N, spec + (size_t)(n0 + s) * N, N * sizeof(T), &bar);
+  }
   const T kx = (T)(kPi * kPi * tau / ((double)N * N));
   const T ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     W[i] = Wg[i];
+    E[i] = Eg[i];
     fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
   }
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
@@ -72,13 +84,18 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     fyS[s] = texp(-ky * n * n) / (T)Ly;
   }
   __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0, kMbarTries)) {
+    if (threadIdx.x == 0) st->bad = 2;
+    mbar_wait_bounded(&bar, 0, kMbarTries);
+    return;
+  }
 
   const T kd = (T)(kPi / N);
   const int P = N / 2 + 1;
   for (int task = threadIdx.x; task < S * P; task += blockDim.x) {
     const int s = task / P, m = task - s * P;
-    const T* row = spec + (size_t)(n0 + s) * N;
-    C* x = buf + s * F::STRIDE;
+    const T* row = stage + s * N;
+    C* x = buf + s * F::SSTRIDE;
     const T f = fyS[s];
     const T am = row[m] * fx[m] * f;
     if (m == 0) {
@@ -89,54 +106,75 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     const int q = N - m;
     const T aq = row[q] * fx[q] * f;
     const T bq = -kd * (T)q * aq;
-    x[F::pidx(m)] = cmul(Eg[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
-    if (q != m) x[F::pidx(q)] = cmul(Eg[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+    x[F::pidx(m)] = cmul(E[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
+    if (q != m) x[F::pidx(q)] = cmul(E[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
   }
   __syncthreads();
   block_fft<T, LOG2N>(buf, S, W);
   for (int task = threadIdx.x; task < S * N; task += blockDim.x) {
-    const int s = task >> LOG2N, i = task & (N - 1);
-    const C u = buf[s * F::STRIDE + F::out_slot(dct3_src(i, N))];
-    AB[(size_t)(n0 + s) * N + i] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
+    const int i = task / S, s = task - i * S;
+    const C u = buf[s * F::SSTRIDE + F::out_slot(dct3_src(i, N))];
+    ABt[(size_t)i * Ly + n0 + s] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
   }
 }
 
 // ---------------------------------------------------------------------------
 // pass 2: (A, B) columns -> velocity. Wc columns per block (even): Wc signals for
-// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs.
+// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs. The Wc columns of
+// ABt are contiguous and staged by bulk asynchronous copies.
 // blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc.
-// shared: W[N] (C), buf[(Wc + Wc/2) * STRIDE] (C), red[64] (T)
+// shared: W[N] E[N] (C), stage[Wc*N] (C), buf[(Wc + Wc/2) * SSTRIDE] (C), red[64] (T)
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
-__global__ void inv_cols_kernel(const V2<T>* __restrict__ AB, V2<T>* vbuf0, V2<T>* vbuf1,
+__global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<T>* vbuf1,
                                 T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
                                 const V2<T>* __restrict__ Eg, int Lx, int Wc, DevState* st,
                                 int mode) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
+  __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* W = reinterpret_cast<C*>(smem_raw);
-  C* buf = W + N;
-  T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::STRIDE);
+  C* E = W + N;
+  C* stage = E + N;
+  C* buf = stage + Wc * N;
+  T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::SSTRIDE);
 
   if (mode != kModeFixed && st->status != kRunning) return;
   V2<T>* out = vbuf0;
   if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
 
-  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
   const int c0 = blockIdx.x * Wc;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, (uint32_t)(Wc * N * sizeof(C)));
+    for (int cc = 0; cc < Wc; ++cc)
+      bulk_g2s(stage + cc * N, ABt + (size_t)(c0 + cc) * N, N * sizeof(C), &bar);
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    W[i] = Wg[i];
+    E[i] = Eg[i];
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0, kMbarTries)) {
+    if (threadIdx.x == 0) st->bad = 2;
+    mbar_wait_bounded(&bar, 0, kMbarTries);
+    return;
+  }
+
   const int Wp = Wc / 2;
   const int P = N / 2 + 1;
   const T kd = (T)(kPi / N);
   for (int task = threadIdx.x; task < P * Wp; task += blockDim.x) {
-    const int m = task / Wp, p = task - m * Wp;
-    const int c = c0 + 2 * p;
-    const C Am0 = AB[(size_t)m * Lx + c], Am1 = AB[(size_t)m * Lx + c + 1];
-    C* x0 = buf + (2 * p) * F::STRIDE;
-    C* x1 = buf + (2 * p + 1) * F::STRIDE;
-    C* x2 = buf + (Wc + p) * F::STRIDE;
+    const int p = task / P, m = task - p * P;
+    const C* s0 = stage + (2 * p) * N;
+    const C* s1 = s0 + N;
+    const C Am0 = s0[m], Am1 = s1[m];
+    C* x0 = buf + (2 * p) * F::SSTRIDE;
+    C* x1 = x0 + F::SSTRIDE;
+    C* x2 = buf + (Wc + p) * F::SSTRIDE;
     if (m == 0) {
       x0[F::pidx(0)] = mk2<T>(Am0.x, T(0));
       x1[F::pidx(0)] = mk2<T>(Am1.x, T(0));
@@ -144,8 +182,8 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ AB, V2<T>* vbuf0, V2<T
       continue;
     }
     const int q = N - m;
-    const C Aq0 = AB[(size_t)q * Lx + c], Aq1 = AB[(size_t)q * Lx + c + 1];
-    const C em = Eg[m], eq = Eg[q];
+    const C Aq0 = s0[q], Aq1 = s1[q];
+    const C em = E[m], eq = E[q];
     {  // (rho', d_y rho) of column c
       const T am = Am0.x, aq = Aq0.x, bm = -kd * (T)m * am, bq = -kd * (T)q * aq;
       x0[F::pidx(m)] = cmul(em, mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
@@ -170,8 +208,8 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ AB, V2<T>* vbuf0, V2<T
   for (int task = threadIdx.x; task < N * Wc; task += blockDim.x) {
     const int j = task / Wc, cc = task - j * Wc;
     const int slot = F::out_slot(dct3_src(j, N));
-    const C u1 = buf[cc * F::STRIDE + slot];
-    const C u2 = buf[(Wc + (cc >> 1)) * F::STRIDE + slot];
+    const C u1 = buf[cc * F::SSTRIDE + slot];
+    const C u2 = buf[(Wc + (cc >> 1)) * F::SSTRIDE + slot];
     const T rp = u1.x;
     const T gy = (j & 1) ? -u1.y : u1.y;
     const T gx = (cc & 1) ? u2.y : u2.x;
@@ -217,7 +255,7 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
     const int s = task / (N / 2), k = task - s * (N / 2);
     const double2 e = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s) * N + 2 * k);
     const double2 o = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s + 1) * N + 2 * k);
-    C* x = buf + s * F::STRIDE;
+    C* x = buf + s * F::SSTRIDE;
     x[F::pidx(k)] = mk2<double>(e.x, o.x);
     x[F::pidx(N - 1 - k)] = mk2<double>(e.y, o.y);
   }
@@ -225,7 +263,7 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
   block_fft<double, LOG2N>(buf, S2, W);
   for (int task = threadIdx.x; task < S2 * N; task += blockDim.x) {
     const int s = task >> LOG2N, m = task & (N - 1);
-    const C* x = buf + s * F::STRIDE;
+    const C* x = buf + s * F::SSTRIDE;
     const C Vm = x[F::out_slot(m)];
     const C Vq = x[F::out_slot((N - m) & (N - 1))];
     const C em = Eg[m];
@@ -261,7 +299,7 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
     const int k = task / Wp, p = task - k * Wp;
     const double2 e = *reinterpret_cast<const double2*>(R + (size_t)(2 * k) * Lx + c0 + 2 * p);
     const double2 o = *reinterpret_cast<const double2*>(R + (size_t)(2 * k + 1) * Lx + c0 + 2 * p);
-    C* x = buf + p * F::STRIDE;
+    C* x = buf + p * F::SSTRIDE;
     x[F::pidx(k)] = e;
     x[F::pidx(N - 1 - k)] = o;
   }
@@ -269,7 +307,7 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   block_fft<double, LOG2N>(buf, Wp, W);
   for (int task = threadIdx.x; task < N * Wp; task += blockDim.x) {
     const int n = task / Wp, p = task - n * Wp;
-    const C* x = buf + p * F::STRIDE;
+    const C* x = buf + p * F::SSTRIDE;
     const C Vn = x[F::out_slot(n)];
     const C Vq = x[F::out_slot((N - n) & (N - 1))];
     const C en = Eg[n];

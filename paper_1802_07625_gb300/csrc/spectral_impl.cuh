@@ -11,9 +11,17 @@ namespace cg {
 
 template <typename T>
 cudaError_t prepare_spectral(int log2Lx, int log2Ly) {
+  // allow the largest shared memory any tuning candidate needs
   const int Lx = 1 << log2Lx, Ly = 1 << log2Ly;
-  const LaunchCfg r = inv_rows_cfg(log2Lx, Ly, sizeof(T));
-  const LaunchCfg c = inv_cols_cfg(log2Ly, Lx, sizeof(T));
+  LaunchCfg r = inv_rows_cfg(log2Lx, Ly, sizeof(T), 1), c = inv_cols_cfg(log2Ly, Lx, sizeof(T), 2);
+  for (int S = 1; S <= 16 && S <= Ly; S *= 2) {
+    const LaunchCfg k = inv_rows_cfg(log2Lx, Ly, sizeof(T), S);
+    if (k.smem <= 227 * 1024 && k.smem > r.smem) r = k;
+  }
+  for (int W = 2; W <= 16 && W <= Lx; W *= 2) {
+    const LaunchCfg k = inv_cols_cfg(log2Ly, Lx, sizeof(T), W);
+    if (k.smem <= 227 * 1024 && k.smem > c.smem) c = k;
+  }
   const LaunchCfg f = fwd_cols_cfg(log2Ly, Lx);
   cudaError_t e = cudaSuccess;
   switch (log2Lx) {
@@ -44,10 +52,11 @@ cudaError_t prepare_spectral(int log2Lx, int log2Ly) {
 }
 
 template <typename T>
-void launch_inv_rows(int log2Lx, int Ly, const T* spec, V2<T>* AB, const V2<T>* W, const V2<T>* E,
-                     DevState* st, int mode, double tau, cudaGraphConditionalHandle handle,
-                     int use_cond, unsigned int max_body, cudaStream_t s) {
-  const LaunchCfg c = inv_rows_cfg(log2Lx, Ly, sizeof(T));
+void launch_inv_rows(int log2Lx, int Ly, int S, const T* spec, V2<T>* AB, const V2<T>* W,
+                     const V2<T>* E, DevState* st, int mode, double tau,
+                     cudaGraphConditionalHandle handle, int use_cond, unsigned int max_body,
+                     cudaStream_t s) {
+  const LaunchCfg c = inv_rows_cfg(log2Lx, Ly, sizeof(T), S);
   switch (log2Lx) {
 #define CG_CASE(L)                                                                                \
   case L:                                                                                         \
@@ -62,9 +71,10 @@ void launch_inv_rows(int log2Lx, int Ly, const T* spec, V2<T>* AB, const V2<T>* 
 }
 
 template <typename T>
-void launch_inv_cols(int log2Ly, int Lx, const V2<T>* AB, V2<T>* v0, V2<T>* v1, T* rho_out,
-                     const V2<T>* W, const V2<T>* E, DevState* st, int mode, cudaStream_t s) {
-  const LaunchCfg c = inv_cols_cfg(log2Ly, Lx, sizeof(T));
+void launch_inv_cols(int log2Ly, int Lx, int Wc, const V2<T>* AB, V2<T>* v0, V2<T>* v1,
+                     T* rho_out, const V2<T>* W, const V2<T>* E, DevState* st, int mode,
+                     cudaStream_t s) {
+  const LaunchCfg c = inv_cols_cfg(log2Ly, Lx, sizeof(T), Wc);
   switch (log2Ly) {
 #define CG_CASE(L)                                                                              \
   case L:                                                                                       \
@@ -98,10 +108,10 @@ void launch_fwd(int log2Lx, int log2Ly, const double* rho, double* R, double* sp
 
 #define CG_INSTANTIATE_SPECTRAL(T)                                                                 \
   template cudaError_t prepare_spectral<T>(int, int);                                              \
-  template void launch_inv_rows<T>(int, int, const T*, V2<T>*, const V2<T>*, const V2<T>*,        \
+  template void launch_inv_rows<T>(int, int, int, const T*, V2<T>*, const V2<T>*, const V2<T>*,   \
                                    DevState*, int, double, cudaGraphConditionalHandle, int,        \
                                    unsigned int, cudaStream_t);                                    \
-  template void launch_inv_cols<T>(int, int, const V2<T>*, V2<T>*, V2<T>*, T*, const V2<T>*,      \
+  template void launch_inv_cols<T>(int, int, int, const V2<T>*, V2<T>*, V2<T>*, T*, const V2<T>*, \
                                    const V2<T>*, DevState*, int, cudaStream_t);                    \
   template void launch_fwd<T>(int, int, const double*, double*, double*, T*, const double2*,      \
                               const double2*, const double2*, const double2*, const double*,       \

@@ -5,6 +5,16 @@
 
 namespace cg {
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
+  }
+  return n;
+}
+
 static inline int blocks_for(long long n, int threads, int cap) {
   long long b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -15,12 +25,15 @@ static inline int blocks_for(long long n, int threads, int cap) {
 template <typename T>
 void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
                  V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
-                 int use_cond, cudaStream_t s) {
+                 int use_cond, int blocks_per_sm, cudaStream_t s) {
   int log2Lx = 0;
   while ((1 << log2Lx) < Lx) ++log2Lx;
-  const int N = Lx * Ly;
-  heun_kernel<T><<<blocks_for(N, 256, 1 << 20), 256, 0, s>>>(st, sp, v0, v1, d0, d1, Lx, Ly, log2Lx,
-                                                             mode, h, handle, use_cond);
+  // a grid-stride loop over point pairs with a few resident blocks per SM keeps the
+  // number of same-address atomics of the block reductions small
+  const int pairs = Lx * Ly / 2;
+  if (blocks_per_sm <= 0) blocks_per_sm = 8;
+  heun_kernel<T><<<blocks_for(pairs, 256, sm_count() * blocks_per_sm), 256, 0, s>>>(
+      st, sp, v0, v1, d0, d1, Lx, Ly, log2Lx, mode, h, handle, use_cond);
 }
 
 void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s) {
@@ -69,7 +82,7 @@ void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s) {
 
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
-                               V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int,      \
+                               V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
                                cudaStream_t);                                                       \
   template void launch_snapshot<T>(const DevState*, const V2<T>*, const V2<T>*, V2<T>*, int,        \
                                    cudaStream_t);                                                   \
