@@ -239,7 +239,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     c = P.Cartogram(m.Lx, m.Ly, blur, precision="mixed", max_iter=100,
-                    use_graph=0 if args.host_loop else 1)
+                    use_graph=0 if args.host_loop else args.loop_mode)
     c.set_stream(stream)
     P.cartogram_set_regions(c.ctx, d_vals, d_off, d_reg, d_xy)
     c._map = P._Map(m.n_regions, m.n_vertices)
@@ -324,7 +324,7 @@ def run_ours(args):
     # the plain FP64 GPU path on the same workload (one converged cartogram)
     fp64 = None
     if args.fp64_steps > 0:
-        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64", max_iter=100)
+        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64", max_iter=100, use_graph=args.loop_mode)
         f.set_stream(stream)
         P.cartogram_set_regions(f.ctx, d_vals, d_off, d_reg, d_xy)
         f._map = P._Map(m.n_regions, m.n_vertices)
@@ -360,6 +360,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "%dx%d" % (m.Lx, m.Ly), "regions": m.n_regions,
                        "vertices": m.n_vertices, "precision": "mixed", "blur": blur,
                        "l2": "flushed between timed steps (256 MB write)",
+                       "step_loop": {2: "persistent cooperative kernel", 1: "conditional CUDA graph"}[args.loop_mode]
+                       if not args.host_loop else "host loop",
                        "parallelism": "replicas" if world > 1 else "single"},
             "s_per_cartogram": s_per_cartogram,
             "iterations": last.iterations, "attempted_steps_per_cartogram": last.steps_accepted + last.steps_rejected,
@@ -398,6 +400,8 @@ def main():
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loop-mode", type=int, default=1, choices=[1, 2],
+                    help="2: persistent cooperative kernel per integration; 1: conditional CUDA graph")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the step kernels from the host instead of the conditional CUDA graph "
                          "(profilers cannot capture kernel nodes of graphs with conditional nodes)")

@@ -48,6 +48,7 @@ enum {
     CG_ENOCONVERGE = -4,   /* max_iter outer iterations did not reach area_tol */
     CG_EFOLD = -5,         /* a projected grid folded over (non-positive quad area) */
     CG_ESTEPFAIL = -6,     /* an integration used max_steps attempts, or its step collapsed */
+    CG_ETIMEOUT = -7,      /* a bounded device-side wait (grid barrier, bulk copy) gave up */
     CG_ESTATE = -8         /* call out of order (e.g. integrate before set_regions) */
 };
 
@@ -71,8 +72,11 @@ typedef struct cg_options {
     double area_tol;    /* outer iterations end when max |A_i/A^_i - 1| < area_tol (0.01) */
     int max_steps;      /* attempted steps per integration before CG_ESTEPFAIL (4000) */
     int max_iter;       /* outer iterations before CG_ENOCONVERGE (50) */
-    int use_graph;      /* 1: whole integration is one CUDA-graph launch with a device-side
-                           loop (default); 0: host-driven loop of the same kernels */
+    int use_graph;      /* how an integration's step loop runs: 1 (default) one CUDA-graph
+                           launch whose conditional WHILE node repeats the per-phase kernels;
+                           2 one persistent cooperative kernel whose phases meet at grid
+                           barriers (falls back to 1 where a cooperative launch does not fit);
+                           0 the same per-phase kernels launched by a host loop */
     double blur_decay;  /* blur width of outer iteration k (counted from set_regions/reset) is
                            blur_width * blur_decay^k (0.5); 1: the same blur in every
                            iteration, 0: only the first integration is blurred */

@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_ENOCONVERGE", "CG_EFOLD", "CG_ESTEPFAIL",
+    "CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_ENOCONVERGE", "CG_EFOLD", "CG_ESTEPFAIL", "CG_ETIMEOUT",
     "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
@@ -28,11 +28,11 @@ __all__ = [
 ]
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
-CG_ESTATE = -8
+CG_ETIMEOUT, CG_ESTATE = -7, -8
 CG_PRECISION_FP64, CG_PRECISION_MIXED = 0, 1
 
 _ERRNAMES = {0: "CG_OK", -1: "CG_EINVAL", -2: "CG_ENOMEM", -3: "CG_ECUDA", -4: "CG_ENOCONVERGE",
-             -5: "CG_EFOLD", -6: "CG_ESTEPFAIL", -8: "CG_ESTATE"}
+             -5: "CG_EFOLD", -6: "CG_ESTEPFAIL", -7: "CG_ETIMEOUT", -8: "CG_ESTATE"}
 
 
 class CartogramError(RuntimeError):

@@ -27,8 +27,9 @@ __device__ __forceinline__ V2<T> interp_v(const V2<T>* __restrict__ v, int Lx, i
   const T fx = dx - flx, fy = dy - fly;
   const int i0 = min(max(ix, 0), Lx - 1), i1 = min(max(ix + 1, 0), Lx - 1);
   const int j0 = min(max(iy, 0), Ly - 1), j1 = min(max(iy + 1, 0), Ly - 1);
-  const V2<T> a = v[(size_t)j0 * Lx + i0], b = v[(size_t)j0 * Lx + i1];
-  const V2<T> c = v[(size_t)j1 * Lx + i0], d = v[(size_t)j1 * Lx + i1];
+  const int r0 = j0 * Lx, r1 = j1 * Lx;  // Lx * Ly < 2^31
+  const V2<T> a = v[r0 + i0], b = v[r0 + i1];
+  const V2<T> c = v[r1 + i0], d = v[r1 + i1];
   const T gx = T(1) - fx, gy = T(1) - fy;
   T ux = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
   T uy = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
@@ -96,36 +97,17 @@ __device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
   if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
 }
 
-// One Heun step of every grid point. Step mode: buffers by parity, h from the state,
-// and the last block to finish runs the controller. Fixed mode (single step on
-// explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0, dout = dbuf1, step h.
+// Heun step of the point pairs q = q0, q0 + qstride, ... (two horizontally adjacent
+// points per pair, Lx even); returns this thread's max ||r_corr - r_pred||^2.
 template <typename T>
-__global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
-                                                    const V2<T>* vbuf0, const V2<T>* vbuf1,
-                                                    V2<T>* dbuf0, V2<T>* dbuf1, int Lx, int Ly,
-                                                    int log2Lx, int mode, double h_fixed,
-                                                    cudaGraphConditionalHandle handle, int use_cond) {
-  __shared__ T red[32];
-  __shared__ int last;
-  if (mode == kModeStep && st->status != kRunning) return;
-  const V2<T>* vcur = vbuf0;
-  const V2<T>* vnew = vbuf1;
-  const V2<T>* din = dbuf0;
-  V2<T>* dout = dbuf1;
-  double hd = h_fixed;
-  if (mode == kModeStep) {
-    const int par = st->parity;
-    vcur = par ? vbuf1 : vbuf0;
-    vnew = par ? vbuf0 : vbuf1;
-    din = par ? dbuf1 : dbuf0;
-    dout = par ? dbuf0 : dbuf1;
-    hd = st->h;
-  }
+__device__ __forceinline__ T heun_pairs(const V2<T>* __restrict__ vcur, const V2<T>* __restrict__ vnew,
+                                        const V2<T>* __restrict__ din, V2<T>* __restrict__ dout, int Lx,
+                                        int Ly, int log2Lx, double hd, int q0, int qstride) {
   const T h = (T)hd, hh = (T)(0.5 * hd);
   const int npairs = (Lx * Ly) >> 1;
   T e2 = T(0);
   // two horizontally adjacent points per thread (Lx is even), one vector load/store
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+  for (int q = q0; q < npairs; q += qstride) {
     const int p = 2 * q;
     const int i = p & (Lx - 1), j = p >> log2Lx;
     V2<T> d[2];
@@ -148,25 +130,67 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
     }
     store_pair(dout + p, o);
   }
-  e2 = block_max(e2, red);
+  return e2;
+}
+
+// One Heun step of every grid point. Step mode: buffers by parity, h from the state,
+// and the last block to finish runs the controller. Fixed mode (single step on
+// explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0, dout = dbuf1, step h.
+template <typename T>
+__global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
+                                                    const V2<T>* vbuf0, const V2<T>* vbuf1,
+                                                    V2<T>* dbuf0, V2<T>* dbuf1, int Lx, int Ly,
+                                                    int log2Lx, int mode, double h_fixed,
+                                                    cudaGraphConditionalHandle handle, int use_cond) {
+  __shared__ unsigned long long s_err2;
+  __shared__ unsigned int s_warps;
+  if (mode == kModeStep && st->status != kRunning) return;
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&st->err2_bits, (double)e2);
-    if (mode == kModeStep) {
-      __threadfence();
-      const unsigned int t = atomicAdd(&st->ticket, 1u);
-      last = (t == gridDim.x - 1);
-    }
+    s_err2 = 0ull;
+    s_warps = 0u;
   }
-  if (mode != kModeStep) return;
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    control_step(st, sp, handle, use_cond);
+  const V2<T>* vcur = vbuf0;
+  const V2<T>* vnew = vbuf1;
+  const V2<T>* din = dbuf0;
+  V2<T>* dout = dbuf1;
+  double hd = h_fixed;
+  if (mode == kModeStep) {
+    const int par = st->parity;
+    vcur = par ? vbuf1 : vbuf0;
+    vnew = par ? vbuf0 : vbuf1;
+    din = par ? dbuf1 : dbuf0;
+    dout = par ? dbuf0 : dbuf1;
+    hd = st->h;
+  }
+  T e2 = heun_pairs<T>(vcur, vnew, din, dout, Lx, Ly, log2Lx, hd,
+                       blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  // Block reduction without a block-wide barrier: each warp folds its maximum into
+  // shared memory; the last warp of the block to arrive publishes the block maximum
+  // and takes the block's ticket; the last block runs the controller.
+  e2 = warp_max(e2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&s_err2, (unsigned long long)__double_as_longlong((double)e2));
+    __threadfence_block();
+    const unsigned int arrived = atomicAdd(&s_warps, 1u);
+    if (arrived == (blockDim.x >> 5) - 1) {
+      __threadfence_block();
+      const double bm = __longlong_as_double((long long)atomicOr(&s_err2, 0ull));
+      atomic_max_nonneg(&st->err2_bits, bm);
+      if (mode == kModeStep) {
+        __threadfence();
+        const unsigned int t = atomicAdd(&st->ticket, 1u);
+        if (t == gridDim.x - 1) {
+          __threadfence();
+          control_step(st, sp, handle, use_cond);
+        }
+      }
+    }
   }
 }
 
 // Reset the state for a new integration (t = 0, h = dt0, parity 0, counters 0).
-__global__ void init_state_kernel(DevState* st, StepParams sp) {
+static __global__ void init_state_kernel(DevState* st, StepParams sp) {
   st->t = 0.0;
   st->h = sp.dt0;
   st->vmax = 0.0;
@@ -184,7 +208,7 @@ __global__ void init_state_kernel(DevState* st, StepParams sp) {
 
 // After the field at t = 0: stop at once if the density is already equal, else cap
 // the first step.
-__global__ void init_finish_kernel(DevState* st, StepParams sp, cudaGraphConditionalHandle handle,
+static __global__ void init_finish_kernel(DevState* st, StepParams sp, cudaGraphConditionalHandle handle,
                                    int use_cond) {
   const double vmax = sqrt(__longlong_as_double((long long)st->vmax2_bits));
   const double dev = __longlong_as_double((long long)st->dev_bits);

@@ -74,6 +74,13 @@ struct cg_ctx {
   double2* pts = nullptr;
   long long pts_cap = 0;
 
+  // persistent integration kernel
+  cg::GridBarrier* gb = nullptr;
+  cg::StepAcc* acc2 = nullptr;  // two reduction slots
+  int persist_grid = 0;         // 0: not available
+  size_t persist_smem = 0;
+  int persist_rows = 0, persist_cols = 0;
+
   // launch shapes of the step kernels
   cg::Tune tune;
   bool tuned = false;
@@ -130,16 +137,23 @@ StepParams step_params(const cg_ctx* c) {
 
 template <typename T>
 int upload_tables(cg_ctx* c, int N, void** Wd, void** Ed, double2** Wfd, double2** Efd) {
-  // roots W[p] = exp(+2 pi i p/N) and quarter-wave factors E[m] = exp(i pi m/(2N)),
-  // angles reduced exactly on the integers before the library cos/sin
+  // inter-step twiddles of the four-step FFT in [k2][n1] order, TW[k2*N1 + n1] =
+  // exp(+-2 pi i n1 k2 / N), and quarter-wave factors E[m] = exp(i pi m/(2N)); the
+  // angles are reduced exactly on the integers before the library cos/sin
+  const int log2N = ilog2(N);
+  const int N1 = 1 << ((log2N + 1) / 2), N2 = N / N1;
   std::vector<V2<T>> W(N), E(N);
   std::vector<double2> Wf(N), Ef(N);
+  for (int k2 = 0; k2 < N2; ++k2)
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const int p = (n1 * k2) % N;
+      const double a = 2.0 * cg::kPi * (double)p / N;
+      const double cw = std::cos(a), sw = std::sin(a);
+      W[k2 * N1 + n1].x = (T)cw;
+      W[k2 * N1 + n1].y = (T)sw;
+      Wf[k2 * N1 + n1] = make_double2(cw, -sw);
+    }
   for (int p = 0; p < N; ++p) {
-    const double a = 2.0 * cg::kPi * (double)p / N;
-    const double cw = std::cos(a), sw = std::sin(a);
-    W[p].x = (T)cw;
-    W[p].y = (T)sw;
-    Wf[p] = make_double2(cw, -sw);
     const double b = cg::kPi * (double)p / (2.0 * N);
     const double ce = std::cos(b), se = std::sin(b);
     E[p].x = (T)ce;
@@ -212,6 +226,24 @@ int alloc_fields(cg_ctx* c) {
   if (sizeof(T) == 4) CG_CUDA(c, cudaMemset(c->specT, 0, sizeof(T) * N));
   CG_CUDA(c, cg::prepare_spectral<T>(c->log2Lx, c->log2Ly));
   CG_CUDA(c, cg::prepare_forward(c->log2Lx, c->log2Ly));
+  CG_CUDA(c, cudaMalloc((void**)&c->gb, sizeof(cg::GridBarrier)));
+  CG_CUDA(c, cudaMalloc((void**)&c->acc2, 2 * sizeof(cg::StepAcc)));
+  // the persistent kernel: one resident grid sized to the larger of the two passes
+  {
+    const int S = cg::default_rows(c->log2Lx, c->Ly), Wc = cg::default_cols(c->Lx, sizeof(T));
+    const size_t smem = std::max(cg::inv_rows_cfg(c->log2Lx, c->Ly, sizeof(T), S).smem,
+                                 cg::inv_cols_cfg(c->log2Ly, c->Lx, sizeof(T), Wc).smem);
+    int bps = 0, coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (coop && smem <= 227 * 1024 && cg::prepare_integrate<T>(smem, &bps) == cudaSuccess && bps > 0) {
+      const int items = std::max(c->Ly / S, c->Lx / Wc);
+      c->persist_grid = std::min(bps * cg::sm_count(), std::max(items, cg::sm_count()));
+      c->persist_smem = smem;
+      c->persist_rows = S;
+      c->persist_cols = Wc;
+    }
+    cudaGetLastError();
+  }
   return CG_OK;
 }
 
@@ -393,6 +425,38 @@ int build_graph(cg_ctx* c) {
 template <typename T>
 int run_integration(cg_ctx* c) {
   cudaStream_t s = c->stream;
+  if (c->opt.use_graph == 2 && c->persist_grid > 0) {
+    cg::IntegrateArgs<T> a;
+    a.spec = (const T*)c->specT;
+    a.ABt = (V2<T>*)c->AB;
+    a.Wx = (const V2<T>*)c->Wx;
+    a.Ex = (const V2<T>*)c->Ex;
+    a.Wy = (const V2<T>*)c->Wy;
+    a.Ey = (const V2<T>*)c->Ey;
+    a.v0 = (V2<T>*)c->vbuf[0];
+    a.v1 = (V2<T>*)c->vbuf[1];
+    a.d0 = (V2<T>*)c->dbuf[0];
+    a.d1 = (V2<T>*)c->dbuf[1];
+    a.dres = (V2<T>*)c->dres;
+    a.st = c->st;
+    a.gb = c->gb;
+    a.acc = c->acc2;
+    a.sp = step_params(c);
+    a.Lx = c->Lx;
+    a.Ly = c->Ly;
+    a.log2Lx = c->log2Lx;
+    a.log2Ly = c->log2Ly;
+    a.S = c->persist_rows;
+    a.Wc = c->persist_cols;
+    CG_CUDA(c, cudaEventRecord(c->ev0, s));
+    CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+    CG_CUDA(c, cudaMemsetAsync(c->gb, 0, sizeof(cg::GridBarrier), s));
+    CG_CUDA(c, cudaMemsetAsync(c->acc2, 0, 2 * sizeof(cg::StepAcc), s));
+    CG_CUDA(c, cg::launch_integrate<T>(a, c->persist_grid, c->persist_smem, s));
+    cg::launch_collect(c->st, c->info, s);
+    CG_CUDA(c, cudaEventRecord(c->ev1, s));
+    return CG_OK;
+  }
   if (c->opt.autotune && !c->tuned) {
     int r = do_autotune<T>(c, 10);
     if (r) return r;
@@ -488,8 +552,9 @@ int do_integrate(cg_ctx* c, cg_stats* stats) {
     s.steps_rejected += inf.rejected;
     s.t_end = inf.t_end;
     if (inf.status != cg::kDone) {
-      status = fail(c, CG_ESTEPFAIL, "integration %d ended with status %d after %lld/%lld steps", it + 1,
-                    inf.status, inf.accepted, inf.rejected);
+      status = fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
+                    "integration %d ended with status %d after %lld/%lld steps", it + 1, inf.status,
+                    inf.accepted, inf.rejected);
       break;
     }
     if ((int)c->hist.size() <= c->hist_len) {
@@ -608,7 +673,9 @@ int do_integrate_once(cg_ctx* c, double* grid, long long* acc, long long* rej, d
   if (rej) *rej = inf.rejected;
   if (t_end) *t_end = inf.t_end;
   if (grid && (r = grid_out<T>(c, c->dres, grid))) return r;
-  if (inf.status != cg::kDone) return fail(c, CG_ESTEPFAIL, "integration ended with status %d", inf.status);
+  if (inf.status != cg::kDone)
+    return fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL, "integration ended with status %d",
+                inf.status);
   return CG_OK;
 }
 
@@ -745,6 +812,7 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   cartogram_default_options(&o);
   if (opt) o = *opt;
   if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED) return CG_EINVAL;
+  if (o.use_graph < 0 || o.use_graph > 2) return CG_EINVAL;
   if (!(o.dt0 > 0) || !(o.atol > 0) || !(o.grow >= 1.0) || !(o.shrink > 0 && o.shrink < 1) ||
       !(o.cfl > 0) || !(o.rho_tol > 0) || !(o.area_tol > 0) || o.max_steps < 1 || o.max_iter < 0 ||
       !is_finite(o.dt0) || !is_finite(o.atol) || !is_finite(o.grow) || !is_finite(o.cfl) || !is_finite(o.rho_tol) ||
@@ -1002,7 +1070,7 @@ void cartogram_destroy(cg_ctx* c) {
   free_regions(c);
   void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
-                c->dres, c->rho_tmp, c->st, c->info, c->pts};
+                c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);

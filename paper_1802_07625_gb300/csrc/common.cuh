@@ -52,6 +52,7 @@ enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2 };
 constexpr int kRunning = 0;
 constexpr int kDone = 1;
 constexpr int kStepFail = -6;
+constexpr int kTimeout = -7;
 
 // Per-iteration results read back by the host in one copy.
 struct IterInfo {
@@ -61,6 +62,20 @@ struct IterInfo {
   long long rejected;
   int status;           // DevState status after the integration
   int pad;
+};
+
+// Grid-wide barrier state of the persistent integration kernel.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+struct StepAcc {
+  unsigned long long err2;   // max ||r_corr - r_pred||^2 (bits of a non-negative double)
+  unsigned long long vmax2;  // max |v|^2 of the new field
+  unsigned long long dev;    // max |rho/rho_bar - 1| of the new field
+  unsigned int bad;          // a non-positive or non-finite density
+  unsigned int pad;
 };
 
 // Step-control constants passed by value to the kernels that need them.
@@ -99,5 +114,26 @@ template <typename T> __device__ __forceinline__ T block_max(T v, T* red) {
   }
   return v;
 }
+
+// Arguments of the persistent integration kernel.
+template <typename T>
+struct IntegrateArgs {
+  const T* spec;
+  V2<T>* ABt;
+  const V2<T>* Wx;
+  const V2<T>* Ex;
+  const V2<T>* Wy;
+  const V2<T>* Ey;
+  V2<T>* v0;
+  V2<T>* v1;
+  V2<T>* d0;
+  V2<T>* d1;
+  V2<T>* dres;
+  DevState* st;
+  GridBarrier* gb;
+  StepAcc* acc;  // two slots, zero at launch
+  StepParams sp;
+  int Lx, Ly, log2Lx, log2Ly, S, Wc;
+};
 
 }  // namespace cg

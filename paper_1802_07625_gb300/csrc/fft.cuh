@@ -4,11 +4,18 @@
 //   input index  n = n1 + N1*n2,   output index k = k2 + N2*k1,
 //   X[k2 + N2 k1] = sum_n1 W_N^{n1 k2} W_N1^{n1 k1} sum_n2 x[n1 + N1 n2] W_N2^{n2 k2}.
 // Step A: one thread per (signal, n1) does the N2-point DFT in registers and the
-// twiddle; step B: one thread per (signal, k2) does the N1-point DFT of a
+// twiddle W_N^{n1 k2}; step B: one thread per (signal, k2) does the N1-point DFT of a
 // contiguous row. Both steps work in place; afterwards X[k] sits at position
 // k1 + N1*k2. One padding element after every N1 keeps both steps free of shared-
 // memory bank conflicts.
+//
+// The register DFTs are radix-2 decimation in time with every twiddle a compile-time
+// constant: cos and sin of 2 pi j / n are evaluated at compile time from their Taylor
+// series after an exact integer reduction to the first quadrant; multiplications by
+// 1 and by +-i are elided.
 #pragma once
+
+#include <utility>
 
 #include "common.cuh"
 
@@ -22,34 +29,93 @@ __host__ __device__ constexpr int bitrev(int x, int bits) {
   return r;
 }
 
-// In-register DFT of R (power of two) points. W[p] = exp(s 2 pi i p / N) is the root
-// table of the enclosing length-N transform (the sign s picks the direction);
-// tstride = N / R. Radix-2 decimation in time after a compile-time bit reversal.
-template <typename C, int R>
-__device__ __forceinline__ void reg_dft(C (&a)[R], const C* __restrict__ W, int tstride) {
-  constexpr int LR = ilog2c(R);
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int j = bitrev(i, LR);
-    if (j > i) {
-      C t = a[i];
-      a[i] = a[j];
-      a[j] = t;
+// Taylor series of sin and cos, accurate to double rounding on [0, pi/2].
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int k = 1; k < 24; ++k) {
+    t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k < 24; ++k) {
+    t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    s += t;
+  }
+  return s;
+}
+// cos and sin of 2 pi k / n for n a multiple of 4: quadrant q = floor(4k/n) and
+// remainder r = k - q n/4 are exact integers; x = 2 pi r / n lies in [0, pi/2).
+__host__ __device__ constexpr double cos2pi(int k, int n) {
+  const int kk = ((k % n) + n) % n;
+  const int q = (4 * kk) / n, r = kk - q * (n / 4);
+  const double x = 2.0 * 3.14159265358979323846 * r / n;
+  return q == 0 ? taylor_cos(x) : q == 1 ? -taylor_sin(x) : q == 2 ? -taylor_cos(x) : taylor_sin(x);
+}
+__host__ __device__ constexpr double sin2pi(int k, int n) {
+  const int kk = ((k % n) + n) % n;
+  const int q = (4 * kk) / n, r = kk - q * (n / 4);
+  const double x = 2.0 * 3.14159265358979323846 * r / n;
+  return q == 0 ? taylor_sin(x) : q == 1 ? taylor_cos(x) : q == 2 ? -taylor_sin(x) : -taylor_cos(x);
+}
+
+// One radix-2 butterfly of a length-2*HALF sub-transform on a[U], a[U+HALF] with twiddle
+// exp(s 2 pi i J / (2 HALF)), s = +1 for the inverse direction.
+template <typename C, int R, bool INV, int HALF, int U, int J>
+__device__ __forceinline__ void butterfly(C (&a)[R]) {
+  using T = decltype(a[0].x);
+  C v = a[U + HALF];
+  if constexpr (J != 0) {
+    if constexpr (4 * J == 2 * HALF) {
+      // multiply by +i (inverse) or -i (forward)
+      v = INV ? mk2<T>(-v.y, v.x) : mk2<T>(v.y, -v.x);
+    } else {
+      constexpr double wr = cos2pi(J, 2 * HALF);
+      constexpr double wi = (INV ? 1.0 : -1.0) * sin2pi(J, 2 * HALF);
+      const T r = (T)wr, i = (T)wi;
+      v = mk2<T>(v.x * r - v.y * i, v.x * i + v.y * r);
     }
   }
-#pragma unroll
-  for (int half = 1; half < R; half <<= 1) {
-#pragma unroll
-    for (int i = 0; i < R; i += 2 * half) {
-#pragma unroll
-      for (int j = 0; j < half; ++j) {
-        C v = a[i + j + half];
-        if (j != 0) v = cmul(v, W[j * (R / (2 * half)) * tstride]);
-        const C u = a[i + j];
-        a[i + j] = cadd(u, v);
-        a[i + j + half] = csub(u, v);
-      }
-    }
+  const C u = a[U];
+  a[U] = cadd(u, v);
+  a[U + HALF] = csub(u, v);
+}
+
+template <typename C, int R, bool INV, int HALF, int... B>
+__device__ __forceinline__ void dft_stage(C (&a)[R], std::integer_sequence<int, B...>) {
+  (butterfly<C, R, INV, HALF, (B / HALF) * 2 * HALF + (B % HALF), B % HALF>(a), ...);
+}
+
+template <typename C, int R, int I>
+__device__ __forceinline__ void bitrev_swap(C (&a)[R]) {
+  constexpr int J = bitrev(I, ilog2c(R));
+  if constexpr (J > I) {
+    const C t = a[I];
+    a[I] = a[J];
+    a[J] = t;
+  }
+}
+template <typename C, int R, int... I>
+__device__ __forceinline__ void bitrev_all(C (&a)[R], std::integer_sequence<int, I...>) {
+  (bitrev_swap<C, R, I>(a), ...);
+}
+
+template <typename C, int R, bool INV, int HALF>
+__device__ __forceinline__ void dft_stages(C (&a)[R]) {
+  if constexpr (HALF < R) {
+    dft_stage<C, R, INV, HALF>(a, std::make_integer_sequence<int, R / 2>{});
+    dft_stages<C, R, INV, 2 * HALF>(a);
+  }
+}
+
+// In-register unnormalised DFT of R points (power of two), direction INV.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void reg_dft(C (&a)[R]) {
+  if constexpr (R > 1) {
+    bitrev_all<C, R>(a, std::make_integer_sequence<int, R>{});
+    dft_stages<C, R, INV, 1>(a);
   }
 }
 
@@ -69,10 +135,12 @@ struct FFTShape {
   }
 };
 
-// In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N), with root
-// table W (shared memory, N entries). Unnormalised. Ends with __syncthreads().
-template <typename T, int LOG2N>
-__device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ W) {
+// In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N).
+// TW[k2*N1 + n1] = exp(s 2 pi i n1 k2 / N) holds the inter-step twiddles (shared
+// memory; consecutive threads read consecutive entries). Unnormalised. Ends with
+// __syncthreads().
+template <typename T, int LOG2N, bool INV>
+__device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ TW) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   for (int task = threadIdx.x; task < S * F::N1; task += blockDim.x) {
@@ -81,9 +149,9 @@ __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __rest
     C a[F::N2];
 #pragma unroll
     for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
-    reg_dft<C, F::N2>(a, W, F::N1);
+    reg_dft<C, F::N2, INV>(a);
 #pragma unroll
-    for (int k2 = 1; k2 < F::N2; ++k2) a[k2] = cmul(a[k2], W[n1 * k2]);
+    for (int k2 = 1; k2 < F::N2; ++k2) a[k2] = cmul(a[k2], TW[k2 * F::N1 + n1]);
 #pragma unroll
     for (int k2 = 0; k2 < F::N2; ++k2) x[F::pidx(n1 + F::N1 * k2)] = a[k2];
   }
@@ -94,7 +162,7 @@ __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __rest
     C a[F::N1];
 #pragma unroll
     for (int n1 = 0; n1 < F::N1; ++n1) a[n1] = x[F::pidx(n1 + F::N1 * k2)];
-    reg_dft<C, F::N1>(a, W, F::N2);
+    reg_dft<C, F::N1, INV>(a);
 #pragma unroll
     for (int k1 = 0; k1 < F::N1; ++k1) x[F::pidx(k1 + F::N1 * k2)] = a[k1];
   }

@@ -122,6 +122,12 @@ void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T
                  V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
                  int use_cond, int blocks_per_sm, cudaStream_t s);
 int sm_count();
+
+// persistent integration kernel (persist.cu)
+constexpr int kIntegrateThreads = 256;
+template <typename T> cudaError_t prepare_integrate(size_t smem, int* blocks_per_sm);
+template <typename T>
+cudaError_t launch_integrate(const IntegrateArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s);
 void launch_init_finish(DevState* st, const StepParams& sp, cudaGraphConditionalHandle handle,
                         int use_cond, cudaStream_t s);

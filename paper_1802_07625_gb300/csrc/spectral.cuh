@@ -30,65 +30,62 @@ __device__ __forceinline__ double texp(double x) { return exp(x); }
 // Output index i of a cosine sum -> index of the complex DFT output that holds it.
 __device__ __forceinline__ int dct3_src(int i, int N) { return (i & 1) ? (N - 1 - (i >> 1)) : (i >> 1); }
 
+// Shared-memory footprint (bytes) of one pass-1 item of S rows and one pass-2 item of
+// Wc columns; mirrored by the host-side launch configurations.
+template <typename T, int LOG2N>
+__host__ __device__ constexpr size_t p1_smem(int S) {
+  using F = FFTShape<LOG2N>;
+  return (size_t)F::N * 4 * sizeof(T) + (size_t)S * F::N * sizeof(T) +
+         (size_t)S * F::SSTRIDE * 2 * sizeof(T) + (size_t)(F::N + S) * sizeof(T);
+}
+template <typename T, int LOG2N>
+__host__ __device__ constexpr size_t p2_smem(int Wc) {
+  using F = FFTShape<LOG2N>;
+  return (size_t)F::N * 4 * sizeof(T) + (size_t)Wc * F::N * 2 * sizeof(T) +
+         (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(T) + 64 * sizeof(T);
+}
+
 // ---------------------------------------------------------------------------
-// pass 1: damped spectrum rows -> (A, B), written transposed: ABt[i][n].
-// blockDim = S * N1, grid = Ly / S. The S spectral rows are staged in shared memory
-// by bulk asynchronous copies while the tables are loaded.
-// shared: W[N] E[N] (C), stage[S*N] (T), buf[S*SSTRIDE] (C), fx[N] fy[S] (T)
+// pass 1 item: damped spectrum rows [n0, n0+S) -> (A, B), written transposed: ABt[i][n].
+// The tables and the S spectral rows arrive in shared memory by bulk asynchronous
+// copies on `bar` (phase `ph`, toggled here) while the damping factors are computed.
+// All threads of the block call it. Returns false if the copies did not complete.
+// shared: W[N] (inter-step twiddles) E[N] (C), stage[S*N] (T), buf[S*SSTRIDE] (C),
+// fx[N] fy[S] (T)
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
-__global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
-                                const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
-                                int Ly, int S, DevState* st, int mode, double tau_fixed,
-                                cudaGraphConditionalHandle handle, int use_cond,
-                                unsigned int max_body) {
+__device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
+                                        const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+                                        int Ly, int S, int n0, double tau, unsigned char* smem,
+                                        uint64_t* bar, uint32_t& ph) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;
-  __shared__ __align__(8) uint64_t bar;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* W = reinterpret_cast<C*>(smem_raw);
+  C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
   T* stage = reinterpret_cast<T*>(E + N);
   C* buf = reinterpret_cast<C*>(stage + S * N);
   T* fx = reinterpret_cast<T*>(buf + S * F::SSTRIDE);
   T* fyS = fx + N;
-
-  double tau = tau_fixed;
-  if (mode == kModeStep && blockIdx.x == 0 && threadIdx.x == 0) {
-    // first kernel of a loop iteration: end the loop if the integration is over or
-    // has run more iterations than the controller allows
-    const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
-    if (st->status == kRunning && it > max_body) st->status = kStepFail;
-    if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
-  }
-  if (mode != kModeFixed) {
-    if (st->status != kRunning) return;
-    tau = (mode == kModeInit) ? st->t : st->t + st->h;
-  }
-  const int n0 = blockIdx.x * S;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (uint32_t)(S * N * sizeof(T)));
-    for (int s = 0; s < S; ++s) bulk_g2s(stage + s * N, spec + (size_t)(n0 + s) * N, N * sizeof(T), &bar);
+    // one transaction: both tables and the S spectral rows
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + S * N * sizeof(T)));
+    bulk_g2s(W, Wg, N * sizeof(C), bar);
+    bulk_g2s(E, Eg, N * sizeof(C), bar);
+    for (int s = 0; s < S; ++s) bulk_g2s(stage + s * N, spec + (size_t)(n0 + s) * N, N * sizeof(T), bar);
   }
   const T kx = (T)(kPi * kPi * tau / ((double)N * N));
   const T ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    W[i] = Wg[i];
-    E[i] = Eg[i];
-    fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
-  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
     const T n = (T)(n0 + s);
     fyS[s] = texp(-ky * n * n) / (T)Ly;
   }
   __syncthreads();
-  if (!mbar_wait_bounded(&bar, 0, kMbarTries)) {
-    if (threadIdx.x == 0) st->bad = 2;
-    mbar_wait_bounded(&bar, 0, kMbarTries);
-    return;
-  }
+  const bool ok = mbar_wait_bounded(bar, ph, kMbarTries);
+  ph ^= 1u;
+  if (!__syncthreads_and(ok)) return false;
 
   const T kd = (T)(kPi / N);
   const int P = N / 2 + 1;
@@ -110,59 +107,54 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     if (q != m) x[F::pidx(q)] = cmul(E[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
   }
   __syncthreads();
-  block_fft<T, LOG2N>(buf, S, W);
+  block_fft<T, LOG2N, true>(buf, S, W);
   for (int task = threadIdx.x; task < S * N; task += blockDim.x) {
     const int i = task / S, s = task - i * S;
     const C u = buf[s * F::SSTRIDE + F::out_slot(dct3_src(i, N))];
     ABt[(size_t)i * Ly + n0 + s] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
   }
+  __syncthreads();
+  return true;
 }
 
+// Block-reduced results of a pass-2 item (valid in thread 0).
+template <typename T> struct FieldRed {
+  T dev;    // max |rho/rho_bar - 1|
+  T v2max;  // max |v|^2
+  bool bad; // a non-positive or non-finite density
+};
+
 // ---------------------------------------------------------------------------
-// pass 2: (A, B) columns -> velocity. Wc columns per block (even): Wc signals for
-// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs. The Wc columns of
-// ABt are contiguous and staged by bulk asynchronous copies.
-// blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc.
+// pass 2 item: (A, B) columns [c0, c0+Wc) -> velocity (Wc even): Wc signals for
+// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs. The Wc columns of ABt
+// are contiguous and arrive with the tables by bulk asynchronous copies.
 // shared: W[N] E[N] (C), stage[Wc*N] (C), buf[(Wc + Wc/2) * SSTRIDE] (C), red[64] (T)
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
-__global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<T>* vbuf1,
-                                T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
-                                const V2<T>* __restrict__ Eg, int Lx, int Wc, DevState* st,
-                                int mode) {
+__device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __restrict__ out,
+                                        T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
+                                        const V2<T>* __restrict__ Eg, int Lx, int Wc, int c0,
+                                        unsigned char* smem, uint64_t* bar, uint32_t& ph,
+                                        FieldRed<T>& res) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
-  __shared__ __align__(8) uint64_t bar;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* W = reinterpret_cast<C*>(smem_raw);
+  C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
   C* stage = E + N;
   C* buf = stage + Wc * N;
   T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::SSTRIDE);
-
-  if (mode != kModeFixed && st->status != kRunning) return;
-  V2<T>* out = vbuf0;
-  if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
-  else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
-
-  const int c0 = blockIdx.x * Wc;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (uint32_t)(Wc * N * sizeof(C)));
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_expect_tx(bar, (uint32_t)((2 + Wc) * N * sizeof(C)));
+    bulk_g2s(W, Wg, N * sizeof(C), bar);
+    bulk_g2s(E, Eg, N * sizeof(C), bar);
     for (int cc = 0; cc < Wc; ++cc)
-      bulk_g2s(stage + cc * N, ABt + (size_t)(c0 + cc) * N, N * sizeof(C), &bar);
+      bulk_g2s(stage + cc * N, ABt + (size_t)(c0 + cc) * N, N * sizeof(C), bar);
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    W[i] = Wg[i];
-    E[i] = Eg[i];
-  }
-  __syncthreads();
-  if (!mbar_wait_bounded(&bar, 0, kMbarTries)) {
-    if (threadIdx.x == 0) st->bad = 2;
-    mbar_wait_bounded(&bar, 0, kMbarTries);
-    return;
-  }
+  const bool ok = mbar_wait_bounded(bar, ph, kMbarTries);
+  ph ^= 1u;
+  if (!__syncthreads_and(ok)) return false;
 
   const int Wp = Wc / 2;
   const int P = N / 2 + 1;
@@ -201,7 +193,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
     }
   }
   __syncthreads();
-  block_fft<T, LOG2N>(buf, Wc + Wp, W);
+  block_fft<T, LOG2N, true>(buf, Wc + Wp, W);
 
   T dev = T(0), v2max = T(0);
   bool bad = false;
@@ -223,13 +215,70 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
     dev = max(dev, fabs(rp));
     v2max = max(v2max, vx * vx + vy * vy);
   }
-  bad = __syncthreads_or(bad);
-  dev = block_max(dev, red);
-  v2max = block_max(v2max, red + 32);
+  res.bad = __syncthreads_or(bad);
+  res.dev = block_max(dev, red);
+  res.v2max = block_max(v2max, red + 32);
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// pass 1 as its own kernel. blockDim = S * N1, grid = Ly / S.
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
+                                const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+                                int Ly, int S, DevState* st, int mode, double tau_fixed,
+                                cudaGraphConditionalHandle handle, int use_cond,
+                                unsigned int max_body) {
+  __shared__ __align__(8) uint64_t bar;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double tau = tau_fixed;
+  if (mode == kModeStep && blockIdx.x == 0 && threadIdx.x == 0) {
+    // first kernel of a loop iteration: end the loop if the integration is over or
+    // has run more iterations than the controller allows
+    const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
+    if (st->status == kRunning && it > max_body) st->status = kStepFail;
+    if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+  }
+  if (mode != kModeFixed) {
+    if (st->status != kRunning) return;
+    tau = (mode == kModeInit) ? st->t : st->t + st->h;
+  }
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t ph = 0;
+  if (!p1_rows<T, LOG2N>(spec, ABt, Wg, Eg, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) &&
+      threadIdx.x == 0)
+    st->bad = 2;
+}
+
+// ---------------------------------------------------------------------------
+// pass 2 as its own kernel. blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc.
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<T>* vbuf1,
+                                T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
+                                const V2<T>* __restrict__ Eg, int Lx, int Wc, DevState* st,
+                                int mode) {
+  __shared__ __align__(8) uint64_t bar;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (mode != kModeFixed && st->status != kRunning) return;
+  V2<T>* out = vbuf0;
+  if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
+  else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t ph = 0;
+  FieldRed<T> r;
+  if (!p2_cols<T, LOG2N>(ABt, out, rho_out, Wg, Eg, Lx, Wc, blockIdx.x * Wc, smem_raw, &bar, ph, r)) {
+    if (threadIdx.x == 0) st->bad = 2;
+    return;
+  }
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&st->dev_bits, (double)dev);
-    atomic_max_nonneg(&st->vmax2_bits, (double)v2max);
-    if (bad) st->bad = 1;
+    atomic_max_nonneg(&st->dev_bits, (double)r.dev);
+    atomic_max_nonneg(&st->vmax2_bits, (double)r.v2max);
+    if (r.bad) st->bad = 1;
   }
 }
 
@@ -260,7 +309,7 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
     x[F::pidx(N - 1 - k)] = mk2<double>(e.y, o.y);
   }
   __syncthreads();
-  block_fft<double, LOG2N>(buf, S2, W);
+  block_fft<double, LOG2N, false>(buf, S2, W);
   for (int task = threadIdx.x; task < S2 * N; task += blockDim.x) {
     const int s = task >> LOG2N, m = task & (N - 1);
     const C* x = buf + s * F::SSTRIDE;
@@ -304,7 +353,7 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
     x[F::pidx(N - 1 - k)] = o;
   }
   __syncthreads();
-  block_fft<double, LOG2N>(buf, Wp, W);
+  block_fft<double, LOG2N, false>(buf, Wp, W);
   for (int task = threadIdx.x; task < N * Wp; task += blockDim.x) {
     const int n = task / Wp, p = task - n * Wp;
     const C* x = buf + p * F::SSTRIDE;
