@@ -214,6 +214,31 @@ int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
  * itself when the autotune option is set. Errors: CG_EINVAL, CG_ECUDA. */
 int cartogram_autotune(cg_ctx* ctx, int reps, int* shapes_out, double* ms_out);
 
+/* Velocity field from a caller's spectrum with no device allocation. The paper has no
+ * counterpart; this serves callers that cannot allocate GPU memory when they need the
+ * field (while capturing a CUDA graph, where cudaMalloc is not allowed; under a fixed
+ * memory budget; inside a real-time loop that must not touch the allocator).
+ *   Lx, Ly   powers of two from 8 to 512 (at most 512 x 512 cells); larger sizes
+ *            return CG_EINVAL
+ *   spec     device, FP32, [Ly][Lx] indexed [n*Lx + m], 16-byte aligned: the cosine
+ *            spectrum of rho/rho_bar - 1 (so spec[0] = 0), e.g. cartogram_spectrum's
+ *            output with its (0,0) entry set to zero, rounded to FP32
+ *   t        diffusion time (D = 1) at which the field is evaluated, >= 0
+ *   v_out    device, FP32, [Lx*Ly][2] (vx, vy) at the cell centres, 8-byte aligned
+ *   stream   cudaStream_t the work is queued on (NULL: the legacy default stream);
+ *            the call returns without waiting for it
+ * The scratch (about 2.1 MB: the intermediate of the two transform passes, the
+ * transform tables and a reduction state) is one array in device memory created when
+ * the library is loaded onto a GPU and kept until the process exits. The first call on
+ * a device, with that device current, looks up the array's device address and sets
+ * the kernels' shared-memory limits; make that first call before any stream capture.
+ * Every call on a device shares the array and leaves its contents behind: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. Returns CG_OK, CG_EINVAL (sizes, NULL, alignment, host
+ * pointers) or CG_ECUDA. */
+int cartogram_velocity_noalloc(int Lx, int Ly, const float* spec, double t, float* v_out,
+                               void* stream);
+
 /* Description of the last error on this context ("" if none); valid until the next call. */
 const char* cartogram_last_error(const cg_ctx* ctx);
 

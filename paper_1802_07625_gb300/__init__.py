@@ -24,7 +24,7 @@ __all__ = [
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
     "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
-    "cartogram_last_error", "cartogram_destroy", "Cartogram",
+    "cartogram_velocity_noalloc", "cartogram_last_error", "cartogram_destroy", "Cartogram",
 ]
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "cartogram_velocity": (i, [_P, d, _P, _P]),
         "cartogram_heun_step": (i, [_P, d, d, _P, _P, _P]),
         "cartogram_integrate_once": (i, [_P, _P, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(d)]),
+        "cartogram_velocity_noalloc": (i, [i, i, _P, d, _P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
     }
@@ -273,6 +274,22 @@ def cartogram_integrate_once(ctx, grid_out=None):
     a, r, t = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
     _check(ctx, load().cartogram_integrate_once(ctx, pg, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t)))
     return a.value, r.value, t.value
+
+
+def cartogram_velocity_noalloc(Lx, Ly, spec, t, v_out, stream=None) -> None:
+    """Field from a device FP32 spectrum into a device FP32 [Ly, Lx, 2] buffer, with no
+    device allocation (torch CUDA tensors; queued on `stream`, default torch's current)."""
+    import torch
+    if not (spec.is_cuda and v_out.is_cuda and spec.dtype == torch.float32 and v_out.dtype == torch.float32
+            and spec.is_contiguous() and v_out.is_contiguous()):
+        raise ValueError("spec and v_out must be contiguous float32 CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream(spec.device)
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rc = load().cartogram_velocity_noalloc(int(Lx), int(Ly), spec.data_ptr(), float(t), v_out.data_ptr(), stream)
+    if rc != CG_OK:
+        raise CartogramError(rc, "cartogram_velocity_noalloc(%d, %d) failed" % (Lx, Ly))
 
 
 def cartogram_last_error(ctx) -> str:
