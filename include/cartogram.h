@@ -163,6 +163,12 @@ int cartogram_history_length(const cg_ctx* ctx);
  * integration k, xy_out [Lx*Ly][2] FP64. Errors: CG_EINVAL (k out of range). */
 int cartogram_get_grid(cg_ctx* ctx, int k, double* xy_out);
 
+/* Fold check of history entry k (SI Eq. det: a density-equalising map has a positive
+ * Jacobian everywhere): the signed area of every quad of neighbouring projected grid
+ * points. *n_folded (may be NULL) receives the number of quads with non-positive area,
+ * *min_area (may be NULL) the smallest area in cells^2. Errors: CG_EINVAL (k). */
+int cartogram_fold_count(cg_ctx* ctx, int k, long long* n_folded, double* min_area);
+
 /* ---- step-level entry points (one stage of the method each) ---------------- */
 
 /* Rasterised density of the current vertices, normalised so that the box mean is 1
@@ -208,10 +214,13 @@ int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
 
 /* Pick the launch shapes of the three step kernels (spectral rows per block of the
  * first inverse pass, columns per block of the second, resident blocks per SM of the
- * predictor-corrector step) by timing each candidate `reps` times with CUDA events on
- * the context's stream. shapes_out[3] and ms_out[3] (may be NULL) receive the chosen
- * shapes and their mean times per launch. cartogram_integrate runs this once by
- * itself when the autotune option is set. Errors: CG_EINVAL, CG_ECUDA. */
+ * predictor-corrector step) by timing each candidate `reps` times (best of three rounds)
+ * with CUDA events on the context's stream, on the current spectrum and the
+ * displacements of the last integration. reps = 0 changes nothing and only reports.
+ * shapes_out[3] and ms_out[3] (may be NULL) receive the shapes in use and their mean
+ * times per launch (0 if never timed). cartogram_integrate runs this once by itself,
+ * after its first integration, when the autotune option is set. Errors: CG_EINVAL,
+ * CG_ECUDA. */
 int cartogram_autotune(cg_ctx* ctx, int reps, int* shapes_out, double* ms_out);
 
 /* Velocity field from a caller's spectrum with no device allocation. The paper has no

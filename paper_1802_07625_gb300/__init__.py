@@ -22,7 +22,7 @@ __all__ = [
     "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_velocity_noalloc", "cartogram_last_error", "cartogram_destroy", "Cartogram",
 ]
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         "cartogram_area_errors": (i, [_P, _P]),
         "cartogram_get_vertices": (i, [_P, _P]),
         "cartogram_history_length": (i, [_P]),
+        "cartogram_fold_count": (i, [_P, i, ctypes.POINTER(ll), ctypes.POINTER(d)]),
         "cartogram_reset": (i, [_P]),
         "cartogram_autotune": (i, [_P, i, _P, _P]),
         "cartogram_profile": (i, [_P, i, _P]),
@@ -234,6 +235,12 @@ def cartogram_history_length(ctx) -> int:
     return load().cartogram_history_length(ctx)
 
 
+def cartogram_fold_count(ctx, k):
+    n, a = ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, load().cartogram_fold_count(ctx, int(k), ctypes.byref(n), ctypes.byref(a)))
+    return n.value, a.value
+
+
 def cartogram_get_grid(ctx, k, out):
     po, _ = _ptr(out, np.float64, writable=True)
     _check(ctx, load().cartogram_get_grid(ctx, int(k), po))
@@ -377,6 +384,9 @@ class Cartogram:
 
     def history_length(self):
         return cartogram_history_length(self.ctx)
+
+    def fold_count(self, k):
+        return cartogram_fold_count(self.ctx, k)
 
     def grid(self, k):
         return cartogram_get_grid(self.ctx, k, np.empty((self.Ly, self.Lx, 2)))

@@ -303,13 +303,16 @@ int do_autotune(cg_ctx* c, int reps) {
   enqueue_field<T>(c, cg::kModeFixed, t + h, (V2<T>*)c->vbuf[1], nullptr, nullptr, s);
   auto timeit = [&](auto&& launch, double* ms) -> int {
     launch();
-    CG_CUDA(c, cudaEventRecord(a, s));
-    for (int r = 0; r < reps; ++r) launch();
-    CG_CUDA(c, cudaEventRecord(b, s));
-    CG_CUDA(c, cudaEventSynchronize(b));
-    float f = 0.f;
-    CG_CUDA(c, cudaEventElapsedTime(&f, a, b));
-    *ms = f / reps;
+    *ms = 1e30;
+    for (int round = 0; round < 3; ++round) {
+      CG_CUDA(c, cudaEventRecord(a, s));
+      for (int r = 0; r < reps; ++r) launch();
+      CG_CUDA(c, cudaEventRecord(b, s));
+      CG_CUDA(c, cudaEventSynchronize(b));
+      float f = 0.f;
+      CG_CUDA(c, cudaEventElapsedTime(&f, a, b));
+      *ms = std::min(*ms, (double)f / reps);
+    }
     return CG_OK;
   };
   cg::Tune best = c->tune;
@@ -457,10 +460,6 @@ int run_integration(cg_ctx* c) {
     CG_CUDA(c, cudaEventRecord(c->ev1, s));
     return CG_OK;
   }
-  if (c->opt.autotune && !c->tuned) {
-    int r = do_autotune<T>(c, 10);
-    if (r) return r;
-  }
   if (c->opt.use_graph) {
     if (!c->exec) {
       int r = build_graph<T>(c);
@@ -557,6 +556,8 @@ int do_integrate(cg_ctx* c, cg_stats* stats) {
                     inf.accepted, inf.rejected);
       break;
     }
+    // pick the launch shapes once, on the displacements of a real integration
+    if (c->opt.autotune && !c->tuned && (r = do_autotune<T>(c, 10))) return r;
     if ((int)c->hist.size() <= c->hist_len) {
       void* p = nullptr;
       CG_CUDA(c, cudaMalloc(&p, fbytes));
@@ -982,12 +983,33 @@ int cartogram_profile(cg_ctx* c, int reps, double* ms_out) {
 int cartogram_autotune(cg_ctx* c, int reps, int* shapes_out, double* ms_out) {
   int r = check_ctx(c, false);
   if (r) return r;
-  if (reps < 1) return fail(c, CG_EINVAL, "reps must be positive");
-  r = c->mixed ? do_autotune<float>(c, reps) : do_autotune<double>(c, reps);
-  if (r) return r;
+  if (reps < 0) return fail(c, CG_EINVAL, "reps must not be negative");
+  if (reps > 0) {
+    r = c->mixed ? do_autotune<float>(c, reps) : do_autotune<double>(c, reps);
+    if (r) return r;
+  }
   const int shp[3] = {c->tune.rows, c->tune.cols, c->tune.heun_bps};
   if (shapes_out) CG_CUDA(c, cudaMemcpy(shapes_out, shp, sizeof shp, cudaMemcpyDefault));
   if (ms_out) CG_CUDA(c, cudaMemcpy(ms_out, c->tune_ms, sizeof c->tune_ms, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+int cartogram_fold_count(cg_ctx* c, int k, long long* n_folded, double* min_area) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (k < 0 || k >= c->hist_len) return fail(c, CG_EINVAL, "history entry %d out of range", k);
+  unsigned long long* d = (unsigned long long*)c->acc2;  // scratch: the persistent kernel's slots
+  if (c->mixed) cg::launch_fold_count<float>((const V2<float>*)c->hist[k], c->Lx, c->Ly, d, c->stream);
+  else cg::launch_fold_count<double>((const V2<double>*)c->hist[k], c->Lx, c->Ly, d, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  unsigned long long h[2];
+  CG_CUDA(c, cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  const unsigned long long b = (h[1] & 0x8000000000000000ull) ? (h[1] & 0x7fffffffffffffffull) : ~h[1];
+  double mn;
+  memcpy(&mn, &b, sizeof mn);
+  if (n_folded) *n_folded = (long long)h[0];
+  if (min_area) *min_area = mn;
   return CG_OK;
 }
 

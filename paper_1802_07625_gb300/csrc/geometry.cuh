@@ -216,3 +216,47 @@ __global__ void map_points_kernel(const double2* in, double2* out, long long n,
 }
 
 }  // namespace cg
+
+namespace cg {
+
+// Signed area of every quad of a projected grid (cell centres + displacements), as the
+// cross product of its two edges from the lower-left corner; counts the quads whose area
+// is not positive (folds) and the smallest area. out[0]: count (u64), out[1]: bits of the
+// smallest area mapped to an order-preserving unsigned key.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename T>
+__global__ void fold_kernel(const V2<T>* __restrict__ disp, int Lx, int Ly,
+                            unsigned long long* out) {
+  __shared__ unsigned long long s_cnt, s_min;
+  if (threadIdx.x == 0) {
+    s_cnt = 0ull;
+    s_min = ~0ull;
+  }
+  __syncthreads();
+  unsigned long long cnt = 0, mn = ~0ull;
+  const int nq = (Lx - 1) * (Ly - 1);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int i = q % (Lx - 1), j = q / (Lx - 1);
+    const int k = j * Lx + i;
+    const V2<T> d00 = disp[k], d10 = disp[k + 1], d01 = disp[k + Lx];
+    const double ax = 1.0 + (double)d10.x - (double)d00.x, ay = (double)d10.y - (double)d00.y;
+    const double bx = (double)d01.x - (double)d00.x, by = 1.0 + (double)d01.y - (double)d00.y;
+    const double area = ax * by - ay * bx;
+    if (!(area > 0.0)) ++cnt;
+    const unsigned long long key = order_key(area);
+    mn = key < mn ? key : mn;
+  }
+  atomicAdd(&s_cnt, cnt);
+  atomicMin(&s_min, mn);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&out[0], s_cnt);
+    atomicMin(&out[1], s_min);
+  }
+}
+
+}  // namespace cg

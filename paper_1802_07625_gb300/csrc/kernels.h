@@ -135,6 +135,8 @@ template <typename T>
 void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>* dst, int N,
                      cudaStream_t s);
 template <typename T>
+void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
+template <typename T>
 void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,
                        int Ly, cudaStream_t s);
 

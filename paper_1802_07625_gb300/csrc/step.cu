@@ -80,6 +80,13 @@ void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s) {
   collect_kernel<<<1, 1, 0, s>>>(st, info);
 }
 
+template <typename T>
+void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(out + 1, 0xff, sizeof(unsigned long long), s);
+  fold_kernel<T><<<blocks_for((long long)(Lx - 1) * (Ly - 1), 256, sm_count() * 4), 256, 0, s>>>(disp, Lx, Ly, out);
+}
+
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
                                V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
@@ -87,7 +94,8 @@ void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s) {
   template void launch_snapshot<T>(const DevState*, const V2<T>*, const V2<T>*, V2<T>*, int,        \
                                    cudaStream_t);                                                   \
   template void launch_map_points<T>(const double2*, double2*, long long, const V2<T>*, int, int,   \
-                                     cudaStream_t);
+                                     cudaStream_t);                                                 \
+  template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);
 CG_INSTANTIATE_STEP(float)
 CG_INSTANTIATE_STEP(double)
 
