@@ -145,6 +145,21 @@ def replica_throughput(world, updates, seconds):
     return _sum_over_ranks(world, float(updates)) / _max_over_ranks(world, float(seconds))
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None once the
+    sources of the step kernels differ from the ones that were profiled."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        h = hashlib.sha256()
+        for f in d["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_1802_07625_gb300", "csrc", f), "rb").read())
+        return d.get(kernel) if h.hexdigest() == d["source_sha256"] else None
+    except Exception:
+        return None
+
+
 def launches_per_cartogram(iterations, attempted):
     """Kernels the library launches for one cartogram_integrate call: initial areas (2);
     per iteration rasterise (2), forward transform (2), integration init (3: state,
@@ -298,13 +313,7 @@ def run_ours(args):
     dominant = max(step_ms, key=step_ms.get)
     peaks, peak_kind = _peaks()
     achieved = bpp[dominant] * m.Lx * m.Ly / (prof[dominant] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(dominant)
-        except Exception:
-            traffic = None
+    traffic = _traffic(dominant)
 
     # end to end through the C-ABI with host buffers: pinned host -> set_regions ->
     # integrate -> vertices back to pinned host
