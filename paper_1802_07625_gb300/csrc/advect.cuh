@@ -144,12 +144,13 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
                                                     cudaGraphConditionalHandle handle, int use_cond) {
   __shared__ unsigned long long s_err2;
   __shared__ unsigned int s_warps;
-  if (mode == kModeStep && st->status != kRunning) return;
   if (threadIdx.x == 0) {
     s_err2 = 0ull;
     s_warps = 0u;
   }
   __syncthreads();
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the fields of the previous kernel
+  if (mode == kModeStep && st->status != kRunning) return;
   const V2<T>* vcur = vbuf0;
   const V2<T>* vnew = vbuf1;
   const V2<T>* din = dbuf0;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
   }
   T e2 = heun_pairs<T>(vcur, vnew, din, dout, Lx, Ly, log2Lx, hd,
                        blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // Block reduction without a block-wide barrier: each warp folds its maximum into
   // shared memory; the last warp of the block to arrive publishes the block maximum
   // and takes the block's ticket; the last block runs the controller.

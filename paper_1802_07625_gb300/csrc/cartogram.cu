@@ -365,6 +365,8 @@ int do_autotune(cg_ctx* c, int reps) {
   return CG_OK;
 }
 
+constexpr int kGraphUnroll = 4;
+
 // One integration as a graph: init kernels, then a WHILE node whose body is one
 // attempted step (field at t+h, Heun step + controller); the controller clears the
 // condition when the integration ends.
@@ -402,7 +404,9 @@ int build_graph(cg_ctx* c) {
     cudaGraph_t body = cp.conditional.phGraph_out ? cp.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      enqueue_body<T>(c, h, 1, bs);
+      // several attempted steps per evaluation of the condition; the kernels of an
+      // attempt after the integration has ended return at once
+      for (int k = 0; k < kGraphUnroll; ++k) enqueue_body<T>(c, h, 1, bs);
       cudaGraph_t bg = nullptr;
       e = cudaStreamEndCapture(bs, &bg);
     }

@@ -97,6 +97,25 @@ inline LaunchCfg fwd_cols_cfg(int log2Ly, int Lx) {
   return c;
 }
 
+// Launch `kernel` with programmatic dependent launch allowed: it may start while the
+// previous kernel on the stream drains, and waits for it (griddepcontrol.wait) before
+// using its results.
+template <typename... P, typename... A>
+inline void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaStream_t s,
+                       A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // Allow the dynamic shared memory the spectral kernels of this grid need.
 template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);
 cudaError_t prepare_forward(int log2Lx, int log2Ly);

@@ -45,19 +45,31 @@ __host__ __device__ constexpr size_t p2_smem(int Wc) {
          (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(T) + 64 * sizeof(T);
 }
 
-// ---------------------------------------------------------------------------
-// pass 1 item: damped spectrum rows [n0, n0+S) -> (A, B), written transposed: ABt[i][n].
-// The tables and the S spectral rows arrive in shared memory by bulk asynchronous
-// copies on `bar` (phase `ph`, toggled here) while the damping factors are computed.
-// All threads of the block call it. Returns false if the copies did not complete.
-// shared: W[N] (inter-step twiddles) E[N] (C), stage[S*N] (T), buf[S*SSTRIDE] (C),
-// fx[N] fy[S] (T)
-// ---------------------------------------------------------------------------
+// Issue the bulk copies of a pass-1 item (thread 0): both tables and the S spectral rows,
+// none of which depend on the previous kernel of the step loop.
 template <typename T, int LOG2N>
-__device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
-                                        const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
-                                        int Ly, int S, int n0, double tau, unsigned char* smem,
-                                        uint64_t* bar, uint32_t& ph) {
+__device__ __forceinline__ void p1_issue(const T* __restrict__ spec, const V2<T>* __restrict__ Wg,
+                                         const V2<T>* __restrict__ Eg, int S, int n0,
+                                         unsigned char* smem, uint64_t* bar) {
+  using C = V2<T>;
+  constexpr int N = 1 << LOG2N;
+  C* W = reinterpret_cast<C*>(smem);
+  C* E = W + N;
+  T* stage = reinterpret_cast<T*>(E + N);
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + S * N * sizeof(T)));
+    bulk_g2s(W, Wg, N * sizeof(C), bar);
+    bulk_g2s(E, Eg, N * sizeof(C), bar);
+    for (int s = 0; s < S; ++s) bulk_g2s(stage + s * N, spec + (size_t)(n0 + s) * N, N * sizeof(T), bar);
+  }
+}
+
+// Rest of a pass-1 item once its copies are issued: damping at tau, packing, FFT,
+// transposed write. All threads call it; false if the copies did not complete.
+template <typename T, int LOG2N>
+__device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S, int n0, double tau,
+                                          unsigned char* smem, uint64_t* bar, uint32_t& ph) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;
@@ -67,14 +79,6 @@ __device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __res
   C* buf = reinterpret_cast<C*>(stage + S * N);
   T* fx = reinterpret_cast<T*>(buf + S * F::SSTRIDE);
   T* fyS = fx + N;
-  if (threadIdx.x == 0) {
-    // one transaction: both tables and the S spectral rows
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + S * N * sizeof(T)));
-    bulk_g2s(W, Wg, N * sizeof(C), bar);
-    bulk_g2s(E, Eg, N * sizeof(C), bar);
-    for (int s = 0; s < S; ++s) bulk_g2s(stage + s * N, spec + (size_t)(n0 + s) * N, N * sizeof(T), bar);
-  }
   const T kx = (T)(kPi * kPi * tau / ((double)N * N));
   const T ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
   for (int i = threadIdx.x; i < N; i += blockDim.x) fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
@@ -117,6 +121,20 @@ __device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __res
   return true;
 }
 
+// pass 1 item: damped spectrum rows [n0, n0+S) -> (A, B), written transposed: ABt[i][n].
+// The tables and the S spectral rows arrive in shared memory by bulk asynchronous
+// copies on `bar` (phase `ph`, toggled here) while the damping factors are computed.
+// shared: W[N] (inter-step twiddles) E[N] (C), stage[S*N] (T), buf[S*SSTRIDE] (C),
+// fx[N] fy[S] (T)
+template <typename T, int LOG2N>
+__device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
+                                        const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+                                        int Ly, int S, int n0, double tau, unsigned char* smem,
+                                        uint64_t* bar, uint32_t& ph) {
+  p1_issue<T, LOG2N>(spec, Wg, Eg, S, n0, smem, bar);
+  return p1_finish<T, LOG2N>(ABt, Ly, S, n0, tau, smem, bar, ph);
+}
+
 // Block-reduced results of a pass-2 item (valid in thread 0).
 template <typename T> struct FieldRed {
   T dev;    // max |rho/rho_bar - 1|
@@ -130,12 +148,44 @@ template <typename T> struct FieldRed {
 // are contiguous and arrive with the tables by bulk asynchronous copies.
 // shared: W[N] E[N] (C), stage[Wc*N] (C), buf[(Wc + Wc/2) * SSTRIDE] (C), red[64] (T)
 // ---------------------------------------------------------------------------
+// Pass-2 copies in two parts on one mbarrier phase (thread 0): the tables, which do not
+// depend on pass 1, and then the Wc columns of ABt that pass 1 wrote.
 template <typename T, int LOG2N>
-__device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __restrict__ out,
-                                        T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
-                                        const V2<T>* __restrict__ Eg, int Lx, int Wc, int c0,
-                                        unsigned char* smem, uint64_t* bar, uint32_t& ph,
-                                        FieldRed<T>& res) {
+__device__ __forceinline__ void p2_issue_tables(const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+                                                int Wc, unsigned char* smem, uint64_t* bar) {
+  using C = V2<T>;
+  constexpr int N = 1 << LOG2N;
+  C* W = reinterpret_cast<C*>(smem);
+  C* E = W + N;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (uint32_t)((2 + Wc) * N * sizeof(C)));
+    bulk_g2s(W, Wg, N * sizeof(C), bar);
+    bulk_g2s(E, Eg, N * sizeof(C), bar);
+  }
+}
+template <typename T, int LOG2N>
+__device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int Wc, int c0,
+                                              unsigned char* smem, uint64_t* bar) {
+  using C = V2<T>;
+  constexpr int N = 1 << LOG2N;
+  C* stage = reinterpret_cast<C*>(smem) + 2 * N;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    for (int cc = 0; cc < Wc; ++cc)
+      bulk_g2s(stage + cc * N, ABt + (size_t)(c0 + cc) * N, N * sizeof(C), bar);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2 item: (A, B) columns [c0, c0+Wc) -> velocity (Wc even): Wc signals for
+// (rho', d_y rho) and Wc/2 signals for d_x rho of column pairs, once the copies issued
+// by p2_issue_tables and p2_issue_cols have landed.
+// shared: W[N] E[N] (C), stage[Wc*N] (C), buf[(Wc + Wc/2) * SSTRIDE] (C), red[64] (T)
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2N>
+__device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict__ rho_out, int Lx,
+                                          int Wc, int c0, unsigned char* smem, uint64_t* bar,
+                                          uint32_t& ph, FieldRed<T>& res) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
@@ -144,14 +194,6 @@ __device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __
   C* stage = E + N;
   C* buf = stage + Wc * N;
   T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::SSTRIDE);
-  if (threadIdx.x == 0) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_expect_tx(bar, (uint32_t)((2 + Wc) * N * sizeof(C)));
-    bulk_g2s(W, Wg, N * sizeof(C), bar);
-    bulk_g2s(E, Eg, N * sizeof(C), bar);
-    for (int cc = 0; cc < Wc; ++cc)
-      bulk_g2s(stage + cc * N, ABt + (size_t)(c0 + cc) * N, N * sizeof(C), bar);
-  }
   const bool ok = mbar_wait_bounded(bar, ph, kMbarTries);
   ph ^= 1u;
   if (!__syncthreads_and(ok)) return false;
@@ -222,8 +264,26 @@ __device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __
   return true;
 }
 
+template <typename T, int LOG2N>
+__device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __restrict__ out,
+                                        T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
+                                        const V2<T>* __restrict__ Eg, int Lx, int Wc, int c0,
+                                        unsigned char* smem, uint64_t* bar, uint32_t& ph,
+                                        FieldRed<T>& res) {
+  p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem, bar);
+  p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem, bar);
+  return p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem, bar, ph, res);
+}
+
+// Programmatic dependent launch: let the next kernel of the step loop start its
+// independent prologue, and wait for the previous kernel before using its results.
+// Both are no-ops for a kernel launched without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
-// pass 1 as its own kernel. blockDim = S * N1, grid = Ly / S.
+// pass 1 as its own kernel. blockDim = S * N1, grid = Ly / S. The bulk copies of the
+// constant inputs (tables, spectral rows) start before waiting for the previous kernel.
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
 __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ ABt,
@@ -233,6 +293,10 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
                                 unsigned int max_body) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  p1_issue<T, LOG2N>(spec, Wg, Eg, S, blockIdx.x * S, smem_raw, &bar);
+  pdl_wait();
   double tau = tau_fixed;
   if (mode == kModeStep && blockIdx.x == 0 && threadIdx.x == 0) {
     // first kernel of a loop iteration: end the loop if the integration is over or
@@ -242,15 +306,16 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
   }
   if (mode != kModeFixed) {
-    if (st->status != kRunning) return;
+    if (st->status != kRunning) {
+      mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
+      return;
+    }
     tau = (mode == kModeInit) ? st->t : st->t + st->h;
   }
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
   uint32_t ph = 0;
-  if (!p1_rows<T, LOG2N>(spec, ABt, Wg, Eg, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) &&
-      threadIdx.x == 0)
+  if (!p1_finish<T, LOG2N>(ABt, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) && threadIdx.x == 0)
     st->bad = 2;
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -263,15 +328,22 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
                                 int mode) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (mode != kModeFixed && st->status != kRunning) return;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const int c0 = blockIdx.x * Wc;
+  p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem_raw, &bar);
+  pdl_wait();
+  p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem_raw, &bar);
+  if (mode != kModeFixed && st->status != kRunning) {
+    mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
+    return;
+  }
   V2<T>* out = vbuf0;
   if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
   uint32_t ph = 0;
   FieldRed<T> r;
-  if (!p2_cols<T, LOG2N>(ABt, out, rho_out, Wg, Eg, Lx, Wc, blockIdx.x * Wc, smem_raw, &bar, ph, r)) {
+  if (!p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r)) {
     if (threadIdx.x == 0) st->bad = 2;
     return;
   }
@@ -280,6 +352,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
     atomic_max_nonneg(&st->vmax2_bits, (double)r.v2max);
     if (r.bad) st->bad = 1;
   }
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------

@@ -60,9 +60,8 @@ void launch_inv_rows(int log2Lx, int Ly, int S, const T* spec, V2<T>* AB, const 
   switch (log2Lx) {
 #define CG_CASE(L)                                                                                \
   case L:                                                                                         \
-    inv_rows_kernel<T, L><<<c.grid, c.threads, c.smem, s>>>(spec, AB, W, E, Ly, c.per_block, st, \
-                                                             mode, tau, handle, use_cond,        \
-                                                             max_body);                          \
+    launch_pdl(inv_rows_kernel<T, L>, c.grid, c.threads, c.smem, s, spec, AB, W, E, Ly,        \
+               c.per_block, st, mode, tau, handle, use_cond, max_body);                          \
     break;
     CG_FOR_EACH_LOG2N(CG_CASE)
 #undef CG_CASE
@@ -78,8 +77,8 @@ void launch_inv_cols(int log2Ly, int Lx, int Wc, const V2<T>* AB, V2<T>* v0, V2<
   switch (log2Ly) {
 #define CG_CASE(L)                                                                              \
   case L:                                                                                       \
-    inv_cols_kernel<T, L><<<c.grid, c.threads, c.smem, s>>>(AB, v0, v1, rho_out, W, E, Lx,     \
-                                                             c.per_block, st, mode);           \
+    launch_pdl(inv_cols_kernel<T, L>, c.grid, c.threads, c.smem, s, AB, v0, v1, rho_out, W, E, \
+               Lx, c.per_block, st, mode);                                                      \
     break;
     CG_FOR_EACH_LOG2N(CG_CASE)
 #undef CG_CASE

@@ -32,8 +32,8 @@ void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T
   // number of same-address atomics of the block reductions small
   const int pairs = Lx * Ly / 2;
   if (blocks_per_sm <= 0) blocks_per_sm = 8;
-  heun_kernel<T><<<blocks_for(pairs, 256, sm_count() * blocks_per_sm), 256, 0, s>>>(
-      st, sp, v0, v1, d0, d1, Lx, Ly, log2Lx, mode, h, handle, use_cond);
+  launch_pdl(heun_kernel<T>, blocks_for(pairs, 256, sm_count() * blocks_per_sm), 256, 0, s, st, sp, v0,
+             v1, d0, d1, Lx, Ly, log2Lx, mode, h, handle, use_cond);
 }
 
 void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s) {
