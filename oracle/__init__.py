@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("dt0", ctypes.c_double), ("atol", ctypes.c_double), ("grow", ctypes.c_double),
                 ("shrink", ctypes.c_double), ("cfl", ctypes.c_double), ("rho_tol", ctypes.c_double),
                 ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("blur_decay", ctypes.c_double)]
+                ("blur_decay", ctypes.c_double), ("flow", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -57,14 +57,14 @@ class Stats(ctypes.Structure):
 # independently of the CUDA library's defaults; the parity tests pass the same
 # values to both sides explicitly.
 DEFAULTS = dict(dt0=1e-2, atol=1e-2, grow=1.2, shrink=0.5, cfl=1.0, rho_tol=1e-4,
-                area_tol=0.01, max_steps=4000, max_iter=50, blur_decay=0.5)
+                area_tol=0.01, max_steps=4000, max_iter=50, blur_decay=0.5, flow=0)
 
 
 def params(Lx, Ly, blur, **kw) -> Params:
     d = dict(DEFAULTS)
     d.update(kw)
     return Params(Lx, Ly, blur, d["dt0"], d["atol"], d["grow"], d["shrink"], d["cfl"],
-                  d["rho_tol"], d["area_tol"], d["max_steps"], d["max_iter"], d["blur_decay"])
+                  d["rho_tol"], d["area_tol"], d["max_steps"], d["max_iter"], d["blur_decay"], d["flow"])
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -94,6 +94,8 @@ def lib():
         L.orc_map_points.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_longlong, _D, _D]
         L.orc_cartogram.argtypes = [ctypes.POINTER(Params), ctypes.c_int, _D, ctypes.c_longlong, _LL, _I,
                                     ctypes.c_longlong, _D, _D, _D, ctypes.POINTER(Stats)]
+        L.orc_flux_linear.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
+        L.orc_integrate_linear.argtypes = [ctypes.POINTER(Params), _D, _D, _D, _LL, _LL, _D]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -190,6 +192,28 @@ def integrate(spec: np.ndarray, blur: float = 0.0, sched_cap: int = 20000, **kw)
                              ctypes.byref(t), _d(sh), sa.ctypes.data_as(_I), sched_cap)
     n = min(a.value + r.value, sched_cap)
     return IntegrateResult(X, Y, a.value, r.value, t.value, st, sh[:n], sa[:n])
+
+
+def flux_linear(spec: np.ndarray):
+    """Flux (Jx, Jy) of the linear-equalisation flow at the cell centres."""
+    spec = _f64(spec)
+    Ly, Lx = spec.shape
+    jx = np.empty_like(spec)
+    jy = np.empty_like(spec)
+    lib().orc_flux_linear(Lx, Ly, _d(spec), _d(jx), _d(jy))
+    return jx, jy
+
+
+def integrate_linear(spec: np.ndarray, blur: float = 0.0, **kw) -> IntegrateResult:
+    spec = _f64(spec)
+    Ly, Lx = spec.shape
+    P = params(Lx, Ly, blur, **kw)
+    X = np.empty((Ly, Lx))
+    Y = np.empty((Ly, Lx))
+    a, r, t = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    st = lib().orc_integrate_linear(ctypes.byref(P), _d(spec), _d(X), _d(Y), ctypes.byref(a), ctypes.byref(r),
+                                    ctypes.byref(t))
+    return IntegrateResult(X, Y, a.value, r.value, t.value, st, np.zeros(0), np.zeros(0, dtype=np.int32))
 
 
 def region_areas(n_regions, ring_offsets, ring_region, xy) -> np.ndarray:

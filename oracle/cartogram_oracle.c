@@ -31,6 +31,10 @@
  *                                 discretisation error only)
  *  orc_rasterize                  hand-computed coverages, total mass (pinned)
  *  orc_region_areas, orc_area_errors, orc_map_points   closed forms (pinned)
+ *  orc_flux_linear                single-mode and 2-D-mode closed forms, discrete
+ *                                 continuity against the density change (pinned)
+ *  orc_integrate_linear           x-only density -> closed-form 1-D map at t = 1 (pinned
+ *                                 to the discretisation error)
  *  orc_cartogram                  invariants only (strip map converges to the 1-D
  *                                 closed form); the exact 2-D result of a Voronoi map
  *                                 is not fixed by the paper: parity unpinned there.
@@ -58,6 +62,7 @@ typedef struct {
     int max_steps;     /* per integration (accepted + rejected) */
     int max_iter;      /* outer iterations */
     double blur_decay; /* iteration k blurs with width blur * blur_decay^k */
+    int flow;          /* 0: diffusion flow (SI Eq. fmn_diff); 1: linear equalisation (Eq. fmn_fast) */
 } orc_params;
 
 typedef struct {
@@ -371,6 +376,138 @@ int orc_integrate(const orc_params* P, const double* spec, double* X, double* Y,
     return status;
 }
 
+
+/* Flux of the linear-equalisation flow (SI Eq. fmn_fast, f_mn = 1 - t for t <= 1): with
+ * f'_mn = -1, SI Eqs. Jxmn and Jymn give the t-independent coefficients
+ *   Jx~_mn = m Lx Ly^2 rho~_mn / (pi (m^2 Ly^2 + n^2 Lx^2)),
+ *   Jy~_mn = n Lx^2 Ly rho~_mn / (pi (m^2 Ly^2 + n^2 Lx^2)),
+ * and SI Eqs. Jx, Jy the flux at the cell centres:
+ *   Jx = 1/(Lx Ly) sum_{m>=1,n>=0} Jx~_mn sin(pi m x/Lx) cos(pi n y/Ly),
+ *   Jy = 1/(Lx Ly) sum_{m>=0,n>=1} Jy~_mn cos(pi m x/Lx) sin(pi n y/Ly).
+ * (Main text Eqs. vx_cable, vy_cable print this velocity with a leading minus; the
+ * continuity equation with rho(t) = (1-t) rho0 + t rho_bar fixes the plus sign used here.)
+ * The double sums are evaluated as nested single sums. */
+void orc_flux_linear(int Lx, int Ly, const double* spec, double* jx, double* jy) {
+    double* Cx = cos_matrix(Lx);
+    double* Sx = sin_matrix(Lx);
+    double* Cy = cos_matrix(Ly);
+    double* Sy = sin_matrix(Ly);
+    double* ax = (double*)malloc(sizeof(double) * (size_t)Lx * Ly); /* Jx~[n][m] */
+    double* ay = (double*)malloc(sizeof(double) * (size_t)Lx * Ly); /* Jy~[n][m] */
+    for (int n = 0; n < Ly; ++n)
+        for (int m = 0; m < Lx; ++m) {
+            const double den = ORC_PI * ((double)m * m * Ly * Ly + (double)n * n * Lx * Lx);
+            const double r = spec[(size_t)n * Lx + m];
+            ax[(size_t)n * Lx + m] = (m == 0) ? 0.0 : m * (double)Lx * Ly * Ly * r / den;
+            ay[(size_t)n * Lx + m] = (n == 0) ? 0.0 : n * (double)Lx * Lx * Ly * r / den;
+        }
+    double* P = (double*)malloc(sizeof(double) * (size_t)Lx * Ly); /* sum_m Jx~ sin, [n][i] */
+    double* Q = (double*)malloc(sizeof(double) * (size_t)Lx * Ly); /* sum_m Jy~ cos, [n][i] */
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < Ly; ++n)
+        for (int i = 0; i < Lx; ++i) {
+            double p = 0.0, q = 0.0;
+            for (int m = 0; m < Lx; ++m) {
+                p += ax[(size_t)n * Lx + m] * Sx[(size_t)i * Lx + m];
+                q += ay[(size_t)n * Lx + m] * Cx[(size_t)i * Lx + m];
+            }
+            P[(size_t)n * Lx + i] = p;
+            Q[(size_t)n * Lx + i] = q;
+        }
+    const double norm = 1.0 / ((double)Lx * Ly);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < Ly; ++j) {
+        for (int i = 0; i < Lx; ++i) {
+            jx[(size_t)j * Lx + i] = 0.0;
+            jy[(size_t)j * Lx + i] = 0.0;
+        }
+        for (int n = 0; n < Ly; ++n) {
+            const double c = Cy[(size_t)j * Ly + n] * norm;
+            const double sn = Sy[(size_t)j * Ly + n] * norm;
+            for (int i = 0; i < Lx; ++i) {
+                jx[(size_t)j * Lx + i] += c * P[(size_t)n * Lx + i];
+                jy[(size_t)j * Lx + i] += sn * Q[(size_t)n * Lx + i];
+            }
+        }
+    }
+    free(Cx); free(Sx); free(Cy); free(Sy); free(ax); free(ay); free(P); free(Q);
+}
+
+/* Velocity of the linear flow at the grid points at time t (main text Eq. rho_ffb and
+ * the paragraph after it: v = J / rho with rho(t) = (1-t) rho0 + t rho_bar, t <= 1).
+ * Returns max |v|. */
+static double linear_velocity(int Lx, int Ly, const double* jx, const double* jy, const double* rho0,
+                              double rho_bar, double t, double* vx, double* vy) {
+    double vmax = 0.0;
+    for (size_t k = 0; k < (size_t)Lx * Ly; ++k) {
+        const double r = (1.0 - t) * rho0[k] + t * rho_bar;
+        vx[k] = jx[k] / r;
+        vy[k] = jy[k] / r;
+        const double a = sqrt(vx[k] * vx[k] + vy[k] * vy[k]);
+        if (a > vmax) vmax = a;
+    }
+    return vmax;
+}
+
+/* One integration of the linear flow from t = 0 to t = 1 (main text: "integrate Eq.
+ * rt_diff only until t = 1"), with the same adaptive predictor-corrector as
+ * orc_integrate: h <- min(h, cfl/max|v(t)|, 1 - t); accept if ||r' - r*|| <= atol; the
+ * integration ends with the accepted step that reaches t = 1. */
+int orc_integrate_linear(const orc_params* P, const double* spec, double* X, double* Y,
+                         long long* n_acc, long long* n_rej, double* t_end) {
+    const int Lx = P->Lx, Ly = P->Ly;
+    const size_t N = (size_t)Lx * Ly;
+    double* jx = (double*)malloc(sizeof(double) * N);
+    double* jy = (double*)malloc(sizeof(double) * N);
+    double* rho0 = (double*)malloc(sizeof(double) * N);
+    double* v0x = (double*)malloc(sizeof(double) * N);
+    double* v0y = (double*)malloc(sizeof(double) * N);
+    double* v1x = (double*)malloc(sizeof(double) * N);
+    double* v1y = (double*)malloc(sizeof(double) * N);
+    double* cx = (double*)malloc(sizeof(double) * N);
+    double* cy = (double*)malloc(sizeof(double) * N);
+    const double rho_bar = spec[0] / ((double)Lx * Ly);
+    orc_flux_linear(Lx, Ly, spec, jx, jy);
+    orc_fields(Lx, Ly, spec, 0.0, rho0, NULL, NULL);
+    for (int j = 0; j < Ly; ++j)
+        for (int i = 0; i < Lx; ++i) {
+            X[(size_t)j * Lx + i] = i + 0.5;
+            Y[(size_t)j * Lx + i] = j + 0.5;
+        }
+    double vmax = linear_velocity(Lx, Ly, jx, jy, rho0, rho_bar, 0.0, v0x, v0y);
+    long long acc = 0, rej = 0;
+    double t = 0.0, h = P->dt0;
+    int status = 0;
+    while (t < 1.0) {
+        if (acc + rej >= P->max_steps) { status = -6; break; }
+        if (vmax > 0.0 && h * vmax > P->cfl) h = P->cfl / vmax;
+        if (h > 1.0 - t) h = 1.0 - t;
+        const double t1 = (t + h >= 1.0) ? 1.0 : t + h;
+        const double vmax1 = linear_velocity(Lx, Ly, jx, jy, rho0, rho_bar, t1, v1x, v1y);
+        const double err = orc_heun_step(Lx, Ly, v0x, v0y, v1x, v1y, (long long)N, X, Y, t1 - t,
+                                         NULL, NULL, cx, cy);
+        if (err <= P->atol) {
+            memcpy(X, cx, sizeof(double) * N);
+            memcpy(Y, cy, sizeof(double) * N);
+            double* s;
+            s = v0x; v0x = v1x; v1x = s;
+            s = v0y; v0y = v1y; v1y = s;
+            vmax = vmax1;
+            t = t1;
+            ++acc;
+            h *= P->grow;
+        } else {
+            ++rej;
+            h *= P->shrink;
+        }
+    }
+    *n_acc = acc;
+    *n_rej = rej;
+    *t_end = t;
+    free(jx); free(jy); free(rho0); free(v0x); free(v0y); free(v1x); free(v1y); free(cx); free(cy);
+    return status;
+}
+
 /* Shoelace area of one ring (signed: counter-clockwise positive). */
 static double ring_area(const double* xy, long long a, long long b) {
     double s = 0.0;
@@ -557,7 +694,8 @@ int orc_cartogram(const orc_params* P, int n_regions, const double* values,
         orc_forward(Lx, Ly, rho, P->blur * pow(P->blur_decay, (double)it), spec);
         long long a, r;
         double tend;
-        int s = orc_integrate(P, spec, X, Y, &a, &r, &tend, NULL, NULL, 0);
+        int s = P->flow == 1 ? orc_integrate_linear(P, spec, X, Y, &a, &r, &tend)
+                             : orc_integrate(P, spec, X, Y, &a, &r, &tend, NULL, NULL, 0);
         st->steps_accepted += a;
         st->steps_rejected += r;
         st->t_end_last = tend;

@@ -456,3 +456,76 @@ def test_voronoi_map_converges(orc):
     A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, r.xy)
     err, mx = orc.area_errors(m.values, A)
     assert mx == pytest.approx(r.max_area_error)
+
+
+# --------------------------------------------------------------------------
+# the linear-equalisation flow (SI Eq. fmn_fast, f_mn = 1 - t)
+# --------------------------------------------------------------------------
+
+def test_linear_flux_single_mode_closed_form(orc):
+    # rho0 = 1 + a cos(pi x / Lx): J_x = (a Lx / pi) sin(pi x / Lx), J_y = 0, so that
+    # -d_x J_x = -a cos(pi x/Lx) = rho_bar - rho0 (continuity with rho(t) = (1-t) rho0 + t)
+    Ly, Lx, a = 8, 32, 0.4
+    x = np.arange(Lx) + 0.5
+    rho0 = (1 + a * np.cos(PI * x / Lx))[None, :] * np.ones((Ly, 1))
+    jx, jy = orc.flux_linear(orc.forward(rho0, 0.0))
+    assert np.max(np.abs(jx - (a * Lx / PI * np.sin(PI * x / Lx))[None, :])) < 1e-12
+    assert np.max(np.abs(jy)) < 1e-13
+
+
+def test_linear_flux_two_dimensional_mode(orc):
+    # one coefficient c at (m, n) = (2, 3): SI Eqs. Jxmn, Jymn with f' = -1 and Eqs. Jx, Jy
+    Ly, Lx, c = 12, 16, 5.0
+    spec = np.zeros((Ly, Lx))
+    spec[3, 2] = c
+    jx, jy = orc.flux_linear(spec)
+    x = np.arange(Lx) + 0.5
+    y = np.arange(Ly) + 0.5
+    den = PI * (4 * Ly ** 2 + 9 * Lx ** 2)
+    jxm = 2 * Lx * Ly ** 2 * c / den / (Lx * Ly)
+    jym = 3 * Lx ** 2 * Ly * c / den / (Lx * Ly)
+    assert np.max(np.abs(jx - jxm * np.cos(3 * PI * y / Ly)[:, None] * np.sin(2 * PI * x / Lx)[None, :])) < 1e-15
+    assert np.max(np.abs(jy - jym * np.sin(3 * PI * y / Ly)[:, None] * np.cos(2 * PI * x / Lx)[None, :])) < 1e-15
+
+
+def test_linear_flux_satisfies_continuity(orc):
+    # a smooth 2-D density: the central-difference divergence of J matches rho0 - rho_bar
+    # to the second-order truncation error of the differences
+    L = 64
+    x = np.arange(L) + 0.5
+    X, Y = np.meshgrid(x, x)
+    rho0 = 1 + 0.3 * np.cos(PI * X / L) * np.cos(2 * PI * Y / L) + 0.2 * np.cos(3 * PI * Y / L)
+    jx, jy = orc.flux_linear(orc.forward(rho0, 0.0))
+    div = (jx[1:-1, 2:] - jx[1:-1, :-2]) / 2 + (jy[2:, 1:-1] - jy[:-2, 1:-1]) / 2
+    err = np.max(np.abs(div - (rho0[1:-1, 1:-1] - rho0.mean())))
+    assert err < 0.01 and err > 0.0
+    # curl-free: d_y J_x = d_x J_y (SI Eq. novortex)
+    curl = (jx[2:, 1:-1] - jx[:-2, 1:-1]) / 2 - (jy[1:-1, 2:] - jy[1:-1, :-2]) / 2
+    assert np.max(np.abs(curl)) < 1e-3
+
+
+def test_linear_flow_reaches_one_dimensional_map_at_t_one(orc):
+    Ly, Lx, a = 8, 64, 0.5
+    x = np.arange(Lx) + 0.5
+    rho0 = (1 + a * np.cos(PI * x / Lx))[None, :] * np.ones((Ly, 1))
+    spec = orc.forward(rho0, 0.0)
+    exact = x + a * Lx / PI * np.sin(PI * x / Lx)
+    errs = []
+    for atol in (4e-2, 1e-2, 2.5e-3):
+        r = orc.integrate_linear(spec, atol=atol)
+        assert r.status == 0 and r.t_end == 1.0
+        # the n >= 1 coefficients of an x-only density are rounding noise
+        assert np.max(np.abs(r.Y - (np.arange(Ly) + 0.5)[:, None])) < 1e-12
+        errs.append(np.max(np.abs(r.X - exact[None, :])))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 0.03
+
+
+def test_linear_flow_strip_map_converges(orc):
+    Lx, Ly = 32, 16
+    V = [1.0, 3.0]
+    m = synth.strip_map(Lx, Ly, [0, 16, 32], V, spacing=1.0)
+    r = orc.cartogram(m, blur=0.0, flow=1)
+    assert r.converged and r.max_area_error < 0.01
+    mid = np.abs(m.xy[:, 0] - 16.0) < 1e-12
+    assert np.max(np.abs(r.xy[mid, 0] - Lx * V[0] / sum(V))) < 0.01 * Lx
