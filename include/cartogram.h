@@ -59,6 +59,14 @@ enum {
                                 the step-control arithmetic in FP64 */
 };
 
+enum {
+    CG_FLOW_DIFFUSION = 0,   /* diffusion flow, SI Eq. fmn_diff: the density at time t comes
+                                from the damped spectrum, two transform passes per step */
+    CG_FLOW_LINEAR = 1       /* linear equalisation, SI Eq. fmn_fast (the paper's method):
+                                rho(t) = (1 - t) rho0 + t rho_bar, a flux J = -grad Phi that is
+                                constant in time (SI Eqs. Jxmn, Jymn), integration to t = 1 */
+};
+
 /* Tuning of the method. cartogram_default_options() fills the defaults noted here. */
 typedef struct cg_options {
     int precision;      /* CG_PRECISION_FP64 (default) or CG_PRECISION_MIXED */
@@ -82,6 +90,9 @@ typedef struct cg_options {
                            iteration, 0: only the first integration is blurred */
     int autotune;       /* 1: time the candidate launch shapes of the step kernels on first
                            use and keep the fastest (default); 0: heuristic shapes */
+    int flow;           /* CG_FLOW_DIFFUSION (default) or CG_FLOW_LINEAR. With the linear flow
+                           dt0 is in units of its time t in [0, 1], every integration ends at
+                           t = 1, rho_tol is not used, and use_graph = 2 runs as 1 */
 } cg_options;
 
 typedef struct cg_stats {

@@ -19,7 +19,8 @@ from . import build as _build
 
 __all__ = [
     "CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_ENOCONVERGE", "CG_EFOLD", "CG_ESTEPFAIL", "CG_ETIMEOUT",
-    "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CartogramError", "Options", "Stats",
+    "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CG_FLOW_DIFFUSION",
+    "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
     "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
@@ -30,6 +31,7 @@ __all__ = [
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
 CG_ETIMEOUT, CG_ESTATE = -7, -8
 CG_PRECISION_FP64, CG_PRECISION_MIXED = 0, 1
+CG_FLOW_DIFFUSION, CG_FLOW_LINEAR = 0, 1
 
 _ERRNAMES = {0: "CG_OK", -1: "CG_EINVAL", -2: "CG_ENOMEM", -3: "CG_ECUDA", -4: "CG_ENOCONVERGE",
              -5: "CG_EFOLD", -6: "CG_ESTEPFAIL", -7: "CG_ETIMEOUT", -8: "CG_ESTATE"}
@@ -46,7 +48,7 @@ class Options(ctypes.Structure):
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("flow", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -321,9 +323,12 @@ class _Map:
 class Cartogram:
     """Owns one context; methods call the entry points above."""
 
-    def __init__(self, Lx, Ly, blur_width=0.0, precision="fp64", **options):
+    def __init__(self, Lx, Ly, blur_width=0.0, precision="fp64", flow="diffusion", **options):
         o = cartogram_default_options()
         o.precision = CG_PRECISION_MIXED if precision == "mixed" else CG_PRECISION_FP64
+        if flow not in ("diffusion", "linear"):
+            raise ValueError("flow must be 'diffusion' or 'linear'")
+        o.flow = CG_FLOW_LINEAR if flow == "linear" else CG_FLOW_DIFFUSION
         for k, v in options.items():
             if not hasattr(o, k):
                 raise TypeError("unknown option %s" % k)

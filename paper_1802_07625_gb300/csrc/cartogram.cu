@@ -48,6 +48,9 @@ struct cg_ctx {
   void* dbuf[2] = {nullptr, nullptr};
   void* dres = nullptr;      // displacements of the last integration
   void* rho_tmp = nullptr;   // density output of the field entry point
+  void* phi = nullptr;       // linear flow: Phi~ = rho~ / (pi^2 k^2) in the working type
+  void* flux = nullptr;      // linear flow: J = -grad Phi at the cell centres
+  void* rho0 = nullptr;      // linear flow: initial density at the cell centres
   DevState* st = nullptr;
   IterInfo* info = nullptr;
   IterInfo* info_h = nullptr;  // pinned
@@ -218,6 +221,11 @@ int alloc_fields(cg_ctx* c) {
   CG_CUDA(c, cudaMalloc(&c->dres, sizeof(V2<T>) * N));
   CG_CUDA(c, cudaMemset(c->dres, 0, sizeof(V2<T>) * N));
   CG_CUDA(c, cudaMalloc(&c->rho_tmp, sizeof(T) * N));
+  if (c->opt.flow == CG_FLOW_LINEAR) {
+    CG_CUDA(c, cudaMalloc(&c->phi, sizeof(T) * N));
+    CG_CUDA(c, cudaMalloc(&c->flux, sizeof(V2<T>) * N));
+    CG_CUDA(c, cudaMalloc(&c->rho0, sizeof(T) * N));
+  }
   CG_CUDA(c, cudaMalloc((void**)&c->st, sizeof(DevState)));
   CG_CUDA(c, cudaMemset(c->st, 0, sizeof(DevState)));
   CG_CUDA(c, cudaMalloc((void**)&c->info, sizeof(IterInfo)));
@@ -276,6 +284,34 @@ void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStr
   cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
                      (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeStep, 0.0, h,
                      use_cond, c->tune.heun_bps, s);
+}
+
+// Linear flow, once per integration: Phi~, the flux J = -grad Phi and rho0 at the cell
+// centres (transform passes at tau = 0), the speed at t = 0 and the first step.
+template <typename T>
+void enqueue_init_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const StepParams sp = step_params(c);
+  cg::launch_init_state(c->st, sp, s);
+  cudaMemsetAsync(c->dbuf[0], 0, sizeof(V2<T>) * (size_t)c->Lx * c->Ly, s);
+  cg::launch_phi_spectrum<T>(c->spec64, (T*)c->phi, c->Lx, c->Ly, s);
+  cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->phi, (V2<T>*)c->AB,
+                         (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFlux, 0.0, 0, 0, 0u, s);
+  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->flux, nullptr,
+                         nullptr, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFlux, s);
+  cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->specT, (V2<T>*)c->AB,
+                         (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFixed, 0.0, 0, 0, 0u, s);
+  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[0], nullptr,
+                         (T*)c->rho0, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
+  cudaMemsetAsync(&c->st->vmax2_bits, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(&c->st->dev_bits, 0, sizeof(unsigned long long), s);
+  cg::launch_linear_init<T>(c->st, sp, (const V2<T>*)c->flux, (const T*)c->rho0, c->Lx * c->Ly, h, use_cond, s);
+}
+
+template <typename T>
+void enqueue_body_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  cg::launch_linear_step<T>(c->st, step_params(c), (const V2<T>*)c->flux, (const T*)c->rho0,
+                            (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, h, use_cond,
+                            (unsigned int)c->opt.max_steps + 8u, c->tune.heun_bps, s);
 }
 
 template <typename T>
@@ -392,7 +428,8 @@ int build_graph(cg_ctx* c) {
       rc = fail(c, CG_ECUDA, "conditional handle: %s", cudaGetErrorString(e));
       break;
     }
-    enqueue_init<T>(c, h, 1, cs);
+    if (c->opt.flow == CG_FLOW_LINEAR) enqueue_init_linear<T>(c, h, 1, cs);
+    else enqueue_init<T>(c, h, 1, cs);
     e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = h;
@@ -406,7 +443,10 @@ int build_graph(cg_ctx* c) {
     if (e == cudaSuccess) {
       // several attempted steps per evaluation of the condition; the kernels of an
       // attempt after the integration has ended return at once
-      for (int k = 0; k < kGraphUnroll; ++k) enqueue_body<T>(c, h, 1, bs);
+      for (int k = 0; k < kGraphUnroll; ++k) {
+        if (c->opt.flow == CG_FLOW_LINEAR) enqueue_body_linear<T>(c, h, 1, bs);
+        else enqueue_body<T>(c, h, 1, bs);
+      }
       cudaGraph_t bg = nullptr;
       e = cudaStreamEndCapture(bs, &bg);
     }
@@ -432,7 +472,7 @@ int build_graph(cg_ctx* c) {
 template <typename T>
 int run_integration(cg_ctx* c) {
   cudaStream_t s = c->stream;
-  if (c->opt.use_graph == 2 && c->persist_grid > 0) {
+  if (c->opt.use_graph == 2 && c->persist_grid > 0 && c->opt.flow == CG_FLOW_DIFFUSION) {
     cg::IntegrateArgs<T> a;
     a.spec = (const T*)c->specT;
     a.ABt = (V2<T>*)c->AB;
@@ -476,10 +516,15 @@ int run_integration(cg_ctx* c) {
   }
   // host-driven loop: the same kernels; the kernels return at once after the end
   CG_CUDA(c, cudaEventRecord(c->ev0, s));
-  enqueue_init<T>(c, 0, 0, s);
+  const bool lin = c->opt.flow == CG_FLOW_LINEAR;
+  if (lin) enqueue_init_linear<T>(c, 0, 0, s);
+  else enqueue_init<T>(c, 0, 0, s);
   const int chunk = 8;
   for (long long done = 0; done < (long long)c->opt.max_steps + chunk; done += chunk) {
-    for (int k = 0; k < chunk; ++k) enqueue_body<T>(c, 0, 0, s);
+    for (int k = 0; k < chunk; ++k) {
+      if (lin) enqueue_body_linear<T>(c, 0, 0, s);
+      else enqueue_body<T>(c, 0, 0, s);
+    }
     cg::launch_collect(c->st, c->info, s);
     CG_CUDA(c, cudaMemcpyAsync(c->info_h, c->info, sizeof(IterInfo), cudaMemcpyDeviceToHost, s));
     CG_CUDA(c, cudaStreamSynchronize(s));
@@ -805,6 +850,7 @@ int cartogram_default_options(cg_options* o) {
   o->use_graph = 1;
   o->blur_decay = 0.5;
   o->autotune = 1;
+  o->flow = CG_FLOW_DIFFUSION;
   return CG_OK;
 }
 
@@ -818,6 +864,7 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   if (opt) o = *opt;
   if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED) return CG_EINVAL;
   if (o.use_graph < 0 || o.use_graph > 2) return CG_EINVAL;
+  if (o.flow != CG_FLOW_DIFFUSION && o.flow != CG_FLOW_LINEAR) return CG_EINVAL;
   if (!(o.dt0 > 0) || !(o.atol > 0) || !(o.grow >= 1.0) || !(o.shrink > 0 && o.shrink < 1) ||
       !(o.cfl > 0) || !(o.rho_tol > 0) || !(o.area_tol > 0) || o.max_steps < 1 || o.max_iter < 0 ||
       !is_finite(o.dt0) || !is_finite(o.atol) || !is_finite(o.grow) || !is_finite(o.cfl) || !is_finite(o.rho_tol) ||
@@ -1096,7 +1143,8 @@ void cartogram_destroy(cg_ctx* c) {
   free_regions(c);
   void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
-                c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2};
+                c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
+                c->rho0};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);

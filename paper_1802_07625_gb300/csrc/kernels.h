@@ -154,6 +154,15 @@ template <typename T>
 void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>* dst, int N,
                      cudaStream_t s);
 template <typename T>
+void launch_phi_spectrum(const double* spec, T* phi, int Lx, int Ly, cudaStream_t s);
+template <typename T>
+void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, int N,
+                        cudaGraphConditionalHandle handle, int use_cond, cudaStream_t s);
+template <typename T>
+void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* d0,
+                        V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle, int use_cond,
+                        unsigned int max_body, int blocks_per_sm, cudaStream_t s);
+template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>
 void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,

@@ -185,7 +185,7 @@ __device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int
 template <typename T, int LOG2N>
 __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict__ rho_out, int Lx,
                                           int Wc, int c0, unsigned char* smem, uint64_t* bar,
-                                          uint32_t& ph, FieldRed<T>& res) {
+                                          uint32_t& ph, FieldRed<T>& res, bool raw = false) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
@@ -248,8 +248,8 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     const T gy = (j & 1) ? -u1.y : u1.y;
     const T gx = (cc & 1) ? u2.y : u2.x;
     const T rho = T(1) + rp;
-    bad |= !(rho > T(0));
-    const T inv = T(1) / rho;
+    if (!raw) bad |= !(rho > T(0));
+    const T inv = raw ? T(1) : T(1) / rho;
     const T vx = -gx * inv, vy = -gy * inv;
     const size_t o = (size_t)j * Lx + c0 + cc;
     out[o] = mk2<T>(vx, vy);
@@ -305,7 +305,7 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
     if (st->status == kRunning && it > max_body) st->status = kStepFail;
     if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
   }
-  if (mode != kModeFixed) {
+  if (mode == kModeInit || mode == kModeStep) {
     if (st->status != kRunning) {
       mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
       return;
@@ -334,7 +334,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
   p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem_raw, &bar);
   pdl_wait();
   p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem_raw, &bar);
-  if (mode != kModeFixed && st->status != kRunning) {
+  if ((mode == kModeInit || mode == kModeStep) && st->status != kRunning) {
     mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
     return;
   }
@@ -343,7 +343,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
   uint32_t ph = 0;
   FieldRed<T> r;
-  if (!p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r)) {
+  if (!p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux)) {
     if (threadIdx.x == 0) st->bad = 2;
     return;
   }

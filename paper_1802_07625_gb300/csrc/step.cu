@@ -1,6 +1,7 @@
 // Instantiation of the advection, step-control and geometry kernels.
 #include "advect.cuh"
 #include "geometry.cuh"
+#include "linear.cuh"
 #include "kernels.h"
 
 namespace cg {
@@ -87,6 +88,29 @@ void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* ou
   fold_kernel<T><<<blocks_for((long long)(Lx - 1) * (Ly - 1), 256, sm_count() * 4), 256, 0, s>>>(disp, Lx, Ly, out);
 }
 
+template <typename T>
+void launch_phi_spectrum(const double* spec, T* phi, int Lx, int Ly, cudaStream_t s) {
+  phi_spectrum_kernel<T><<<blocks_for((long long)Lx * Ly, 256, 4096), 256, 0, s>>>(spec, phi, Lx, Ly);
+}
+
+template <typename T>
+void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, int N,
+                        cudaGraphConditionalHandle handle, int use_cond, cudaStream_t s) {
+  linear_vmax_kernel<T><<<blocks_for(N, 256, sm_count() * 4), 256, 0, s>>>(st, J, rho0, N);
+  linear_init_finish_kernel<<<1, 1, 0, s>>>(st, sp, handle, use_cond);
+}
+
+template <typename T>
+void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* d0,
+                        V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle, int use_cond,
+                        unsigned int max_body, int blocks_per_sm, cudaStream_t s) {
+  int log2Lx = 0;
+  while ((1 << log2Lx) < Lx) ++log2Lx;
+  if (blocks_per_sm <= 0) blocks_per_sm = 8;
+  launch_pdl(linear_step_kernel<T>, blocks_for((long long)Lx * Ly / 2, 256, sm_count() * blocks_per_sm), 256, 0,
+             s, st, sp, J, rho0, d0, d1, Lx, Ly, log2Lx, handle, use_cond, max_body);
+}
+
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
                                V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
@@ -95,7 +119,13 @@ void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* ou
                                    cudaStream_t);                                                   \
   template void launch_map_points<T>(const double2*, double2*, long long, const V2<T>*, int, int,   \
                                      cudaStream_t);                                                 \
-  template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);
+  template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);   \
+  template void launch_phi_spectrum<T>(const double*, T*, int, int, cudaStream_t);                  \
+  template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, int,    \
+                                      cudaGraphConditionalHandle, int, cudaStream_t);               \
+  template void launch_linear_step<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
+                                      V2<T>*, int, int, cudaGraphConditionalHandle, int,            \
+                                      unsigned int, int, cudaStream_t);
 CG_INSTANTIATE_STEP(float)
 CG_INSTANTIATE_STEP(double)
 

@@ -44,6 +44,34 @@ def test_default_options_without_gpu():
     assert o.dt0 == 1e-2 and o.atol == 1e-2 and o.grow == 1.2 and o.shrink == 0.5
     assert o.cfl == 1.0 and o.rho_tol == 1e-4 and o.area_tol == 0.01
     assert o.max_steps == 4000 and o.max_iter == 50 and o.use_graph == 1 and o.blur_decay == 0.5 and o.autotune == 1
+    assert o.flow == P.CG_FLOW_DIFFUSION
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # compile a probe against the header and compare every field offset and the sizes
+    import ctypes
+    import shutil
+    import subprocess
+
+    import paper_1802_07625_gb300 as P
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = []
+    for struct, cls in (("cg_options", P.Options), ("cg_stats", P.Stats)):
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (struct, struct))
+        for name, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (struct, name, struct, name))
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "cartogram.h"\nint main(void) {\n' +
+                   "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for struct, cls in (("cg_options", P.Options), ("cg_stats", P.Stats)):
+        assert got[(struct, "sizeof")] == ctypes.sizeof(cls), struct
+        for name, _ in cls._fields_:
+            assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)
 
 
 def test_init_rejects_bad_sizes_before_touching_the_gpu():
@@ -54,6 +82,11 @@ def test_init_rejects_bad_sizes_before_touching_the_gpu():
         assert e.value.code == P.CG_EINVAL
     with pytest.raises(P.CartogramError) as e:
         P.cartogram_init(64, 64, -1.0)
+    assert e.value.code == P.CG_EINVAL
+    o = P.cartogram_default_options()
+    o.flow = 2
+    with pytest.raises(P.CartogramError) as e:
+        P.cartogram_init(64, 64, 1.0, o)
     assert e.value.code == P.CG_EINVAL
 
 
