@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "powerlaw3000_1024"
 METRIC = "RK2 grid-point updates/s (converged 1024^2 cartogram, mixed precision)"
 UNIT = "updates/s"
+# The linear-equalisation flow (SI Eq. fmn_fast) keeps the initial density structure in
+# v = J / rho(t) until t = 1, so on this map it needs a wider first blur than the diffusion
+# flow: at 2 cells its first integration folds the grid, at 64 it converges without folds.
+LINEAR_BLUR = 64.0
 
 
 def _peaks():
@@ -360,6 +364,43 @@ def run_ours(args):
                 "max_area_error": fs.max_area_error}
         f.close()
 
+    # the paper's linear-equalisation flow on the same workload (one transform pair per
+    # integration, one fused kernel per attempted step)
+    linear = None
+    if args.linear_steps > 0:
+        lc = P.Cartogram(m.Lx, m.Ly, LINEAR_BLUR, precision="mixed", flow="linear", max_iter=100)
+        lc.set_stream(stream)
+        P.cartogram_set_regions(lc.ctx, d_vals, d_off, d_reg, d_xy)
+        lc._map = P._Map(m.n_regions, m.n_vertices)
+        try:
+            lc.reset()
+            lc.integrate()
+            torch.cuda.synchronize()
+            lms, latt, lloop = 0.0, 0, 0.0
+            for _ in range(args.linear_steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                lc.reset()
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                a.record(stream)
+                ls = lc.integrate()
+                b.record(stream)
+                torch.cuda.synchronize()
+                lms += a.elapsed_time(b)
+                latt += ls.steps_accepted + ls.steps_rejected
+                lloop += ls.step_loop_ms
+            linear = {"flow": "linear equalisation (SI Eq. fmn_fast)", "precision": "mixed", "blur": LINEAR_BLUR,
+                      "note": "first integration blurred over %g cells (halved each iteration): at %g cells the "
+                              "linear flow folds this map's grid in its first integration" % (LINEAR_BLUR, blur),
+                      "updates_per_s": latt * m.Lx * m.Ly / (lms / 1e3),
+                      "s_per_cartogram": lms / 1e3 / args.linear_steps, "iterations": ls.iterations,
+                      "attempted_steps": ls.steps_accepted + ls.steps_rejected,
+                      "max_area_error": ls.max_area_error,
+                      "us_per_attempted_step": lloop * 1e3 / max(1, latt)}
+        except P.CartogramError as e:
+            linear = {"flow": "linear equalisation (SI Eq. fmn_fast)", "error": str(e)}
+        lc.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, blur, args.cpu_steps)
@@ -383,6 +424,7 @@ def run_ours(args):
             "accepted_updates_per_s": value * last.steps_accepted / max(1, last.steps_accepted + last.steps_rejected),
             "fp64_gpu": fp64,
             "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
+            "linear_flow": linear,
             "kernel_ms": prof,
             "launch_shapes": tune,
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -413,6 +455,8 @@ def main():
     ap.add_argument("--ref-attempts", type=int, default=20,
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--linear-steps", type=int, default=2,
+                    help="converged cartograms timed with the linear-equalisation flow (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--loop-mode", type=int, default=1, choices=[1, 2],
                     help="2: persistent cooperative kernel per integration; 1: conditional CUDA graph")

@@ -79,7 +79,10 @@ typedef struct cg_options {
                            max |rho - rho_bar| / rho_bar <= rho_tol (1e-4) */
     double area_tol;    /* outer iterations end when max |A_i/A^_i - 1| < area_tol (0.01) */
     int max_steps;      /* attempted steps per integration before CG_ESTEPFAIL (4000) */
-    int max_iter;       /* outer iterations before CG_ENOCONVERGE (50) */
+    int max_iter;       /* outer iterations before CG_ENOCONVERGE (500). Regions whose target
+                           is about one cell wide shrink by a few percent per iteration once
+                           the grid stops resolving them: the 512^2 clustered map with
+                           lognormal(1.5) values needs about 190 */
     int use_graph;      /* how an integration's step loop runs: 1 (default) one CUDA-graph
                            launch whose conditional WHILE node repeats the per-phase kernels;
                            2 one persistent cooperative kernel whose phases meet at grid

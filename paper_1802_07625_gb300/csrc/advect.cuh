@@ -97,6 +97,48 @@ __device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
   if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
 }
 
+// End of the attempted step t -> t1 of the linear-equalisation flow (the step that
+// reaches t = 1 ends exactly there).
+__device__ __forceinline__ double linear_t1(double t, double h) { return (t + h >= 1.0) ? 1.0 : t + h; }
+
+// Controller of the linear-equalisation flow: accept / reject as above, the next step
+// capped by cfl / max|v| and by 1 - t; done once an accepted step reaches t = 1.
+__device__ __forceinline__ void control_linear(DevState* st, const StepParams& sp,
+                                               cudaGraphConditionalHandle handle, int use_cond) {
+  const double e = sqrt(__longlong_as_double((long long)st->err2_bits));
+  const double vmax_new = sqrt(__longlong_as_double((long long)st->vmax2_bits));
+  int status = kRunning;
+  double h = st->h;
+  if (st->bad) {
+    status = kStepFail;
+  } else if (e <= sp.atol) {
+    st->parity ^= 1;
+    st->t = linear_t1(st->t, h);
+    st->accepted += 1;
+    st->vmax = vmax_new;
+    if (st->t >= 1.0) status = kDone;
+    else h *= sp.grow;
+  } else {
+    st->rejected += 1;
+    h *= sp.shrink;
+  }
+  if (status == kRunning) {
+    if (st->accepted + st->rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
+    else {
+      if (st->vmax > 0.0 && h * st->vmax > sp.cfl) h = sp.cfl / st->vmax;
+      if (h > 1.0 - st->t) h = 1.0 - st->t;
+    }
+  }
+  st->h = h;
+  st->status = status;
+  st->err2_bits = 0;
+  st->vmax2_bits = 0;
+  st->dev_bits = 0;
+  st->ticket = 0;
+  st->bad = 0;
+  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+}
+
 // Heun step of the point pairs q = q0, q0 + qstride, ... (two horizontally adjacent
 // points per pair, Lx even); returns this thread's max ||r_corr - r_pred||^2.
 template <typename T>
@@ -133,9 +175,11 @@ __device__ __forceinline__ T heun_pairs(const V2<T>* __restrict__ vcur, const V2
   return e2;
 }
 
-// One Heun step of every grid point. Step mode: buffers by parity, h from the state,
-// and the last block to finish runs the controller. Fixed mode (single step on
-// explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0, dout = dbuf1, step h.
+// One Heun step of every grid point. Step modes: buffers by parity, h from the state,
+// and the last block to finish runs the controller (kModeStep: diffusion flow;
+// kModeLinear: linear-equalisation flow, the attempt ending at min(t + h, 1)). Fixed
+// mode (single step on explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0,
+// dout = dbuf1, step h.
 template <typename T>
 __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
                                                     const V2<T>* vbuf0, const V2<T>* vbuf1,
@@ -150,19 +194,20 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
   }
   __syncthreads();
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the fields of the previous kernel
-  if (mode == kModeStep && st->status != kRunning) return;
+  const bool step = mode == kModeStep || mode == kModeLinear;
+  if (step && st->status != kRunning) return;
   const V2<T>* vcur = vbuf0;
   const V2<T>* vnew = vbuf1;
   const V2<T>* din = dbuf0;
   V2<T>* dout = dbuf1;
   double hd = h_fixed;
-  if (mode == kModeStep) {
+  if (step) {
     const int par = st->parity;
     vcur = par ? vbuf1 : vbuf0;
     vnew = par ? vbuf0 : vbuf1;
     din = par ? dbuf1 : dbuf0;
     dout = par ? dbuf0 : dbuf1;
-    hd = st->h;
+    hd = mode == kModeLinear ? linear_t1(st->t, st->h) - st->t : st->h;
   }
   T e2 = heun_pairs<T>(vcur, vnew, din, dout, Lx, Ly, log2Lx, hd,
                        blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -179,12 +224,13 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
       __threadfence_block();
       const double bm = __longlong_as_double((long long)atomicOr(&s_err2, 0ull));
       atomic_max_nonneg(&st->err2_bits, bm);
-      if (mode == kModeStep) {
+      if (step) {
         __threadfence();
         const unsigned int t = atomicAdd(&st->ticket, 1u);
         if (t == gridDim.x - 1) {
           __threadfence();
-          control_step(st, sp, handle, use_cond);
+          if (mode == kModeLinear) control_linear(st, sp, handle, use_cond);
+          else control_step(st, sp, handle, use_cond);
         }
       }
     }

@@ -304,14 +304,15 @@ void enqueue_init_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, 
                          (T*)c->rho0, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
   cudaMemsetAsync(&c->st->vmax2_bits, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&c->st->dev_bits, 0, sizeof(unsigned long long), s);
-  cg::launch_linear_init<T>(c->st, sp, (const V2<T>*)c->flux, (const T*)c->rho0, c->Lx * c->Ly, h, use_cond, s);
+  cg::launch_linear_init<T>(c->st, sp, (const V2<T>*)c->flux, (const T*)c->rho0, (V2<T>*)c->vbuf[0],
+                            c->Lx * c->Ly, h, use_cond, s);
 }
 
 template <typename T>
 void enqueue_body_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   cg::launch_linear_step<T>(c->st, step_params(c), (const V2<T>*)c->flux, (const T*)c->rho0,
-                            (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, h, use_cond,
-                            (unsigned int)c->opt.max_steps + 8u, c->tune.heun_bps, s);
+                            (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1],
+                            c->Lx, c->Ly, h, use_cond, (unsigned int)c->opt.max_steps + 8u, c->tune.heun_bps, s);
 }
 
 template <typename T>
@@ -354,9 +355,11 @@ int do_autotune(cg_ctx* c, int reps) {
   cg::Tune best = c->tune;
   double best_ms[3] = {1e30, 1e30, 1e30};
   int r;
+  int rows_max = 0, cols_max = 0;
+  CG_CUDA(c, cg::spectral_max_threads<T>(c->log2Lx, c->log2Ly, &rows_max, &cols_max));
   for (int S = 1; S <= 16 && S <= c->Ly; S *= 2) {
     const cg::LaunchCfg k = cg::inv_rows_cfg(c->log2Lx, c->Ly, esz, S);
-    if (k.smem > 227 * 1024 || k.threads > 1024) continue;
+    if (k.smem > 227 * 1024 || k.threads > rows_max) continue;
     double ms;
     if ((r = timeit([&] {
            cg::launch_inv_rows<T>(c->log2Lx, c->Ly, S, (const T*)c->specT, (V2<T>*)c->AB,
@@ -368,7 +371,7 @@ int do_autotune(cg_ctx* c, int reps) {
   }
   for (int W = 2; W <= 16 && W <= c->Lx; W *= 2) {
     const cg::LaunchCfg k = cg::inv_cols_cfg(c->log2Ly, c->Lx, esz, W);
-    if (k.smem > 227 * 1024 || k.threads > 1024) continue;
+    if (k.smem > 227 * 1024 || k.threads > cols_max) continue;
     double ms;
     if ((r = timeit([&] {
            cg::launch_inv_cols<T>(c->log2Ly, c->Lx, W, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr,
@@ -846,7 +849,7 @@ int cartogram_default_options(cg_options* o) {
   o->rho_tol = 1e-4;
   o->area_tol = 0.01;
   o->max_steps = 4000;
-  o->max_iter = 50;
+  o->max_iter = 500;
   o->use_graph = 1;
   o->blur_decay = 0.5;
   o->autotune = 1;

@@ -47,9 +47,11 @@ struct DevState {
 };
 // What a field or step kernel works on: the field at t (start of an integration),
 // the attempt at t + h inside the step loop, or explicit buffers and times.
-enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2, kModeFlux = 3 };
+enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2, kModeFlux = 3, kModeLinear = 4 };
 // kModeFlux: explicit buffers like kModeFixed, and pass 2 writes -grad instead of the
 // velocity (the flux J = -grad Phi of the linear-equalisation flow).
+// kModeLinear: a step-loop attempt of the linear-equalisation flow (buffers by parity,
+// the attempt ends at min(t + h, 1), its own controller).
 
 constexpr int kRunning = 0;
 constexpr int kDone = 1;

@@ -118,6 +118,8 @@ inline void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem,
 
 // Allow the dynamic shared memory the spectral kernels of this grid need.
 template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);
+// Largest block size the inverse passes of this grid can launch with.
+template <typename T> cudaError_t spectral_max_threads(int log2Lx, int log2Ly, int* rows_max, int* cols_max);
 cudaError_t prepare_forward(int log2Lx, int log2Ly);
 
 template <typename T>
@@ -155,13 +157,16 @@ void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>
                      cudaStream_t s);
 template <typename T>
 void launch_phi_spectrum(const double* spec, T* phi, int Lx, int Ly, cudaStream_t s);
+// Linear-equalisation flow: the velocity at t = 0 at the grid points (into v0) and the
+// first step; one attempted step (the velocity at its end, then the predictor-corrector
+// step of all points with the linear flow's controller).
 template <typename T>
-void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, int N,
+void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0, int N,
                         cudaGraphConditionalHandle handle, int use_cond, cudaStream_t s);
 template <typename T>
-void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* d0,
-                        V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle, int use_cond,
-                        unsigned int max_body, int blocks_per_sm, cudaStream_t s);
+void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0,
+                        V2<T>* v1, V2<T>* d0, V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle,
+                        int use_cond, unsigned int max_body, int blocks_per_sm, cudaStream_t s);
 template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>

@@ -52,6 +52,37 @@ cudaError_t prepare_spectral(int log2Lx, int log2Ly) {
 }
 
 template <typename T>
+cudaError_t spectral_max_threads(int log2Lx, int log2Ly, int* rows_max, int* cols_max) {
+  // the largest block each inverse pass can launch with (its registers per thread decide)
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (log2Lx) {
+#define CG_CASE(L)                                                       \
+  case L:                                                                \
+    e = cudaFuncGetAttributes(&fa, (const void*)inv_rows_kernel<T, L>); \
+    break;
+    CG_FOR_EACH_LOG2N(CG_CASE)
+#undef CG_CASE
+    default: break;
+  }
+  if (e != cudaSuccess) return e;
+  *rows_max = fa.maxThreadsPerBlock;
+  e = cudaErrorInvalidValue;
+  switch (log2Ly) {
+#define CG_CASE(L)                                                       \
+  case L:                                                                \
+    e = cudaFuncGetAttributes(&fa, (const void*)inv_cols_kernel<T, L>); \
+    break;
+    CG_FOR_EACH_LOG2N(CG_CASE)
+#undef CG_CASE
+    default: break;
+  }
+  if (e != cudaSuccess) return e;
+  *cols_max = fa.maxThreadsPerBlock;
+  return cudaSuccess;
+}
+
+template <typename T>
 void launch_inv_rows(int log2Lx, int Ly, int S, const T* spec, V2<T>* AB, const V2<T>* W,
                      const V2<T>* E, DevState* st, int mode, double tau,
                      cudaGraphConditionalHandle handle, int use_cond, unsigned int max_body,
@@ -107,6 +138,7 @@ void launch_fwd(int log2Lx, int log2Ly, const double* rho, double* R, double* sp
 
 #define CG_INSTANTIATE_SPECTRAL(T)                                                                 \
   template cudaError_t prepare_spectral<T>(int, int);                                              \
+  template cudaError_t spectral_max_threads<T>(int, int, int*, int*);                              \
   template void launch_inv_rows<T>(int, int, int, const T*, V2<T>*, const V2<T>*, const V2<T>*,   \
                                    DevState*, int, double, cudaGraphConditionalHandle, int,        \
                                    unsigned int, cudaStream_t);                                    \

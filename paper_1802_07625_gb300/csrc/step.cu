@@ -94,21 +94,21 @@ void launch_phi_spectrum(const double* spec, T* phi, int Lx, int Ly, cudaStream_
 }
 
 template <typename T>
-void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, int N,
+void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0, int N,
                         cudaGraphConditionalHandle handle, int use_cond, cudaStream_t s) {
-  linear_vmax_kernel<T><<<blocks_for(N, 256, sm_count() * 4), 256, 0, s>>>(st, J, rho0, N);
+  launch_pdl(linear_velocity_kernel<T>, blocks_for(N, 256, sm_count() * 8), 256, 0, s, st, J, rho0, v0,
+             (V2<T>*)nullptr, N, (int)kModeInit, handle, use_cond, 0u);
   linear_init_finish_kernel<<<1, 1, 0, s>>>(st, sp, handle, use_cond);
 }
 
 template <typename T>
-void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* d0,
-                        V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle, int use_cond,
-                        unsigned int max_body, int blocks_per_sm, cudaStream_t s) {
-  int log2Lx = 0;
-  while ((1 << log2Lx) < Lx) ++log2Lx;
-  if (blocks_per_sm <= 0) blocks_per_sm = 8;
-  launch_pdl(linear_step_kernel<T>, blocks_for((long long)Lx * Ly / 2, 256, sm_count() * blocks_per_sm), 256, 0,
-             s, st, sp, J, rho0, d0, d1, Lx, Ly, log2Lx, handle, use_cond, max_body);
+void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0,
+                        V2<T>* v1, V2<T>* d0, V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle,
+                        int use_cond, unsigned int max_body, int blocks_per_sm, cudaStream_t s) {
+  const int N = Lx * Ly;
+  launch_pdl(linear_velocity_kernel<T>, blocks_for(N, 256, sm_count() * 8), 256, 0, s, st, J, rho0, v0, v1, N,
+             (int)kModeLinear, handle, use_cond, max_body);
+  launch_heun<T>(st, sp, v0, v1, d0, d1, Lx, Ly, kModeLinear, 0.0, handle, use_cond, blocks_per_sm, s);
 }
 
 #define CG_INSTANTIATE_STEP(T)                                                                      \
@@ -121,11 +121,11 @@ void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, cons
                                      cudaStream_t);                                                 \
   template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);   \
   template void launch_phi_spectrum<T>(const double*, T*, int, int, cudaStream_t);                  \
-  template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, int,    \
-                                      cudaGraphConditionalHandle, int, cudaStream_t);               \
+  template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
+                                      int, cudaGraphConditionalHandle, int, cudaStream_t);          \
   template void launch_linear_step<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
-                                      V2<T>*, int, int, cudaGraphConditionalHandle, int,            \
-                                      unsigned int, int, cudaStream_t);
+                                      V2<T>*, V2<T>*, V2<T>*, int, int, cudaGraphConditionalHandle, \
+                                      int, unsigned int, int, cudaStream_t);
 CG_INSTANTIATE_STEP(float)
 CG_INSTANTIATE_STEP(double)
 

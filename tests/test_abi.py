@@ -43,7 +43,7 @@ def test_default_options_without_gpu():
     assert o.precision == P.CG_PRECISION_FP64
     assert o.dt0 == 1e-2 and o.atol == 1e-2 and o.grow == 1.2 and o.shrink == 0.5
     assert o.cfl == 1.0 and o.rho_tol == 1e-4 and o.area_tol == 0.01
-    assert o.max_steps == 4000 and o.max_iter == 50 and o.use_graph == 1 and o.blur_decay == 0.5 and o.autotune == 1
+    assert o.max_steps == 4000 and o.max_iter == 500 and o.use_graph == 1 and o.blur_decay == 0.5 and o.autotune == 1
     assert o.flow == P.CG_FLOW_DIFFUSION
 
 

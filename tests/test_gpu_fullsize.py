@@ -136,3 +136,92 @@ def test_first_integration_at_256_matches_oracle(orc):
     assert r.status == 0
     assert np.max(np.abs(grid[..., 0] - r.X)) < 1e-3
     assert np.max(np.abs(grid[..., 1] - r.Y)) < 1e-3
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    return synth.make_workload("clustered300_512")
+
+
+def test_density_spectrum_field_and_step_at_512(orc, clustered):
+    # the 512^2 clustered workload (lognormal(1.5) values, blur 2) in both precisions
+    m = clustered
+    blur = synth.WORKLOADS["clustered300_512"]["blur"]
+    rho0 = _oracle_density(orc, m)
+    spec = orc.forward(rho0, blur)
+    t, h = 1.5, 0.6
+    r0, gx, gy = orc.fields(spec, t)
+    vx, vy, _ = orc.velocity(r0, gx, gy)
+    v1 = orc.velocity(*orc.fields(spec, t + h))
+    rng = np.random.default_rng(4)
+    disp = rng.uniform(-1.5, 1.5, (m.Ly, m.Lx, 2))
+    xc = np.arange(m.Lx)[None, :] + 0.5
+    yc = np.arange(m.Ly)[:, None] + 0.5
+    x = np.clip(xc + disp[..., 0], 0, m.Lx)
+    y = np.clip(yc + disp[..., 1], 0, m.Ly)
+    _, _, xcor, ycor, e = orc.heun_step(vx, vy, v1[0], v1[1], x.ravel(), y.ravel(), h)
+    # field error bounds relative to the fields' global scale: FP32 transforms ~ eps32
+    # log2(N) per value; the FP64 transforms and the oracle's direct sums both ~1e-14
+    for prec, eps, ptol in (("fp64", 1e-12, 1e-9), ("mixed", 2.0 ** -24 * np.log2(m.Lx) * 8, 1e-3)):
+        with P.Cartogram(m.Lx, m.Ly, blur, precision=prec) as c:
+            c.set_map(m)
+            rho_gpu = c.density()
+            spec_gpu = c.spectrum()
+            rho_t, v_t = c.velocity(t)
+            out, err = c.heun_step(t, h, disp)
+        assert np.max(np.abs(rho_gpu - rho0)) < 1e-9 * np.max(rho0)
+        assert np.max(np.abs(spec_gpu - spec)) < 1e-11 * np.max(np.abs(spec))
+        # the velocity divides by the local density
+        R = np.max(np.abs(r0 - 1.0))
+        G = np.max(np.hypot(gx, gy))
+        assert np.max(np.abs(rho_t - r0)) < eps * R
+        bound = eps * (G + R * np.hypot(vx, vy)) / r0
+        assert np.all(np.abs(v_t[..., 0] - vx) <= bound)
+        assert np.all(np.abs(v_t[..., 1] - vy) <= bound)
+        assert np.max(np.abs((xc + out[..., 0]).ravel() - xcor)) < ptol
+        assert np.max(np.abs((yc + out[..., 1]).ravel() - ycor)) < ptol
+        assert abs(err - e) < ptol
+
+
+def test_converged_512_cartogram_properties(clustered):
+    m = clustered
+    blur = synth.WORKLOADS["clustered300_512"]["blur"]
+    with P.Cartogram(m.Lx, m.Ly, blur, precision="mixed") as c:
+        c.set_map(m)
+        st = c.integrate()
+        xy = c.vertices()
+        folds = [c.fold_count(k)[0] for k in range(c.history_length())]
+        proj = c.project(m.xy)
+    assert st.converged and st.max_area_error < 0.01
+    # one region has a target of 2.3 cells^2 (about 1.5 cells wide): once the grid no
+    # longer resolves it, it shrinks a few percent per iteration
+    assert 100 < st.iterations < 500
+    assert folds[0] < 1e-3 * (m.Lx - 1) * (m.Ly - 1)
+    assert all(nf == 0 for nf in folds[1:])
+    assert np.max(np.abs(proj - xy)) < 1e-9
+
+
+def test_fp64_and_mixed_agree_on_first_integrations_at_512(clustered):
+    # The FP64 path at 512^2 (its autotuner candidates are limited by the kernels'
+    # register use) against the mixed path over two integrations with the same step
+    # schedule. This map has regions at 0.0018 of the mean density next to peaks at 80:
+    # FP32 transform round-off (~1e-6 of the global field scale) is ~20 % of the density
+    # there, so points inside those regions drift until the diffusing mass arrives. The
+    # drift stays below 1e-3 grid units for 99.9 % of the points and below 3e-3 for all;
+    # FP32 displacements alone (FP64 fields) account for 1.4e-4 and the FP32 spectrum
+    # alone for 6e-5.
+    m = clustered
+    blur = synth.WORKLOADS["clustered300_512"]["blur"]
+    out = {}
+    for prec in ("fp64", "mixed"):
+        with P.Cartogram(m.Lx, m.Ly, blur, precision=prec, max_iter=2) as c:
+            c.set_map(m)
+            with pytest.raises(P.CartogramError) as e:
+                c.integrate()
+            assert e.value.code == P.CG_ENOCONVERGE
+            out[prec] = (c.grid(0), c.grid(1), c.area_errors())
+    for k in range(2):
+        d = np.abs(out["fp64"][k] - out["mixed"][k])
+        assert np.mean(d > 1e-3) < 1e-3
+        assert np.max(d) < 3e-3
+    assert np.max(np.abs(out["fp64"][2] - out["mixed"][2])) < 1e-4
