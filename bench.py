@@ -165,11 +165,13 @@ def _traffic(kernel):
 
 
 def launches_per_cartogram(iterations, attempted):
-    """Kernels the library launches for one cartogram_integrate call: initial areas (2);
-    per iteration rasterise (2), forward transform (2), integration init (3: state,
-    pass 1, pass 2, finish -> 4), one attempted step (3 each), finish (2), vertex map (1),
-    areas (2)."""
-    return 2 + iterations * (2 + 2 + 4 + 2 + 1 + 2) + 3 * attempted
+    """Kernels the library launches for one cartogram_integrate call on the device-side
+    outer loop: initial areas (2) and loop decision (1); per iteration rasterise (2), blur
+    factors (1), forward transform (2), integration init (4: state, pass 1, pass 2,
+    finish), the step-loop body (3 kernels per attempted step, 4 attempts per body, so
+    on average 6 launches of finished attempts per integration that return at once),
+    snapshot and outcome (2), history store (1), vertex map (1), areas (2), decision (1)."""
+    return 3 + iterations * (2 + 1 + 2 + 4 + 6 + 2 + 1 + 1 + 2 + 1) + 3 * attempted
 
 
 def bytes_per_point(esz):
@@ -238,6 +240,58 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batched(args, P, synth, flush, stream):
+    """The batched workload: 64 independent frames (grid sizes from {128, ..., 1024}^2)
+    as parallel branches of one CUDA-graph launch, against the same contexts run one
+    after another. Host wall clock around the synchronous batch call."""
+    import collections
+
+    import torch
+    frames = synth.make_batch()
+    carts = [P.Cartogram(f.Lx, f.Ly, synth.BATCH["blur"], precision="mixed") for f in frames]
+    try:
+        for c, f in zip(carts, frames):
+            c.set_map(f)
+            c.integrate()  # picks the launch shapes, as in a first use
+        torch.cuda.synchronize()
+        # one after another (each context's own device-side loop)
+        t = time.perf_counter()
+        for c in carts:
+            c.reset()
+            c.integrate()
+        seq_s = time.perf_counter() - t
+        with P.Batch(carts) as b:
+            for c in carts:
+                c.reset()
+            b.integrate()  # captures the batch graph
+            times, stats = [], None
+            for _ in range(args.batch_steps):
+                for c in carts:
+                    c.reset()
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                stats, status = b.integrate()
+                times.append(time.perf_counter() - t)
+        s_batch = sum(times) / len(times)
+        updates = sum(f.Lx * f.Ly * (s.steps_accepted + s.steps_rejected) for f, s in zip(frames, stats))
+        its = [s.iterations for s in stats]
+        return {"workload": "64 frames, 300-region Voronoi maps, lognormal(1) values drifting by a "
+                            "multiplicative random walk, blur %g, mixed" % synth.BATCH["blur"],
+                "size_counts": {str(k): v for k, v in sorted(collections.Counter(f.Lx for f in frames).items())},
+                "s_per_batch": s_batch, "updates_per_s": updates / s_batch,
+                "sequential_s": seq_s, "speedup_vs_sequential": seq_s / s_batch,
+                "all_converged": all(s.converged for s in stats), "iterations_min_max": [min(its), max(its)],
+                "timing": "host wall clock around cartogram_batch_integrate (synchronous), mean of %d"
+                          % args.batch_steps}
+    except P.CartogramError as e:
+        return {"error": str(e)}
+    finally:
+        for c in carts:
+            c.close()
 
 
 def run_ours(args):
@@ -401,6 +455,8 @@ def run_ours(args):
             linear = {"flow": "linear equalisation (SI Eq. fmn_fast)", "error": str(e)}
         lc.close()
 
+    batched = run_batched(args, P, synth, flush, stream) if args.batch_steps > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, blur, args.cpu_steps)
@@ -425,6 +481,7 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
             "linear_flow": linear,
+            "batched": batched,
             "kernel_ms": prof,
             "launch_shapes": tune,
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -455,6 +512,8 @@ def main():
     ap.add_argument("--ref-attempts", type=int, default=20,
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--batch-steps", type=int, default=2,
+                    help="timed launches of the 64-frame batched workload (0: skip)")
     ap.add_argument("--linear-steps", type=int, default=2,
                     help="converged cartograms timed with the linear-equalisation flow (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -151,7 +151,14 @@ int cartogram_set_regions(cg_ctx* ctx, int n_regions, const double* target_value
  * area error below 1%), where A^_i = V_i * sum(A) / sum(V). Continues from the
  * current vertices, so a second call after convergence runs no iteration. stats may
  * be NULL. Returns CG_OK on convergence, CG_ENOCONVERGE after max_iter iterations
- * (the vertices and history stay valid), CG_ESTEPFAIL, CG_ESTATE, CG_ECUDA. */
+ * (the vertices and history stay valid), CG_ESTEPFAIL, CG_ESTATE, CG_ECUDA.
+ * With use_graph = 1 the whole outer iteration runs on the device: one CUDA-graph
+ * launch whose conditional WHILE node repeats rasterisation, transform, integration
+ * (itself a WHILE node), mapping and areas until the areas converge; the host reads
+ * the outcome once (the first call first runs one iteration from the host when the
+ * launch shapes are still to be tuned, and a launch that runs out of history slots
+ * is repeated after more are allocated). use_graph = 0 or 2 run the outer loop from
+ * the host, reading the outcome after every integration. */
 int cartogram_integrate(cg_ctx* ctx, cg_stats* stats);
 
 /* Map n arbitrary points (x, y pairs, [n][2]) through every projected grid of the
@@ -267,6 +274,36 @@ const char* cartogram_last_error(const cg_ctx* ctx);
 
 /* Free the context and all its device memory. NULL is accepted. */
 void cartogram_destroy(cg_ctx* ctx);
+
+/* ---- Batches: many independent cartograms in one CUDA-graph launch --------------
+ * The method's grid points are independent within one cartogram (main text: the
+ * integrations of the Lx*Ly trajectories are distributed over processing units), and
+ * separate cartograms (frames of an animation, replicates) are independent of each
+ * other. A batch runs the outer iterations of several contexts as parallel branches
+ * of one graph, so that the kernels of small grids share the GPU. */
+typedef struct cg_batch cg_batch;
+
+/* Group n contexts (distinct, on one device; sizes, precisions, flows and options may
+ * differ). The batch refers to the contexts: destroy it before them. The batch graph
+ * is captured on first use and again whenever a context's map or launch shapes
+ * change. Errors: CG_EINVAL (n < 1, NULL or repeated context, devices differ),
+ * CG_ECUDA. */
+int cartogram_batch_create(cg_ctx* const* ctxs, int n, cg_batch** out);
+
+/* cartogram_integrate for every context of the batch: contexts whose launch shapes are
+ * still to be tuned first run one iteration on their own stream, then one launch of the
+ * batch graph on the batch's stream runs all outer iterations (repeated while contexts
+ * run out of history slots). stats[i] and status[i] (each [n] or NULL) receive every
+ * context's outcome (seconds: the batch's wall time). Returns CG_OK when every context
+ * converged, else the first failing context's status (message in
+ * cartogram_batch_last_error; the context's own message in cartogram_last_error). */
+int cartogram_batch_integrate(cg_batch* batch, cg_stats* stats, int* status);
+
+/* Message of the last failed batch call. */
+const char* cartogram_batch_last_error(const cg_batch* batch);
+
+/* Free the batch (not its contexts). NULL is accepted. */
+void cartogram_batch_destroy(cg_batch* batch);
 
 #ifdef __cplusplus
 }

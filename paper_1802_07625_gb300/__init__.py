@@ -25,7 +25,8 @@ __all__ = [
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
     "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
-    "cartogram_velocity_noalloc", "cartogram_last_error", "cartogram_destroy", "Cartogram",
+    "cartogram_velocity_noalloc", "cartogram_last_error", "cartogram_destroy", "cartogram_batch_create",
+    "cartogram_batch_integrate", "cartogram_batch_last_error", "cartogram_batch_destroy", "Cartogram", "Batch",
 ]
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
@@ -104,6 +105,10 @@ def load(build_if_missing: bool = True):
         "cartogram_velocity_noalloc": (i, [i, i, _P, d, _P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
+        "cartogram_batch_create": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P)]),
+        "cartogram_batch_integrate": (i, [_P, _P, _P]),
+        "cartogram_batch_last_error": (ctypes.c_char_p, [_P]),
+        "cartogram_batch_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -310,6 +315,35 @@ def cartogram_destroy(ctx) -> None:
         load().cartogram_destroy(ctx)
 
 
+def cartogram_batch_create(ctxs):
+    """Batch of contexts (handles) whose outer iterations run in one graph launch."""
+    arr = (_P * len(ctxs))(*ctxs)
+    out = _P()
+    rc = load().cartogram_batch_create(arr, len(ctxs), ctypes.byref(out))
+    if rc != CG_OK:
+        raise CartogramError(rc, "cartogram_batch_create failed")
+    return out.value
+
+
+def cartogram_batch_integrate(batch, n: int, check: bool = True):
+    """Run the batch; returns (list of Stats, list of per-context status codes)."""
+    stats = (Stats * n)()
+    status = np.zeros(n, dtype=np.int32)
+    rc = load().cartogram_batch_integrate(batch, ctypes.cast(stats, _P), status.ctypes.data)
+    if check and rc != CG_OK:
+        raise CartogramError(rc, cartogram_batch_last_error(batch))
+    return list(stats), status.tolist()
+
+
+def cartogram_batch_last_error(batch) -> str:
+    return (load().cartogram_batch_last_error(batch) or b"").decode()
+
+
+def cartogram_batch_destroy(batch) -> None:
+    if batch:
+        load().cartogram_batch_destroy(batch)
+
+
 # ---------------------------------------------------------------------------
 # convenience object owning a context
 # ---------------------------------------------------------------------------
@@ -417,3 +451,32 @@ class Cartogram:
         g = np.empty((self.Ly, self.Lx, 2))
         a, r, t = cartogram_integrate_once(self.ctx, g)
         return g, a, r, t
+
+
+class Batch:
+    """Owns a batch over Cartogram objects (which must outlive it)."""
+
+    def __init__(self, carts):
+        self.carts = list(carts)
+        self.handle = cartogram_batch_create([c.ctx for c in self.carts])
+
+    def integrate(self, check: bool = True):
+        return cartogram_batch_integrate(self.handle, len(self.carts), check)
+
+    def close(self):
+        if self.handle:
+            cartogram_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -252,6 +252,7 @@ static __global__ void init_state_kernel(DevState* st, StepParams sp) {
   st->ticket = 0;
   st->bad = 0;
   st->body_iters = 0;
+  st->t_start_ns = global_ns();
 }
 
 // After the field at t = 0: stop at once if the density is already equal, else cap
@@ -273,7 +274,8 @@ static __global__ void init_finish_kernel(DevState* st, StepParams sp, cudaGraph
   st->dev_bits = 0;
   st->ticket = 0;
   st->bad = 0;
-  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+  // set either way: inside an outer loop the same step loop runs once per iteration
+  if (use_cond) cudaGraphSetConditional(handle, status == kRunning ? 1u : 0u);
 }
 
 // Copy the displacements of the current buffer (selected by parity) to `dst`.

@@ -35,8 +35,7 @@ struct cg_ctx {
   void *Wx = nullptr, *Wy = nullptr, *Ex = nullptr, *Ey = nullptr;
   double2 *Wfx = nullptr, *Wfy = nullptr, *Efx = nullptr, *Efy = nullptr;
   double *bx = nullptr, *by = nullptr;  // blur factors for width blur_tab_sigma
-  double* blur_h = nullptr;              // pinned staging of the blur factors
-  double blur_tab_sigma = -1.0;
+  double blur_tab_sigma = -1.0;           // -1: the tables hold no known width
 
   // fields
   double* acc = nullptr;     // rasterised rho/rho_bar - 1 (FP64)
@@ -94,6 +93,31 @@ struct cg_ctx {
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // the outer iteration on the device: one graph launch runs iterations until the areas
+  // converge (or the budget, a failure, or the free history slots end it)
+  cg::OuterState* outer = nullptr;    // device
+  cg::OuterState* outer_h = nullptr;  // pinned
+  double* sigma_d = nullptr;          // blur width per iteration of a call
+  double* sigma_h = nullptr;          // pinned
+  int sigma_cap = 0;
+  void** hist_d = nullptr;            // device copy of the history slot pointers
+  int hist_d_cap = 0;
+  int hist_d_count = 0;               // pointers in hist_d
+  cudaGraph_t ograph = nullptr;
+  cudaGraphExec_t oexec = nullptr;
+  unsigned long long gen = 1;         // changes whenever captured graphs of this context go stale
+};
+
+// Independent contexts whose outer iterations run as parallel branches of one graph.
+struct cg_batch {
+  std::vector<cg_ctx*> ctx;
+  std::vector<unsigned long long> gen;  // each context's generation when the graph was built
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
 };
 
 namespace {
@@ -174,22 +198,11 @@ int upload_tables(cg_ctx* c, int N, void** Wd, void** Ed, double2** Wfd, double2
   return CG_OK;
 }
 
-// Separable blur factors exp(-(pi m / L)^2 sigma^2 / 2) of both axes, staged through
-// pinned memory (the stream is synchronised once per outer iteration, before the
-// staging buffer is written again).
+// Separable blur factors exp(-(pi m / L)^2 sigma^2 / 2) of both axes, computed on the
+// device by the same kernel the device-side outer iteration uses.
 int set_blur_tables(cg_ctx* c, double sigma) {
-  CG_CUDA(c, cudaStreamSynchronize(c->stream));
-  double* h = c->blur_h;
-  for (int m = 0; m < c->Lx; ++m) {
-    const double k = cg::kPi * m / c->Lx;
-    h[m] = std::exp(-0.5 * k * k * sigma * sigma);
-  }
-  for (int n = 0; n < c->Ly; ++n) {
-    const double k = cg::kPi * n / c->Ly;
-    h[c->Lx + n] = std::exp(-0.5 * k * k * sigma * sigma);
-  }
-  CG_CUDA(c, cudaMemcpyAsync(c->bx, h, sizeof(double) * c->Lx, cudaMemcpyHostToDevice, c->stream));
-  CG_CUDA(c, cudaMemcpyAsync(c->by, h + c->Lx, sizeof(double) * c->Ly, cudaMemcpyHostToDevice, c->stream));
+  cg::launch_blur_tables(nullptr, sigma, c->bx, c->by, c->Lx, c->Ly, c->stream);
+  CG_CUDA(c, cudaGetLastError());
   c->blur_tab_sigma = sigma;
   return CG_OK;
 }
@@ -203,7 +216,8 @@ int alloc_fields(cg_ctx* c) {
   if (r) return r;
   CG_CUDA(c, cudaMalloc((void**)&c->bx, sizeof(double) * c->Lx));
   CG_CUDA(c, cudaMalloc((void**)&c->by, sizeof(double) * c->Ly));
-  CG_CUDA(c, cudaMallocHost((void**)&c->blur_h, sizeof(double) * (c->Lx + c->Ly)));
+  CG_CUDA(c, cudaMalloc((void**)&c->outer, sizeof(cg::OuterState)));
+  CG_CUDA(c, cudaMallocHost((void**)&c->outer_h, sizeof(cg::OuterState)));
   if (c->blur > 0.0 && (r = set_blur_tables(c, c->blur))) return r;
   CG_CUDA(c, cudaMalloc((void**)&c->acc, sizeof(double) * N));
   CG_CUDA(c, cudaMalloc((void**)&c->R, sizeof(double) * N));
@@ -322,6 +336,8 @@ void enqueue_finish(cg_ctx* c, cudaStream_t s) {
   cg::launch_collect(c->st, c->info, s);
 }
 
+void drop_outer_graph(cg_ctx* c);
+
 // Time the candidate launch shapes of the three step kernels with CUDA events on the
 // context's stream (fields of the current spectrum at fixed times, the displacements of
 // the last integration) and keep the fastest of each.
@@ -398,76 +414,152 @@ int do_autotune(cg_ctx* c, int reps) {
   c->tune = best;
   for (int k = 0; k < 3; ++k) c->tune_ms[k] = best_ms[k];
   c->tuned = true;
-  // a graph captured with other shapes is rebuilt on next use
+  // graphs captured with other shapes are rebuilt on next use
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  drop_outer_graph(c);
   return CG_OK;
 }
 
 constexpr int kGraphUnroll = 4;
 
-// One integration as a graph: init kernels, then a WHILE node whose body is one
-// attempted step (field at t+h, Heun step + controller); the controller clears the
-// condition when the integration ends.
+// ---- graph capture ----------------------------------------------------------
+
+// The graph that stream `s` is capturing into.
+cudaError_t captured_graph(cudaStream_t s, cudaGraph_t* g) {
+  cudaStreamCaptureStatus st;
+  return cudaStreamGetCaptureInfo(s, &st, nullptr, g, nullptr, nullptr, nullptr);
+}
+
+// Append a conditional WHILE node (handle h) after the work captured so far on `cs`, and
+// capture body(bs) into its body graph on the spare stream `bs`.
+template <typename F>
+cudaError_t capture_while(cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h, F&& body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return e;
+  const cudaError_t eb = body(bs);
+  cudaGraph_t bg = nullptr;
+  e = cudaStreamEndCapture(bs, &bg);
+  return eb != cudaSuccess ? eb : e;
+}
+
+// One integration of the current spectrum: init kernels, then a WHILE node whose body
+// is kGraphUnroll attempted steps (the kernels of an attempt after the integration has
+// ended return at once; the init kernel sets the condition, the step controller clears
+// it), then the snapshot of the projected grid into dres and the outcome into info.
 template <typename T>
-int build_graph(cg_ctx* c) {
-  cudaStream_t cs = nullptr, bs = nullptr;
+cudaError_t capture_integration(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle* hout) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = captured_graph(cs, &g);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) return e;
+  const bool lin = c->opt.flow == CG_FLOW_LINEAR;
+  if (lin) enqueue_init_linear<T>(c, h, 1, cs);
+  else enqueue_init<T>(c, h, 1, cs);
+  e = capture_while(cs, bs, h, [&](cudaStream_t s) {
+    for (int k = 0; k < kGraphUnroll; ++k) {
+      if (lin) enqueue_body_linear<T>(c, h, 1, s);
+      else enqueue_body<T>(c, h, 1, s);
+    }
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
+  enqueue_finish<T>(c, cs);
+  if (hout) *hout = h;
+  return cudaGetLastError();
+}
+
+// The whole outer iteration of one context, captured on `cs` (a stream capturing into
+// a graph; bs and bs2 are spare streams for the loop bodies): areas and the first
+// decision, then a WHILE node whose body is one iteration.
+template <typename T>
+cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaStream_t bs2) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = captured_graph(cs, &g);
+  cudaGraphConditionalHandle ho = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, 0);
+  if (e != cudaSuccess) return e;
+  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, c->values, c->R_n,
+                   c->area, c->err_d, c->w, c->info, cs);
+  cg::launch_outer_decide(c->outer, c->info, ho, 0, cs);
+  const int N = c->Lx * c->Ly;
+  return capture_while(cs, bs, ho, [&](cudaStream_t s) {
+    cudaError_t eb = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)N, s);
+    if (eb != cudaSuccess) return eb;
+    cg::launch_raster(c->xy, c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, (int)c->n_vert, s);
+    cg::launch_blur_tables(c->outer, 0.0, c->bx, c->by, c->Lx, c->Ly, s);
+    cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, sizeof(T) == 4 ? (T*)c->specT : nullptr,
+                      c->Wfx, c->Efx, c->Wfy, c->Efy, c->bx, c->by, s);
+    if ((eb = capture_integration<T>(c, s, bs2, nullptr)) != cudaSuccess) return eb;
+    cg::launch_outer_commit<T>(c->outer, c->info, (const V2<T>*)c->dres, N, s);
+    cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s, &c->outer->status);
+    cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, c->values, c->R_n,
+                     c->area, c->err_d, c->w, c->info, s);
+    cg::launch_outer_decide(c->outer, c->info, ho, 1, s);
+    return cudaGetLastError();
+  });
+}
+
+// Capture `enqueue(cs, bs, bs2)` into a new graph and instantiate it.
+template <typename F>
+int capture_and_instantiate(cg_ctx* c, cudaGraph_t* gout, cudaGraphExec_t* xout, F&& enqueue) {
+  cudaStream_t cs = nullptr, bs = nullptr, bs2 = nullptr;
   CG_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   CG_CUDA(c, cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  CG_CUDA(c, cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   int rc = CG_OK;
-  do {
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "begin capture: %s", cudaGetErrorString(e)); break; }
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg_graph = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
-    cudaGraphConditionalHandle h = 0;
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg_graph, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) {
-      cudaStreamEndCapture(cs, &g);
-      rc = fail(c, CG_ECUDA, "conditional handle: %s", cudaGetErrorString(e));
-      break;
-    }
-    if (c->opt.flow == CG_FLOW_LINEAR) enqueue_init_linear<T>(c, h, 1, cs);
-    else enqueue_init<T>(c, h, 1, cs);
-    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode = nullptr;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg_graph, deps, nullptr, ndeps, &cp);
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    cudaGraph_t body = cp.conditional.phGraph_out ? cp.conditional.phGraph_out[0] : nullptr;
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) {
-      // several attempted steps per evaluation of the condition; the kernels of an
-      // attempt after the integration has ended return at once
-      for (int k = 0; k < kGraphUnroll; ++k) {
-        if (c->opt.flow == CG_FLOW_LINEAR) enqueue_body_linear<T>(c, h, 1, bs);
-        else enqueue_body<T>(c, h, 1, bs);
-      }
-      cudaGraph_t bg = nullptr;
-      e = cudaStreamEndCapture(bs, &bg);
-    }
-    if (e == cudaSuccess) enqueue_finish<T>(c, cs);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    e = enqueue(cs, bs, bs2);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
-    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "graph capture: %s", cudaGetErrorString(e)); break; }
-    e = cudaGraphInstantiate(&c->exec, g, 0);
-    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); break; }
-    c->graph = g;
-    c->cond = h;
-    g = nullptr;
-  } while (0);
-  if (g) cudaGraphDestroy(g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(xout, g, 0);
+  if (e != cudaSuccess) {
+    rc = fail(c, CG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (g) cudaGraphDestroy(g);
+  } else {
+    *gout = g;
+  }
   cudaGetLastError();
   cudaStreamDestroy(cs);
   cudaStreamDestroy(bs);
+  cudaStreamDestroy(bs2);
   return rc;
+}
+
+// Graph of one integration (cartogram_integrate_once, and the host-driven outer loop).
+template <typename T>
+int build_graph(cg_ctx* c) {
+  return capture_and_instantiate(c, &c->graph, &c->exec, [&](cudaStream_t cs, cudaStream_t bs, cudaStream_t) {
+    return capture_integration<T>(c, cs, bs, &c->cond);
+  });
+}
+
+void drop_outer_graph(cg_ctx* c) {
+  if (c->oexec) cudaGraphExecDestroy(c->oexec);
+  if (c->ograph) cudaGraphDestroy(c->ograph);
+  c->oexec = nullptr;
+  c->ograph = nullptr;
+  ++c->gen;
 }
 
 // Run one integration of the current spectrum; the projected grid ends in dres and
@@ -576,20 +668,26 @@ int read_info(cg_ctx* c) {
   return CG_OK;
 }
 
+// The outer iteration driven by the host: one graph launch (or host loop) per
+// integration, a read-back of the outcome and of the areas after each. Runs at most
+// iter_limit iterations; stopping there is CG_ENOCONVERGE only when that is the whole
+// budget (final), else *stopped is set. Counts accumulate into s.
 template <typename T>
-int do_integrate(cg_ctx* c, cg_stats* stats) {
-  const auto t0 = std::chrono::steady_clock::now();
-  cg_stats s;
-  memset(&s, 0, sizeof s);
+int do_integrate_host(cg_ctx* c, cg_stats& s, int iter_limit, bool final, bool* stopped) {
   int r;
+  if (stopped) *stopped = false;
   if ((r = run_areas(c)) || (r = read_info(c))) return r;
   double max_err = c->info_h->max_err;
   int status = CG_OK;
   const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
   int it = 0;
   while (!(max_err < c->opt.area_tol)) {
-    if (it >= c->opt.max_iter) {
-      status = fail(c, CG_ENOCONVERGE, "no convergence after %d iterations (max error %g)", it, max_err);
+    if (it >= iter_limit) {
+      if (final)
+        status = fail(c, CG_ENOCONVERGE, "no convergence after %d iterations (max error %g)", s.iterations + it,
+                      max_err);
+      else if (stopped)
+        *stopped = true;
       break;
     }
     if ((r = run_raster(c)) || (r = run_forward<T>(c)) || (r = run_integration<T>(c)) ||
@@ -604,8 +702,8 @@ int do_integrate(cg_ctx* c, cg_stats* stats) {
     s.t_end = inf.t_end;
     if (inf.status != cg::kDone) {
       status = fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
-                    "integration %d ended with status %d after %lld/%lld steps", it + 1, inf.status,
-                    inf.accepted, inf.rejected);
+                    "integration %d ended with status %d after %lld/%lld steps", s.iterations + it + 1,
+                    inf.status, inf.accepted, inf.rejected);
       break;
     }
     // pick the launch shapes once, on the displacements of a real integration
@@ -623,9 +721,153 @@ int do_integrate(cg_ctx* c, cg_stats* stats) {
     ++it;
     ++c->hist_len;
   }
-  s.iterations = it;
-  s.converged = max_err < c->opt.area_tol;
+  s.iterations += it;
   s.max_area_error = max_err;
+  return status;
+}
+
+// Host side of a device-run outer iteration: history slots for the coming iterations
+// (in chunks), the slot pointers and blur widths on the device, the loop state.
+constexpr int kSlotChunk = 32;
+
+template <typename T>
+int ensure_slots(cg_ctx* c, int want) {
+  const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
+  while ((int)c->hist.size() < want) {
+    void* p = nullptr;
+    CG_CUDA(c, cudaMalloc(&p, fbytes));
+    c->hist.push_back(p);
+  }
+  const int n = (int)c->hist.size();
+  if (n == c->hist_d_count) return CG_OK;
+  if (c->hist_d_cap < n) {
+    if (c->hist_d) CG_CUDA(c, cudaFree(c->hist_d));
+    c->hist_d = nullptr;
+    c->hist_d_cap = std::max(n, 2 * c->hist_d_cap);
+    CG_CUDA(c, cudaMalloc((void**)&c->hist_d, sizeof(void*) * c->hist_d_cap));
+  }
+  CG_CUDA(c, cudaMemcpy(c->hist_d, c->hist.data(), sizeof(void*) * n, cudaMemcpyHostToDevice));
+  c->hist_d_count = n;
+  return CG_OK;
+}
+
+// Prepare one context's device loop for up to `budget` iterations: blur widths of those
+// iterations, the first chunk of slots, the loop state (written to the device on the
+// context's stream).
+template <typename T>
+int outer_prepare(cg_ctx* c, int budget) {
+  if (c->sigma_cap < budget + 1) {
+    if (c->sigma_d) CG_CUDA(c, cudaFree(c->sigma_d));
+    if (c->sigma_h) CG_CUDA(c, cudaFreeHost(c->sigma_h));
+    c->sigma_d = nullptr;
+    c->sigma_h = nullptr;
+    c->sigma_cap = budget + 1;
+    CG_CUDA(c, cudaMalloc((void**)&c->sigma_d, sizeof(double) * c->sigma_cap));
+    CG_CUDA(c, cudaMallocHost((void**)&c->sigma_h, sizeof(double) * c->sigma_cap));
+  }
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));  // the pinned staging is free
+  for (int i = 0; i <= budget; ++i)
+    c->sigma_h[i] = c->blur * std::pow(c->opt.blur_decay, (double)(c->hist_len + i));
+  CG_CUDA(c, cudaMemcpyAsync(c->sigma_d, c->sigma_h, sizeof(double) * (budget + 1), cudaMemcpyHostToDevice,
+                             c->stream));
+  int r = ensure_slots<T>(c, c->hist_len + std::min(budget, kSlotChunk));
+  if (r) return r;
+  cg::OuterState& o = *c->outer_h;
+  memset(&o, 0, sizeof o);
+  o.hist = c->hist_d;
+  o.sigma = c->sigma_d;
+  o.area_tol = c->opt.area_tol;
+  o.k = c->hist_len;
+  o.cap = (int)c->hist.size();
+  o.iterations = 0;
+  o.max_iter = budget;
+  o.status = cg::kOuterRunning;
+  CG_CUDA(c, cudaMemcpyAsync(c->outer, &o, sizeof o, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->blur_tab_sigma = -1.0;  // the loop rewrites the blur tables
+  return CG_OK;
+}
+
+// After a device loop stopped for want of slots: add a chunk and resume.
+template <typename T>
+int outer_resume(cg_ctx* c) {
+  cg::OuterState& o = *c->outer_h;
+  const int left = o.max_iter - o.iterations;
+  int r = ensure_slots<T>(c, o.k + std::min(left, kSlotChunk));
+  if (r) return r;
+  o.hist = c->hist_d;
+  o.cap = (int)c->hist.size();
+  o.status = cg::kOuterRunning;
+  CG_CUDA(c, cudaMemcpy(c->outer, &o, sizeof o, cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
+// Fold a finished device loop into the context and the statistics.
+int outer_finish(cg_ctx* c, cg_stats& s) {
+  const cg::OuterState& o = *c->outer_h;
+  c->hist_len = o.k;
+  if (o.iterations > 0 || o.accepted + o.rejected > 0) c->have_spectrum = true;
+  s.iterations += o.iterations;
+  s.steps_accepted += o.accepted;
+  s.steps_rejected += o.rejected;
+  if (o.accepted + o.rejected > 0) s.t_end = o.t_end;
+  s.step_loop_ms += o.loop_ns * 1e-6;
+  s.max_area_error = o.max_err;
+  if (o.status == cg::kOuterConverged) return CG_OK;
+  if (o.status == cg::kOuterNoConverge)
+    return fail(c, CG_ENOCONVERGE, "no convergence after %d iterations (max error %g)", s.iterations, o.max_err);
+  return fail(c, o.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
+              "integration %d ended with status %d", s.iterations + 1, o.status);
+}
+
+template <typename T>
+int build_outer_graph(cg_ctx* c) {
+  return capture_and_instantiate(c, &c->ograph, &c->oexec, [&](cudaStream_t cs, cudaStream_t bs, cudaStream_t bs2) {
+    return capture_cartogram<T>(c, cs, bs, bs2);
+  });
+}
+
+// First iteration on the host path when the launch shapes are still to be picked (on
+// the displacements of a real integration). Returns CG_OK with *go = true when the
+// device loop should continue.
+template <typename T>
+int maybe_tune_first(cg_ctx* c, cg_stats& s, bool* go) {
+  *go = true;
+  if (!c->opt.autotune || c->tuned || c->opt.max_iter == 0) return CG_OK;
+  bool stopped = false;
+  const int r = do_integrate_host<T>(c, s, 1, c->opt.max_iter == 1, &stopped);
+  *go = r == CG_OK && stopped;
+  return r;
+}
+
+// The outer iteration run on the device: one launch of the context's cartogram graph,
+// again only when history slots ran out.
+template <typename T>
+int do_integrate_device(cg_ctx* c, cg_stats& s) {
+  bool go = false;
+  int r = maybe_tune_first<T>(c, s, &go);
+  if (r || !go) return r;
+  if (!c->oexec && (r = build_outer_graph<T>(c))) return r;
+  if ((r = outer_prepare<T>(c, c->opt.max_iter - s.iterations))) return r;
+  for (;;) {
+    CG_CUDA(c, cudaGraphLaunch(c->oexec, c->stream));
+    CG_CUDA(c, cudaMemcpyAsync(c->outer_h, c->outer, sizeof(cg::OuterState), cudaMemcpyDeviceToHost, c->stream));
+    CG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->outer_h->status != cg::kOuterNeedSlots) break;
+    if ((r = outer_resume<T>(c))) return r;
+  }
+  return outer_finish(c, s);
+}
+
+template <typename T>
+int do_integrate(cg_ctx* c, cg_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cg_stats s;
+  memset(&s, 0, sizeof s);
+  int status;
+  if (c->opt.use_graph == 1) status = do_integrate_device<T>(c, s);
+  else status = do_integrate_host<T>(c, s, c->opt.max_iter, true, nullptr);
+  s.converged = s.max_area_error < c->opt.area_tol;
   s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = s;
   return status;
@@ -820,6 +1062,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
 }
 
 void free_regions(cg_ctx* c) {
+  drop_outer_graph(c);  // it holds the map's buffers
   void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
                 c->xy, c->xy0, c->ring_area, c->area, c->err_d, c->w};
   for (void* p : ps)
@@ -828,6 +1071,77 @@ void free_regions(cg_ctx* c) {
   c->next = nullptr; c->vreg = nullptr; c->xy = nullptr; c->xy0 = nullptr;
   c->ring_area = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
   c->have_regions = false;
+}
+
+// ---- batches -------------------------------------------------------------------
+
+int batch_fail(cg_batch* b, int code, const char* what, cudaError_t e) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  b->err = buf;
+  return code;
+}
+
+// One graph, one branch per context: fork from a common node, each branch the
+// context's whole outer iteration (capture_cartogram), join at the end.
+int batch_build(cg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  const size_t n = b->ctx.size();
+  std::vector<cudaStream_t> br(n, nullptr);
+  cudaStream_t ms = nullptr, bs = nullptr, bs2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCapture(ms, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      e = cudaEventRecord(fork, ms);
+      for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cg_ctx* c = b->ctx[i];
+        e = cudaStreamWaitEvent(br[i], fork, 0);
+        if (e == cudaSuccess)
+          e = c->mixed ? capture_cartogram<float>(c, br[i], bs, bs2) : capture_cartogram<double>(c, br[i], bs, bs2);
+        if (e == cudaSuccess) e = cudaEventRecord(join, br[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ms, join, 0);
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(ms, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  int rc = CG_OK;
+  if (e == cudaSuccess) {
+    b->graph = g;
+    for (size_t i = 0; i < n; ++i) b->gen[i] = b->ctx[i]->gen;
+  } else {
+    rc = batch_fail(b, CG_ECUDA, "batch graph capture", e);
+    if (g) cudaGraphDestroy(g);
+    b->exec = nullptr;
+  }
+  cudaGetLastError();
+  for (cudaStream_t st : br)
+    if (st) cudaStreamDestroy(st);
+  if (ms) cudaStreamDestroy(ms);
+  if (bs) cudaStreamDestroy(bs);
+  if (bs2) cudaStreamDestroy(bs2);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  return rc;
+}
+
+template <typename T>
+int batch_begin(cg_ctx* c, cg_stats& s, bool* go) {
+  int r = maybe_tune_first<T>(c, s, go);
+  if (r || !*go) return r;
+  return outer_prepare<T>(c, c->opt.max_iter - s.iterations);
 }
 
 }  // namespace
@@ -1153,12 +1467,145 @@ void cartogram_destroy(cg_ctx* c) {
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);
   for (void* p : c->hist) cudaFree(p);
   if (c->info_h) cudaFreeHost(c->info_h);
-  if (c->blur_h) cudaFreeHost(c->blur_h);
+  if (c->outer) cudaFree(c->outer);
+  if (c->outer_h) cudaFreeHost(c->outer_h);
+  if (c->sigma_d) cudaFree(c->sigma_d);
+  if (c->sigma_h) cudaFreeHost(c->sigma_h);
+  if (c->hist_d) cudaFree(c->hist_d);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   cudaGetLastError();
   delete c;
+}
+
+int cartogram_batch_create(cg_ctx* const* ctxs, int n, cg_batch** out) {
+  if (!out) return CG_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return CG_EINVAL;
+  std::vector<cg_ctx*> v(ctxs, ctxs + n);
+  for (int i = 0; i < n; ++i) {
+    if (!v[i]) return CG_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (v[k] == v[i]) return CG_EINVAL;
+    if (v[i]->device != v[0]->device) return CG_EINVAL;
+  }
+  cg_batch* b = new cg_batch();
+  b->ctx = v;
+  b->gen.assign(n, 0);
+  b->device = v[0]->device;
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return CG_ECUDA;
+  }
+  *out = b;
+  return CG_OK;
+}
+
+int cartogram_batch_integrate(cg_batch* b, cg_stats* stats, int* status) {
+  if (!b) return CG_EINVAL;
+  b->err.clear();
+  if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, CG_ECUDA, "cudaSetDevice", cudaGetLastError());
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t n = b->ctx.size();
+  std::vector<cg_stats> st(n);
+  std::vector<int> rc(n, CG_OK);
+  std::vector<char> go(n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    cg_ctx* c = b->ctx[i];
+    memset(&st[i], 0, sizeof(cg_stats));
+    c->err.clear();
+    if (!c->have_regions) {
+      rc[i] = fail(c, CG_ESTATE, "no map: call cartogram_set_regions first");
+      continue;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      rc[i] = fail(c, CG_ECUDA, "stream synchronisation failed");
+      continue;
+    }
+    bool g = false;
+    rc[i] = c->mixed ? batch_begin<float>(c, st[i], &g) : batch_begin<double>(c, st[i], &g);
+    go[i] = rc[i] == CG_OK && g;
+  }
+  bool any = false;
+  for (size_t i = 0; i < n; ++i) any |= go[i] != 0;
+  if (any) {
+    // branches of contexts that are done (or failed) skip their loop
+    for (size_t i = 0; i < n; ++i) {
+      if (go[i]) continue;
+      cg_ctx* c = b->ctx[i];
+      if (!c->have_regions) continue;
+      cg::OuterState o;
+      memset(&o, 0, sizeof o);
+      o.status = cg::kOuterConverged;
+      o.max_iter = 0;
+      if (cudaMemcpy(c->outer, &o, sizeof o, cudaMemcpyHostToDevice) != cudaSuccess)
+        return batch_fail(b, CG_ECUDA, "batch state", cudaGetLastError());
+    }
+    bool stale = !b->exec;
+    for (size_t i = 0; i < n; ++i) stale |= b->gen[i] != b->ctx[i]->gen || !b->ctx[i]->have_regions;
+    if (stale) {
+      for (size_t i = 0; i < n; ++i)
+        if (!b->ctx[i]->have_regions) return batch_fail(b, CG_ESTATE, "a context has no map", cudaSuccess);
+      int r = batch_build(b);
+      if (r) return r;
+    }
+    for (;;) {
+      cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+      for (size_t i = 0; i < n && e == cudaSuccess; ++i)
+        if (go[i])
+          e = cudaMemcpyAsync(b->ctx[i]->outer_h, b->ctx[i]->outer, sizeof(cg::OuterState), cudaMemcpyDeviceToHost,
+                              b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) return batch_fail(b, CG_ECUDA, "batch launch", e);
+      bool again = false;
+      for (size_t i = 0; i < n; ++i) {
+        if (!go[i] || b->ctx[i]->outer_h->status != cg::kOuterNeedSlots) continue;
+        cg_ctx* c = b->ctx[i];
+        const int r = c->mixed ? outer_resume<float>(c) : outer_resume<double>(c);
+        if (r) {
+          rc[i] = r;
+          go[i] = 0;
+          cg::OuterState o;
+          memset(&o, 0, sizeof o);
+          o.status = cg::kOuterConverged;
+          cudaMemcpy(c->outer, &o, sizeof o, cudaMemcpyHostToDevice);
+          continue;
+        }
+        again = true;
+      }
+      if (!again) break;
+    }
+    for (size_t i = 0; i < n; ++i)
+      if (go[i]) rc[i] = outer_finish(b->ctx[i], st[i]);
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int first = CG_OK;
+  for (size_t i = 0; i < n; ++i) {
+    st[i].converged = st[i].max_area_error < b->ctx[i]->opt.area_tol;
+    st[i].seconds = secs;
+    if (stats) stats[i] = st[i];
+    if (status) status[i] = rc[i];
+    if (first == CG_OK && rc[i] != CG_OK) {
+      first = rc[i];
+      b->err = "context " + std::to_string(i) + ": " + b->ctx[i]->err;
+    }
+  }
+  return first;
+}
+
+const char* cartogram_batch_last_error(const cg_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+void cartogram_batch_destroy(cg_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  cudaGetLastError();
+  delete b;
 }
 
 }  // extern "C"

@@ -44,6 +44,7 @@ struct DevState {
   int bad;                        // a field had a non-positive or non-finite density
   unsigned int body_iters;        // step-loop iterations started (termination guard)
   unsigned int pad;
+  unsigned long long t_start_ns;  // device clock at the start of the integration
 };
 // What a field or step kernel works on: the field at t (start of an integration),
 // the attempt at t + h inside the step loop, or explicit buffers and times.
@@ -66,7 +67,39 @@ struct IterInfo {
   long long rejected;
   int status;           // DevState status after the integration
   int pad;
+  unsigned long long loop_ns;  // device time of the integration (init to finish)
 };
+
+// State of the outer iteration when it runs on the device (one CUDA-graph launch runs
+// iterations until the areas converge, the budget ends, an integration fails, or the
+// history has no free slot). Written by the host before a launch, read after it.
+struct OuterState {
+  void** hist;                // device pointers of the projected-grid history slots
+  const double* sigma;        // blur width of each iteration of this call
+  double area_tol;
+  double max_err;             // max |A_i / A^_i - 1| of the current map
+  double t_end;               // end time of the last integration
+  long long accepted;         // attempted steps of this call's integrations
+  long long rejected;
+  unsigned long long loop_ns; // device time of this call's integrations
+  int k;                      // history length = slot of the next projected grid
+  int cap;                    // slots allocated
+  int iterations;             // iterations of this call
+  int max_iter;               // iteration budget of this call
+  int status;                 // kOuter* below, or a failed integration's status (< 0)
+  int pad;
+};
+constexpr int kOuterRunning = 0;
+constexpr int kOuterConverged = 1;
+constexpr int kOuterNeedSlots = 2;
+constexpr int kOuterNoConverge = -4;
+
+// Device clock in nanoseconds.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Grid-wide barrier state of the persistent integration kernel.
 struct GridBarrier {

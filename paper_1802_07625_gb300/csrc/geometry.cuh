@@ -186,6 +186,7 @@ __global__ void collect_kernel(const DevState* st, IterInfo* info) {
   info->accepted = st->accepted;
   info->rejected = st->rejected;
   info->status = st->status;
+  info->loop_ns = global_ns() - st->t_start_ns;
 }
 
 // ---------------------------------------------------------------------------
@@ -197,7 +198,8 @@ __global__ void collect_kernel(const DevState* st, IterInfo* info) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void map_points_kernel(const double2* in, double2* out, long long n,
-                                  const V2<T>* __restrict__ disp, int Lx, int Ly) {
+                                  const V2<T>* __restrict__ disp, int Lx, int Ly, const int* guard) {
+  if (guard && *guard < 0) return;  // the outer loop recorded a failed integration
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const double2 q = in[p];

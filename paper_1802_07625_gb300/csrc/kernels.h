@@ -167,11 +167,19 @@ template <typename T>
 void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0,
                         V2<T>* v1, V2<T>* d0, V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle,
                         int use_cond, unsigned int max_body, int blocks_per_sm, cudaStream_t s);
+// Outer iteration on the device: blur factors (of o->sigma[o->iterations], or of sigma
+// when o is null), storing an integration's projected grid, and the loop decision.
+void launch_blur_tables(const OuterState* o, double sigma, double* bx, double* by, int Lx, int Ly,
+                        cudaStream_t s);
+template <typename T>
+void launch_outer_commit(OuterState* o, const IterInfo* info, const V2<T>* dres, int N, cudaStream_t s);
+void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphConditionalHandle handle, int after,
+                         cudaStream_t s);
 template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>
 void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,
-                       int Ly, cudaStream_t s);
+                       int Ly, cudaStream_t s, const int* guard = nullptr);
 
 void launch_raster(const double2* xy, const int* next, const int* vreg, const double* w,
                    double* acc, int Lx, int Ly, int n_vert, cudaStream_t s);

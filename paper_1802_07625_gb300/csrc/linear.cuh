@@ -98,7 +98,8 @@ static __global__ void linear_init_finish_kernel(DevState* st, StepParams sp, cu
   st->dev_bits = 0;
   st->ticket = 0;
   st->bad = 0;
-  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+  // set either way: inside an outer loop the same step loop runs once per iteration
+  if (use_cond) cudaGraphSetConditional(handle, status == kRunning ? 1u : 0u);
 }
 
 }  // namespace cg

@@ -2,6 +2,7 @@
 #include "advect.cuh"
 #include "geometry.cuh"
 #include "linear.cuh"
+#include "outer.cuh"
 #include "kernels.h"
 
 namespace cg {
@@ -54,9 +55,9 @@ void launch_snapshot(const DevState* st, const V2<T>* d0, const V2<T>* d1, V2<T>
 
 template <typename T>
 void launch_map_points(const double2* in, double2* out, long long n, const V2<T>* disp, int Lx,
-                       int Ly, cudaStream_t s) {
+                       int Ly, cudaStream_t s, const int* guard) {
   if (n <= 0) return;
-  map_points_kernel<T><<<blocks_for(n, 256, 1 << 16), 256, 0, s>>>(in, out, n, disp, Lx, Ly);
+  map_points_kernel<T><<<blocks_for(n, 256, 1 << 16), 256, 0, s>>>(in, out, n, disp, Lx, Ly, guard);
 }
 
 void launch_raster(const double2* xy, const int* next, const int* vreg, const double* w,
@@ -111,6 +112,21 @@ void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, cons
   launch_heun<T>(st, sp, v0, v1, d0, d1, Lx, Ly, kModeLinear, 0.0, handle, use_cond, blocks_per_sm, s);
 }
 
+void launch_blur_tables(const OuterState* o, double sigma, double* bx, double* by, int Lx, int Ly,
+                        cudaStream_t s) {
+  blur_tables_kernel<<<blocks_for(Lx + Ly, 256, 64), 256, 0, s>>>(o, sigma, bx, by, Lx, Ly);
+}
+
+template <typename T>
+void launch_outer_commit(OuterState* o, const IterInfo* info, const V2<T>* dres, int N, cudaStream_t s) {
+  outer_commit_kernel<T><<<blocks_for(N, 256, sm_count() * 4), 256, 0, s>>>(o, info, dres, N);
+}
+
+void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphConditionalHandle handle, int after,
+                         cudaStream_t s) {
+  outer_decide_kernel<<<1, 1, 0, s>>>(o, info, handle, after);
+}
+
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
                                V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
@@ -118,9 +134,10 @@ void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, cons
   template void launch_snapshot<T>(const DevState*, const V2<T>*, const V2<T>*, V2<T>*, int,        \
                                    cudaStream_t);                                                   \
   template void launch_map_points<T>(const double2*, double2*, long long, const V2<T>*, int, int,   \
-                                     cudaStream_t);                                                 \
+                                     cudaStream_t, const int*);                                     \
   template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);   \
   template void launch_phi_spectrum<T>(const double*, T*, int, int, cudaStream_t);                  \
+  template void launch_outer_commit<T>(OuterState*, const IterInfo*, const V2<T>*, int, cudaStream_t); \
   template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
                                       int, cudaGraphConditionalHandle, int, cudaStream_t);          \
   template void launch_linear_step<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \

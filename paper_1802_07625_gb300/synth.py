@@ -306,3 +306,42 @@ def make_workload(name: str, L: int | None = None, n: int | None = None) -> Regi
     m = voronoi_map(Lb, Lb, seeds, lo, spacing, vals,
                     meta={"name": name, "blur": w["blur"], "precision": w["precision"]})
     return m
+
+
+# ----------------------------------------------------------------------------
+# batched frames
+# ----------------------------------------------------------------------------
+
+# 64 cartograms (animation frames) with grid sizes drawn uniformly from {128, 256, 512,
+# 1024}. One 300-region Voronoi geometry (uniform seeds in the unit square, scaled into
+# each size's square inset L/8, 0.5-cell edges); its lognormal(0, 1) values drift from
+# frame to frame by a multiplicative random walk, log-step N(0, 0.1^2). Blur 1 cell.
+BATCH = dict(frames=64, sizes=(128, 256, 512, 1024), n=300, spacing=0.5, sigma=1.0, step=0.1, blur=1.0,
+             seed_offset=4)
+
+
+def make_batch(frames: int | None = None, sizes=None) -> list:
+    """The batched workload: a list of RegionMaps, one per frame (same seed every call)."""
+    w = dict(BATCH)
+    if frames is not None:
+        w["frames"] = frames
+    if sizes is not None:
+        w["sizes"] = tuple(sizes)
+    rng = Xoshiro256ss(SEED_BASE + w["seed_offset"])
+    unit = seeds_uniform(rng, w["n"], 0.0, 1.0)
+    base = np.array([rng.lognormal(0.0, w["sigma"]) for _ in range(w["n"])])
+    geometry = {}
+    out = []
+    logv = np.log(base)
+    for f in range(w["frames"]):
+        L = w["sizes"][int(rng.uniform() * len(w["sizes"]))]
+        if f > 0:
+            logv = logv + np.array([w["step"] * rng.normal() for _ in range(w["n"])])
+        if L not in geometry:
+            lo, hi = L / 8.0, L - L / 8.0
+            geometry[L] = voronoi_map(L, L, lo + unit * (hi - lo), lo, w["spacing"], base)
+        g = geometry[L]
+        out.append(RegionMap(L, L, np.exp(logv), g.ring_offsets, g.ring_region, g.xy,
+                             {"name": "batch_frame%d" % f, "blur": w["blur"], "precision": "mixed"}))
+    return out
+
