@@ -96,6 +96,8 @@ def lib():
                                     ctypes.c_longlong, _D, _D, _D, ctypes.POINTER(Stats)]
         L.orc_flux_linear.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.orc_integrate_linear.argtypes = [ctypes.POINTER(Params), _D, _D, _D, _LL, _LL, _D]
+        L.orc_distortion.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        L.orc_inverse_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_longlong, _D, _D]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -247,6 +249,26 @@ def map_points(X, Y, pts) -> np.ndarray:
     Ly, Lx = X.shape
     out = np.empty_like(pts)
     lib().orc_map_points(Lx, Ly, _d(X), _d(Y), pts.shape[0], _d(pts), _d(out))
+    return out
+
+
+def distortion(grids) -> np.ndarray:
+    """e_a, e_inf, e~_a, e~_inf of the composed projection given its grids [K][2][Ly][Lx]
+    (projected X, Y at the cell centres) -- SI section 3."""
+    g = _f64(grids)
+    K, _, Ly, Lx = g.shape
+    out = np.empty(4)
+    lib().orc_distortion(Lx, Ly, K, _d(g), _d(out))
+    return out
+
+
+def inverse_points(grids, q) -> np.ndarray:
+    """Preimages of points q [n][2] under the composed projection (NaN where none)."""
+    g = _f64(grids)
+    q = _f64(q)
+    K, _, Ly, Lx = g.shape
+    out = np.empty_like(q)
+    lib().orc_inverse_points(Lx, Ly, K, _d(g), q.shape[0], _d(q), _d(out))
     return out
 
 

@@ -38,6 +38,10 @@
  *  orc_cartogram                  invariants only (strip map converges to the 1-D
  *                                 closed form); the exact 2-D result of a Voronoi map
  *                                 is not fixed by the paper: parity unpinned there.
+ *  orc_distortion                 affine grids (closed-form singular values), their
+ *                                 composition, identity (pinned)
+ *  orc_inverse_points             affine grids (closed-form inverse), round trip
+ *                                 through orc_map_points on cartogram grids (pinned)
  */
 #include <math.h>
 #include <stdint.h>
@@ -717,3 +721,169 @@ int orc_cartogram(const orc_params* P, int n_regions, const double* values,
     free(areas); free(rho); free(spec); free(X); free(Y); free(out);
     return status;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Diagnostics of the composed projection T = T_K o ... o T_1, where T_k is the map of
+ * outer iteration k: bilinear interpolation of its projected grid (X_k, Y_k) over the
+ * quads of cell centres, the nearest quad extended across the half-cell band along the
+ * walls (the same map as orc_map_points).
+ * ------------------------------------------------------------------------------- */
+
+/* Quad of the cell-centre lattice that the map of a grid uses at (x, y), and the
+ * fractional position in it. */
+static void locate_quad(int Lx, int Ly, double x, double y, int* i0, int* j0, double* fx, double* fy) {
+    double u = x - 0.5, w = y - 0.5;
+    int i = (int)floor(u), j = (int)floor(w);
+    if (i < 0) i = 0;
+    if (i > Lx - 2) i = Lx - 2;
+    if (j < 0) j = 0;
+    if (j > Ly - 2) j = Ly - 2;
+    *i0 = i;
+    *j0 = j;
+    *fx = u - i;
+    *fy = w - j;
+}
+
+/* Angular distortion of the composed projection (SI section 3, the Tissot indicatrix):
+ * at the centre of every quad of the original lattice, the Jacobian of T by the chain
+ * rule through the K bilinear maps (each differentiated inside its quad), its singular
+ * values a >= b, e = ln(a/b) and e~ = 2 asin((a - b)/(a + b)). grids: [K][2][Ly][Lx]
+ * (X then Y). out: e_a (mean of e over the (Lx-1)(Ly-1) sample points), e_inf (max),
+ * e~_a, e~_inf. Points where T folds (det J <= 0) count with their singular values. */
+void orc_distortion(int Lx, int Ly, int K, const double* grids, double* out) {
+    const size_t N = (size_t)Lx * Ly;
+    double sum_e = 0.0, max_e = 0.0, sum_t = 0.0, max_t = 0.0;
+    for (int j = 0; j + 1 < Ly; ++j)
+        for (int i = 0; i + 1 < Lx; ++i) {
+            double x = i + 1.0, y = j + 1.0;
+            double a = 1.0, b = 0.0, c = 0.0, d = 1.0; /* J = [[a, b], [c, d]] */
+            for (int k = 0; k < K; ++k) {
+                const double* X = grids + (size_t)k * 2 * N;
+                const double* Y = X + N;
+                int i0, j0;
+                double fx, fy;
+                locate_quad(Lx, Ly, x, y, &i0, &j0, &fx, &fy);
+                size_t k00 = (size_t)j0 * Lx + i0, k10 = k00 + 1, k01 = k00 + Lx, k11 = k01 + 1;
+                /* d T_k / d x and d T_k / d y of the bilinear map inside the quad */
+                double txx = (1 - fy) * (X[k10] - X[k00]) + fy * (X[k11] - X[k01]);
+                double tyx = (1 - fy) * (Y[k10] - Y[k00]) + fy * (Y[k11] - Y[k01]);
+                double txy = (1 - fx) * (X[k01] - X[k00]) + fx * (X[k11] - X[k10]);
+                double tyy = (1 - fx) * (Y[k01] - Y[k00]) + fx * (Y[k11] - Y[k10]);
+                double na = txx * a + txy * c, nb = txx * b + txy * d;
+                double nc = tyx * a + tyy * c, nd = tyx * b + tyy * d;
+                a = na; b = nb; c = nc; d = nd;
+                double c00 = (1 - fx) * (1 - fy), c10 = fx * (1 - fy), c01 = (1 - fx) * fy, c11 = fx * fy;
+                double xn = c00 * X[k00] + c10 * X[k10] + c01 * X[k01] + c11 * X[k11];
+                double yn = c00 * Y[k00] + c10 * Y[k10] + c01 * Y[k01] + c11 * Y[k11];
+                x = xn;
+                y = yn;
+            }
+            /* singular values of J from its conformal and anti-conformal parts,
+             * p = |(a + d, c - b)| and q = |(a - d, c + b)|: s1 = (p + q)/2 and
+             * s2 = |p - q|/2 (free of the cancellation of the characteristic
+             * polynomial near a conformal J) */
+            double pp = hypot(a + d, c - b), qq = hypot(a - d, c + b);
+            double s1 = 0.5 * (pp + qq), s2 = 0.5 * fabs(pp - qq);
+            double e = log(s1 / s2);
+            double et = 2.0 * asin((s1 - s2) / (s1 + s2));
+            sum_e += e;
+            sum_t += et;
+            if (e > max_e) max_e = e;
+            if (et > max_t) max_t = et;
+        }
+    const double n = (double)(Lx - 1) * (Ly - 1);
+    out[0] = sum_e / n;
+    out[1] = max_e;
+    out[2] = sum_t / n;
+    out[3] = max_t;
+}
+
+/* Bilinear map of quad (i0, j0) at fractional position (u, v) (u, v outside [0, 1]
+ * extend the quad linearly). */
+static void quad_map(int Lx, const double* X, const double* Y, int i0, int j0, double u, double v,
+                     double* x, double* y) {
+    size_t k00 = (size_t)j0 * Lx + i0, k10 = k00 + 1, k01 = k00 + Lx, k11 = k01 + 1;
+    *x = (1 - u) * (1 - v) * X[k00] + u * (1 - v) * X[k10] + (1 - u) * v * X[k01] + u * v * X[k11];
+    *y = (1 - u) * (1 - v) * Y[k00] + u * (1 - v) * Y[k10] + (1 - u) * v * Y[k01] + u * v * Y[k11];
+}
+
+/* Preimage of q under one grid's map (the inverse of orc_map_points; the main text's
+ * inverse graticule): every quad whose image could contain q is tried by Newton's
+ * method on its bilinear map, from the quad's centre; the solution is kept when it
+ * falls inside the quad's own domain, which for the quads along the walls extends to
+ * the box edge. Returns 0 if no quad contains q. */
+static int invert_one(int Lx, int Ly, const double* X, const double* Y, double qx, double qy, double* px,
+                      double* py) {
+    for (int j0 = 0; j0 + 1 < Ly; ++j0)
+        for (int i0 = 0; i0 + 1 < Lx; ++i0) {
+            /* domain of the quad in lattice units: [0,1]^2, extended to the box edge */
+            const double ulo = i0 == 0 ? -0.5 : 0.0, uhi = i0 == Lx - 2 ? 1.5 : 1.0;
+            const double vlo = j0 == 0 ? -0.5 : 0.0, vhi = j0 == Ly - 2 ? 1.5 : 1.0;
+            /* bounding box of the image of the (extended) domain: a bilinear map sends
+             * the rectangle into the hull of its corners' images */
+            double xs[4], ys[4];
+            quad_map(Lx, X, Y, i0, j0, ulo, vlo, &xs[0], &ys[0]);
+            quad_map(Lx, X, Y, i0, j0, uhi, vlo, &xs[1], &ys[1]);
+            quad_map(Lx, X, Y, i0, j0, ulo, vhi, &xs[2], &ys[2]);
+            quad_map(Lx, X, Y, i0, j0, uhi, vhi, &xs[3], &ys[3]);
+            double xmin = xs[0], xmax = xs[0], ymin = ys[0], ymax = ys[0];
+            for (int t = 1; t < 4; ++t) {
+                if (xs[t] < xmin) xmin = xs[t];
+                if (xs[t] > xmax) xmax = xs[t];
+                if (ys[t] < ymin) ymin = ys[t];
+                if (ys[t] > ymax) ymax = ys[t];
+            }
+            const double eps = 1e-9;
+            if (qx < xmin - eps || qx > xmax + eps || qy < ymin - eps || qy > ymax + eps) continue;
+            size_t k00 = (size_t)j0 * Lx + i0, k10 = k00 + 1, k01 = k00 + Lx, k11 = k01 + 1;
+            double u = 0.5, v = 0.5;
+            for (int it = 0; it < 60; ++it) {
+                double x, y;
+                quad_map(Lx, X, Y, i0, j0, u, v, &x, &y);
+                double rx = x - qx, ry = y - qy;
+                double xu = (1 - v) * (X[k10] - X[k00]) + v * (X[k11] - X[k01]);
+                double yu = (1 - v) * (Y[k10] - Y[k00]) + v * (Y[k11] - Y[k01]);
+                double xv = (1 - u) * (X[k01] - X[k00]) + u * (X[k11] - X[k10]);
+                double yv = (1 - u) * (Y[k01] - Y[k00]) + u * (Y[k11] - Y[k10]);
+                double det = xu * yv - xv * yu;
+                if (det == 0.0) break;
+                double du = (rx * yv - ry * xv) / det, dv = (ry * xu - rx * yu) / det;
+                u -= du;
+                v -= dv;
+                if (fabs(du) + fabs(dv) < 1e-15) break;
+            }
+            const double tol = 1e-10;
+            if (u >= ulo - tol && u <= uhi + tol && v >= vlo - tol && v <= vhi + tol) {
+                double x, y;
+                quad_map(Lx, X, Y, i0, j0, u, v, &x, &y);
+                if (fabs(x - qx) + fabs(y - qy) < 1e-9) {
+                    *px = i0 + 0.5 + u;
+                    *py = j0 + 0.5 + v;
+                    return 1;
+                }
+            }
+        }
+    return 0;
+}
+
+/* Preimages of n points q under the composed projection: the grids' inverses applied
+ * in reverse order. Points without a preimage get NaN. */
+void orc_inverse_points(int Lx, int Ly, int K, const double* grids, long long n, const double* q, double* p) {
+    const size_t N = (size_t)Lx * Ly;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long t = 0; t < n; ++t) {
+        double x = q[2 * t], y = q[2 * t + 1];
+        int ok = 1;
+        for (int k = K - 1; k >= 0 && ok; --k) {
+            const double* X = grids + (size_t)k * 2 * N;
+            const double* Y = X + N;
+            double px, py;
+            ok = invert_one(Lx, Ly, X, Y, x, y, &px, &py);
+            x = px;
+            y = py;
+        }
+        p[2 * t] = ok ? x : NAN;
+        p[2 * t + 1] = ok ? y : NAN;
+    }
+}
+

@@ -529,3 +529,96 @@ def test_linear_flow_strip_map_converges(orc):
     assert r.converged and r.max_area_error < 0.01
     mid = np.abs(m.xy[:, 0] - 16.0) < 1e-12
     assert np.max(np.abs(r.xy[mid, 0] - Lx * V[0] / sum(V))) < 0.01 * Lx
+
+
+# ---------------------------------------------------------------------------------
+# diagnostics of the composed projection: Tissot distortion (SI section 3) and the
+# inverse map (the main text's inverse graticule)
+# ---------------------------------------------------------------------------------
+
+def _affine_grid(L, A, b):
+    x = np.arange(L) + 0.5
+    X, Y = np.meshgrid(x, x)
+    return np.stack([A[0, 0] * X + A[0, 1] * Y + b[0], A[1, 0] * X + A[1, 1] * Y + b[1]])
+
+
+def _tissot(A):
+    s = np.linalg.svd(A, compute_uv=False)
+    return np.log(s[0] / s[1]), 2 * np.arcsin((s[0] - s[1]) / (s[0] + s[1]))
+
+
+def test_distortion_of_affine_and_composed_grids(orc):
+    # a bilinear grid of an affine map is that map everywhere (its quads extended too):
+    # the Jacobian is A, constant, so mean = max = the closed-form Tissot measures
+    L = 16
+    A1 = np.array([[2.0, 0.3], [0.1, 0.8]])
+    A2 = np.array([[0.7, -0.2], [0.4, 1.3]])
+    g1 = _affine_grid(L, A1, [0.2, -0.1])
+    g2 = _affine_grid(L, A2, [-1.0, 0.5])
+    e, et = _tissot(A1)
+    assert np.allclose(orc.distortion(g1[None]), [e, e, et, et], rtol=0, atol=1e-12)
+    # composition: T2(T1(r)) has the constant Jacobian A2 A1
+    e, et = _tissot(A2 @ A1)
+    assert np.allclose(orc.distortion(np.stack([g1, g2])), [e, e, et, et], rtol=0, atol=1e-12)
+    # identity and a pure rotation are conformal
+    assert np.allclose(orc.distortion(_affine_grid(L, np.eye(2), [0, 0])[None]), 0.0, atol=1e-12)
+    c, s = np.cos(0.4), np.sin(0.4)
+    assert np.allclose(orc.distortion(_affine_grid(L, np.array([[c, -s], [s, c]]), [3, 1])[None]), 0.0, atol=1e-12)
+
+
+def test_distortion_chain_rule_matches_finite_differences(orc):
+    # on the grids of a real cartogram: e at each quad centre from the chain-rule Jacobian
+    # agrees with the Jacobian of the composed point map by central differences
+    m = synth.make_workload("voronoi16_64", L=32, n=10)
+    r = orc.cartogram(m, blur=1.0)
+    g = r.grids
+    L = m.Lx
+    xc = np.arange(1, L) * 1.0
+    P0 = np.stack(np.meshgrid(xc, xc), axis=-1).reshape(-1, 2)
+    h = 1e-6
+
+    def T(p):
+        for k in range(g.shape[0]):
+            p = orc.map_points(g[k, 0], g[k, 1], p)
+        return p
+
+    Jx = (T(P0 + [h, 0]) - T(P0 - [h, 0])) / (2 * h)
+    Jy = (T(P0 + [0, h]) - T(P0 - [0, h])) / (2 * h)
+    J = np.stack([Jx, Jy], axis=-1)  # [n][2 (T component)][2 (d/dx, d/dy)]
+    s = np.linalg.svd(J, compute_uv=False)
+    e = np.log(s[:, 0] / s[:, 1])
+    et = 2 * np.arcsin((s[:, 0] - s[:, 1]) / (s[:, 0] + s[:, 1]))
+    d = orc.distortion(g)
+    assert abs(d[0] - e.mean()) < 1e-6 and abs(d[1] - e.max()) < 1e-6
+    assert abs(d[2] - et.mean()) < 1e-6 and abs(d[3] - et.max()) < 1e-6
+    assert d[1] > 0.1  # the map is not conformal
+
+
+def test_inverse_points_of_affine_grids(orc):
+    # maps that keep the box's points inside the box, as the cartogram's grids do (the
+    # inverse looks for preimages inside the box)
+    L = 16
+    A1 = np.array([[0.9, 0.05], [0.05, 0.85]])
+    A2 = np.array([[0.95, -0.05], [0.05, 0.9]])
+    b1, b2 = np.array([0.5, 0.8]), np.array([0.6, 0.4])
+    g = np.stack([_affine_grid(L, A1, b1), _affine_grid(L, A2, b2)])
+    rng = np.random.default_rng(11)
+    p = rng.uniform(1.0, L - 1.0, (50, 2))
+    q = (A2 @ (A1 @ p.T + b1[:, None]) + b2[:, None]).T
+    assert np.max(np.abs(orc.inverse_points(g, q) - p)) < 1e-10
+
+
+def test_inverse_points_undo_the_cartograms_point_map(orc):
+    # round trip through orc_map_points on the grids of a real cartogram, including
+    # points in the half-cell band along the walls
+    m = synth.make_workload("voronoi16_64", L=32, n=10)
+    g = orc.cartogram(m, blur=1.0).grids
+    rng = np.random.default_rng(12)
+    p = np.concatenate([rng.uniform(0.0, m.Lx, (300, 2)), [[0.1, 0.2], [31.9, 0.3], [0.25, 31.8], [31.95, 31.9]]])
+    q = p.copy()
+    for k in range(g.shape[0]):
+        q = orc.map_points(g[k, 0], g[k, 1], q)
+    back = orc.inverse_points(g, q)
+    assert np.max(np.abs(back - p)) < 1e-9
+    # a point outside the image of the box has no preimage
+    assert np.all(np.isnan(orc.inverse_points(g, np.array([[-5.0, 3.0]]))))
