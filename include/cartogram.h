@@ -167,6 +167,26 @@ int cartogram_integrate(cg_ctx* ctx, cg_stats* stats);
  * CG_EINVAL, CG_ECUDA. */
 int cartogram_project(cg_ctx* ctx, int64_t n, const double* xy_in, double* xy_out);
 
+/* Preimages under the composed projection (the main text's inverse graticule: features
+ * found on the cartogram identified in the original domain): every projected grid of the
+ * history inverted in reverse order. Each grid's map is the bilinear map that
+ * cartogram_project applies (the quads along the walls extended to the box edge); its
+ * inverse is found by Newton's method inside a quad, walking to the neighbouring quad
+ * until the solution lies in the current one. cartogram_inverse_project(project(p)) = p
+ * wherever the grids do not fold. Points without a preimage in the box (outside it, or
+ * where a walk does not settle) come back as NaN. xy_in and xy_out may alias and may be
+ * host or device memory. Errors: CG_EINVAL, CG_ECUDA. */
+int cartogram_inverse_project(cg_ctx* ctx, int64_t n, const double* xy_in, double* xy_out);
+
+/* Angular distortion of the composed projection (SI section 3, the Tissot indicatrix):
+ * at the centre of every quad of the original cell-centre lattice ((Lx-1)(Ly-1) points),
+ * the Jacobian of the composed bilinear maps by the chain rule, its singular values
+ * a >= b, e = ln(a/b) and e~ = 2 asin((a - b)/(a + b)). out[4] = {e_a, e_inf, e~_a,
+ * e~_inf}: the means and maxima over those points (SI: the average and the supremum
+ * over the Lx x Ly box). An empty history (the identity) gives zeros. FP64 on the
+ * stored displacements. Errors: CG_EINVAL, CG_ECUDA. */
+int cartogram_distortion(cg_ctx* ctx, double* out);
+
 /* Signed relative area errors A_i / A^_i - 1 of the current vertices, [n_regions]. */
 int cartogram_area_errors(cg_ctx* ctx, double* err);
 

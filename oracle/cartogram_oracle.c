@@ -753,7 +753,8 @@ static void locate_quad(int Lx, int Ly, double x, double y, int* i0, int* j0, do
 void orc_distortion(int Lx, int Ly, int K, const double* grids, double* out) {
     const size_t N = (size_t)Lx * Ly;
     double sum_e = 0.0, max_e = 0.0, sum_t = 0.0, max_t = 0.0;
-    for (int j = 0; j + 1 < Ly; ++j)
+#pragma omp parallel for schedule(static) reduction(+ : sum_e, sum_t) reduction(max : max_e, max_t)
+    for (int j = 0; j < Ly - 1; ++j)
         for (int i = 0; i + 1 < Lx; ++i) {
             double x = i + 1.0, y = j + 1.0;
             double a = 1.0, b = 0.0, c = 0.0, d = 1.0; /* J = [[a, b], [c, d]] */

@@ -25,7 +25,8 @@ __all__ = [
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
     "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
-    "cartogram_velocity_noalloc", "cartogram_last_error", "cartogram_destroy", "cartogram_batch_create",
+    "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion", "cartogram_last_error",
+    "cartogram_destroy", "cartogram_batch_create",
     "cartogram_batch_integrate", "cartogram_batch_last_error", "cartogram_batch_destroy", "Cartogram", "Batch",
 ]
 
@@ -103,6 +104,8 @@ def load(build_if_missing: bool = True):
         "cartogram_heun_step": (i, [_P, d, d, _P, _P, _P]),
         "cartogram_integrate_once": (i, [_P, _P, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(d)]),
         "cartogram_velocity_noalloc": (i, [i, i, _P, d, _P, _P]),
+        "cartogram_inverse_project": (i, [_P, ll, _P, _P]),
+        "cartogram_distortion": (i, [_P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
         "cartogram_batch_create": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P)]),
@@ -306,6 +309,20 @@ def cartogram_velocity_noalloc(Lx, Ly, spec, t, v_out, stream=None) -> None:
         raise CartogramError(rc, "cartogram_velocity_noalloc(%d, %d) failed" % (Lx, Ly))
 
 
+def cartogram_inverse_project(ctx, xy_in, xy_out):
+    pi_, _a = _ptr(xy_in, np.float64)
+    po, _ = _ptr(xy_out, np.float64, writable=True)
+    n = xy_in.shape[0] if hasattr(xy_in, "shape") else len(xy_in)
+    _check(ctx, load().cartogram_inverse_project(ctx, int(n), pi_, po))
+    return xy_out
+
+
+def cartogram_distortion(ctx) -> dict:
+    out = np.zeros(4)
+    _check(ctx, load().cartogram_distortion(ctx, out.ctypes.data))
+    return {"e_a": out[0], "e_inf": out[1], "et_a": out[2], "et_inf": out[3]}
+
+
 def cartogram_last_error(ctx) -> str:
     return (load().cartogram_last_error(ctx) or b"").decode()
 
@@ -405,6 +422,15 @@ class Cartogram:
 
     def project(self, xy, out=None):
         return cartogram_project(self.ctx, xy, out)
+
+    def inverse_project(self, xy, out=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64) if not hasattr(xy, "data_ptr") else xy
+        if out is None:
+            out = np.empty_like(xy)
+        return cartogram_inverse_project(self.ctx, xy, out)
+
+    def distortion(self):
+        return cartogram_distortion(self.ctx)
 
     def area_errors(self):
         return cartogram_area_errors(self.ctx, np.empty(self._map.n_regions))

@@ -75,6 +75,7 @@ struct cg_ctx {
   int hist_len = 0;
   double2* pts = nullptr;
   long long pts_cap = 0;
+  double* diag = nullptr;  // distortion scratch: per-block sums, maxima, results
 
   // persistent integration kernel
   cg::GridBarrier* gb = nullptr;
@@ -999,6 +1000,46 @@ int do_project(cg_ctx* c, int64_t n, const double* in, double* out) {
   return CG_OK;
 }
 
+// The first hist_len history slots as a device pointer table.
+template <typename T>
+int hist_table(cg_ctx* c) {
+  return ensure_slots<T>(c, (int)c->hist.size());
+}
+
+template <typename T>
+int do_distortion(cg_ctx* c, double* out) {
+  int r = hist_table<T>(c);
+  if (r) return r;
+  if (!c->diag) {
+    const int nb = cg::distortion_blocks(c->Lx, c->Ly);
+    CG_CUDA(c, cudaMalloc((void**)&c->diag, sizeof(double) * (2 * nb + 8)));
+  }
+  const int nb = cg::distortion_blocks(c->Lx, c->Ly);
+  double* part = c->diag;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(c->diag + 2 * nb);
+  double* res = c->diag + 2 * nb + 2;
+  cg::launch_distortion<T>((const void* const*)c->hist_d, c->hist_len, c->Lx, c->Ly, part, mx, res, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  double h[4];
+  CG_CUDA(c, cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  CG_CUDA(c, cudaMemcpy(out, h, sizeof h, cudaMemcpyDefault));
+  return CG_OK;
+}
+
+template <typename T>
+int do_inverse_project(cg_ctx* c, int64_t n, const double* in, double* out) {
+  if (n == 0) return CG_OK;
+  int r = hist_table<T>(c);
+  if (r || (r = ensure_pts(c, n))) return r;
+  CG_CUDA(c, cudaMemcpyAsync(c->pts, in, sizeof(double2) * n, cudaMemcpyDefault, c->stream));
+  cg::launch_inverse_points<T>((const void* const*)c->hist_d, c->hist_len, c->Lx, c->Ly, n, c->pts, c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  CG_CUDA(c, cudaMemcpyAsync(out, c->pts, sizeof(double2) * n, cudaMemcpyDefault, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
 template <typename T>
 int do_profile(cg_ctx* c, int reps, double* ms_out) {
   cudaStream_t s = c->stream;
@@ -1449,6 +1490,20 @@ int cartogram_integrate_once(cg_ctx* c, double* grid_out, long long* accepted, l
                   : do_integrate_once<double>(c, grid_out, accepted, rejected, t_end);
 }
 
+int cartogram_distortion(cg_ctx* c, double* out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (!out) return fail(c, CG_EINVAL, "NULL output");
+  return c->mixed ? do_distortion<float>(c, out) : do_distortion<double>(c, out);
+}
+
+int cartogram_inverse_project(cg_ctx* c, int64_t n, const double* xy_in, double* xy_out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (n < 0 || (n > 0 && (!xy_in || !xy_out))) return fail(c, CG_EINVAL, "bad point array");
+  return c->mixed ? do_inverse_project<float>(c, n, xy_in, xy_out) : do_inverse_project<double>(c, n, xy_in, xy_out);
+}
+
 const char* cartogram_last_error(const cg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
 void cartogram_destroy(cg_ctx* c) {
@@ -1461,7 +1516,7 @@ void cartogram_destroy(cg_ctx* c) {
   void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
                 c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
-                c->rho0};
+                c->rho0, c->diag};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);

@@ -175,6 +175,16 @@ template <typename T>
 void launch_outer_commit(OuterState* o, const IterInfo* info, const V2<T>* dres, int N, cudaStream_t s);
 void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphConditionalHandle handle, int after,
                          cudaStream_t s);
+// Diagnostics of the composed projection (history grids hist[0..K)): angular
+// distortion into out[4] (part: 2 * distortion_blocks doubles, max_bits: 2 words), and
+// the preimages of n points, in place.
+int distortion_blocks(int Lx, int Ly);
+template <typename T>
+void launch_distortion(const void* const* hist, int K, int Lx, int Ly, double* part, unsigned long long* max_bits,
+                       double* out, cudaStream_t s);
+template <typename T>
+void launch_inverse_points(const void* const* hist, int K, int Lx, int Ly, long long n, double2* pts,
+                           cudaStream_t s);
 template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>

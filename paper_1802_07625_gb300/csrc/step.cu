@@ -3,6 +3,7 @@
 #include "geometry.cuh"
 #include "linear.cuh"
 #include "outer.cuh"
+#include "diagnostics.cuh"
 #include "kernels.h"
 
 namespace cg {
@@ -127,6 +128,24 @@ void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphCondition
   outer_decide_kernel<<<1, 1, 0, s>>>(o, info, handle, after);
 }
 
+int distortion_blocks(int Lx, int Ly) { return blocks_for((long long)(Lx - 1) * (Ly - 1), 256, sm_count() * 8); }
+
+template <typename T>
+void launch_distortion(const void* const* hist, int K, int Lx, int Ly, double* part, unsigned long long* max_bits,
+                       double* out, cudaStream_t s) {
+  const int nb = distortion_blocks(Lx, Ly);
+  cudaMemsetAsync(max_bits, 0, 2 * sizeof(unsigned long long), s);
+  distortion_kernel<T><<<nb, 256, 0, s>>>(hist, K, Lx, Ly, part, max_bits);
+  distortion_finish_kernel<<<1, 1, 0, s>>>(part, nb, max_bits, (Lx - 1) * (Ly - 1), out);
+}
+
+template <typename T>
+void launch_inverse_points(const void* const* hist, int K, int Lx, int Ly, long long n, double2* pts,
+                           cudaStream_t s) {
+  if (n <= 0) return;
+  inverse_points_kernel<T><<<blocks_for(n, 128, 1 << 16), 128, 0, s>>>(hist, K, Lx, Ly, n, pts);
+}
+
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
                                V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
@@ -138,6 +157,10 @@ void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphCondition
   template void launch_fold_count<T>(const V2<T>*, int, int, unsigned long long*, cudaStream_t);   \
   template void launch_phi_spectrum<T>(const double*, T*, int, int, cudaStream_t);                  \
   template void launch_outer_commit<T>(OuterState*, const IterInfo*, const V2<T>*, int, cudaStream_t); \
+  template void launch_distortion<T>(const void* const*, int, int, int, double*, unsigned long long*,  \
+                                     double*, cudaStream_t);                                        \
+  template void launch_inverse_points<T>(const void* const*, int, int, int, long long, double2*,       \
+                                         cudaStream_t);                                             \
   template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
                                       int, cudaGraphConditionalHandle, int, cudaStream_t);          \
   template void launch_linear_step<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
