@@ -363,6 +363,12 @@ def run_ours(args):
         c.close()
         return 0
 
+    # angular distortion of the converged map (SI section 3; the paper's Table 1 reports
+    # these measures for its case studies) and the time of the diagnostic
+    t = time.perf_counter()
+    dist = c.distortion()
+    dist["seconds"] = time.perf_counter() - t
+
     # live per-kernel timing for the roofline (same stream, CUDA events)
     prof = c.profile(reps=20)
     esz = 4
@@ -481,6 +487,7 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
             "linear_flow": linear,
+            "distortion": dist,
             "batched": batched,
             "kernel_ms": prof,
             "launch_shapes": tune,
