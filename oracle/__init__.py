@@ -97,6 +97,7 @@ def lib():
         L.orc_flux_linear.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.orc_integrate_linear.argtypes = [ctypes.POINTER(Params), _D, _D, _D, _LL, _LL, _D]
         L.orc_distortion.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        L.orc_coverage.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _LL, _I, _D, _D]
         L.orc_inverse_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_longlong, _D, _D]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -249,6 +250,17 @@ def map_points(X, Y, pts) -> np.ndarray:
     Ly, Lx = X.shape
     out = np.empty_like(pts)
     lib().orc_map_points(Lx, Ly, _d(X), _d(Y), pts.shape[0], _d(pts), _d(out))
+    return out
+
+
+def coverage(m) -> np.ndarray:
+    """Area of every cell covered by every region, [n_regions][Ly][Lx]."""
+    ro = np.ascontiguousarray(m.ring_offsets, dtype=np.int64)
+    rr = np.ascontiguousarray(m.ring_region, dtype=np.int32)
+    xy = _f64(m.xy)
+    out = np.empty((m.n_regions, m.Ly, m.Lx))
+    lib().orc_coverage(m.Lx, m.Ly, m.n_regions, rr.size, ro.ctypes.data_as(_LL), rr.ctypes.data_as(_I), _d(xy),
+                       _d(out))
     return out
 
 

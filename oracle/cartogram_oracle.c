@@ -29,7 +29,8 @@
  *  orc_integrate                  uniform density -> identity; x-only density ->
  *                                 closed-form 1-D equalising map (pinned to the
  *                                 discretisation error only)
- *  orc_rasterize                  hand-computed coverages, total mass (pinned)
+ *  orc_rasterize, orc_coverage    hand-computed coverages, total mass; the density as
+ *                                 the coverage-weighted sum of the region densities (pinned)
  *  orc_region_areas, orc_area_errors, orc_map_points   closed forms (pinned)
  *  orc_flux_linear                single-mode and 2-D-mode closed forms, discrete
  *                                 continuity against the density change (pinned)
@@ -583,6 +584,54 @@ static double poly_area(const double* px, const double* py, int n) {
  *   rho[j][i] = d_out + sum_rings (d_region - d_out) * area(ring  intersect  cell_ij)
  * where the area of the ring inside the unit cell is exact (polygon clipping),
  * signed by the ring's orientation. */
+/* Add w * area(ring intersect cell) to rho[cell] for every cell the ring touches (the
+ * ring clipped to each row strip, then to each cell of the strip). */
+static void raster_ring(int Lx, int Ly, const double* xy, long long a, long long b, double w, double* rho) {
+    int n = (int)(b - a);
+    if (n < 3) return;
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (long long v = a; v < b; ++v) {
+        x0 = fmin(x0, xy[2 * v]); x1 = fmax(x1, xy[2 * v]);
+        y0 = fmin(y0, xy[2 * v + 1]); y1 = fmax(y1, xy[2 * v + 1]);
+    }
+    int cap = 16 * n + 64; /* each half-plane clip at most doubles the vertex count */
+    double* rx = (double*)malloc(sizeof(double) * n);
+    double* ry = (double*)malloc(sizeof(double) * n);
+    double* b1x = (double*)malloc(sizeof(double) * cap);
+    double* b1y = (double*)malloc(sizeof(double) * cap);
+    double* b2x = (double*)malloc(sizeof(double) * cap);
+    double* b2y = (double*)malloc(sizeof(double) * cap);
+    double* b3x = (double*)malloc(sizeof(double) * cap);
+    double* b3y = (double*)malloc(sizeof(double) * cap);
+    double* b4x = (double*)malloc(sizeof(double) * cap);
+    double* b4y = (double*)malloc(sizeof(double) * cap);
+    for (int v = 0; v < n; ++v) { rx[v] = xy[2 * (a + v)]; ry[v] = xy[2 * (a + v) + 1]; }
+    int j0 = (int)floor(y0), j1 = (int)ceil(y1);
+    int i0 = (int)floor(x0), i1 = (int)ceil(x1);
+    if (j0 < 0) j0 = 0;
+    if (i0 < 0) i0 = 0;
+    if (j1 > Ly) j1 = Ly;
+    if (i1 > Lx) i1 = Lx;
+    for (int j = j0; j < j1; ++j) {
+        /* the ring restricted to the row strip j <= y <= j+1 */
+        int m1 = clip_half(rx, ry, n, 1, (double)j, 1.0, b1x, b1y);
+        int m2 = clip_half(b1x, b1y, m1, 1, (double)(j + 1), -1.0, b2x, b2y);
+        if (m2 < 3) continue;
+        for (int i = i0; i < i1; ++i) {
+            int m3 = clip_half(b2x, b2y, m2, 0, (double)i, 1.0, b3x, b3y);
+            int m4 = clip_half(b3x, b3y, m3, 0, (double)(i + 1), -1.0, b4x, b4y);
+            if (m4 < 3) continue;
+            double cov = poly_area(b4x, b4y, m4);
+            if (cov != 0.0) {
+#pragma omp atomic
+                rho[(size_t)j * Lx + i] += w * cov;
+            }
+        }
+    }
+    free(rx); free(ry); free(b1x); free(b1y); free(b2x); free(b2y);
+    free(b3x); free(b3y); free(b4x); free(b4y);
+}
+
 void orc_rasterize(int Lx, int Ly, int n_regions, const double* values, const double* areas,
                    long long n_rings, const long long* ring_offsets, const int* ring_region,
                    const double* xy, double* rho) {
@@ -592,53 +641,20 @@ void orc_rasterize(int Lx, int Ly, int n_regions, const double* values, const do
     for (size_t k = 0; k < (size_t)Lx * Ly; ++k) rho[k] = d_out;
 #pragma omp parallel for schedule(dynamic, 1)
     for (long long k = 0; k < n_rings; ++k) {
-        long long a = ring_offsets[k], b = ring_offsets[k + 1];
-        int n = (int)(b - a);
-        if (n < 3) continue;
         int g = ring_region[k];
-        double w = values[g] / areas[g] - d_out;
-        double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
-        for (long long v = a; v < b; ++v) {
-            x0 = fmin(x0, xy[2 * v]); x1 = fmax(x1, xy[2 * v]);
-            y0 = fmin(y0, xy[2 * v + 1]); y1 = fmax(y1, xy[2 * v + 1]);
-        }
-        int cap = 16 * n + 64; /* each half-plane clip at most doubles the vertex count */
-        double* rx = (double*)malloc(sizeof(double) * n);
-        double* ry = (double*)malloc(sizeof(double) * n);
-        double* b1x = (double*)malloc(sizeof(double) * cap);
-        double* b1y = (double*)malloc(sizeof(double) * cap);
-        double* b2x = (double*)malloc(sizeof(double) * cap);
-        double* b2y = (double*)malloc(sizeof(double) * cap);
-        double* b3x = (double*)malloc(sizeof(double) * cap);
-        double* b3y = (double*)malloc(sizeof(double) * cap);
-        double* b4x = (double*)malloc(sizeof(double) * cap);
-        double* b4y = (double*)malloc(sizeof(double) * cap);
-        for (int v = 0; v < n; ++v) { rx[v] = xy[2 * (a + v)]; ry[v] = xy[2 * (a + v) + 1]; }
-        int j0 = (int)floor(y0), j1 = (int)ceil(y1);
-        int i0 = (int)floor(x0), i1 = (int)ceil(x1);
-        if (j0 < 0) j0 = 0;
-        if (i0 < 0) i0 = 0;
-        if (j1 > Ly) j1 = Ly;
-        if (i1 > Lx) i1 = Lx;
-        for (int j = j0; j < j1; ++j) {
-            /* the ring restricted to the row strip j <= y <= j+1 */
-            int m1 = clip_half(rx, ry, n, 1, (double)j, 1.0, b1x, b1y);
-            int m2 = clip_half(b1x, b1y, m1, 1, (double)(j + 1), -1.0, b2x, b2y);
-            if (m2 < 3) continue;
-            for (int i = i0; i < i1; ++i) {
-                int m3 = clip_half(b2x, b2y, m2, 0, (double)i, 1.0, b3x, b3y);
-                int m4 = clip_half(b3x, b3y, m3, 0, (double)(i + 1), -1.0, b4x, b4y);
-                if (m4 < 3) continue;
-                double cov = poly_area(b4x, b4y, m4);
-                if (cov != 0.0) {
-#pragma omp atomic
-                    rho[(size_t)j * Lx + i] += w * cov;
-                }
-            }
-        }
-        free(rx); free(ry); free(b1x); free(b1y); free(b2x); free(b2y);
-        free(b3x); free(b3y); free(b4x); free(b4y);
+        raster_ring(Lx, Ly, xy, ring_offsets[k], ring_offsets[k + 1], values[g] / areas[g] - d_out, rho);
     }
+}
+
+/* Coverage of every cell by every region (signed sum of its rings' clipped areas),
+ * cov[region][Ly][Lx]: the density is linear in the regions' densities through it. */
+void orc_coverage(int Lx, int Ly, int n_regions, long long n_rings, const long long* ring_offsets,
+                  const int* ring_region, const double* xy, double* cov) {
+    memset(cov, 0, sizeof(double) * (size_t)n_regions * Lx * Ly);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long k = 0; k < n_rings; ++k)
+        raster_ring(Lx, Ly, xy, ring_offsets[k], ring_offsets[k + 1], 1.0,
+                    cov + (size_t)ring_region[k] * Lx * Ly);
 }
 
 /* Map points through the projected grid (main text: the output of an integration

@@ -622,3 +622,68 @@ def test_inverse_points_undo_the_cartograms_point_map(orc):
     assert np.max(np.abs(back - p)) < 1e-9
     # a point outside the image of the box has no preimage
     assert np.all(np.isnan(orc.inverse_points(g, np.array([[-5.0, 3.0]]))))
+
+
+# ---------------------------------------------------------------------------------
+# FP64 reverse-mode reference of one outer iteration's loss (oracle/adjoint.py)
+# ---------------------------------------------------------------------------------
+
+def _adjoint_case(orc, L=32, n=8):
+    import torch
+
+    from oracle import adjoint as adj
+    m = synth.make_workload("voronoi16_64", L=L, n=n)
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    it = adj.Iteration(m, orc.coverage(m), A)
+    blur = 1.0
+    with torch.no_grad():
+        spec_t = it.spectrum(torch.tensor(m.values), torch.tensor(blur, dtype=torch.float64))
+    rho_p = np.tensordot(m.values / A * (A.sum() / m.values.sum()) - 1.0, orc.coverage(m), 1)
+    r = orc.integrate(orc.forward(1.0 + rho_p, blur))
+    return adj, m, A, it, blur, spec_t, r
+
+
+def test_adjoint_forward_replays_the_oracle_integration(orc):
+    import torch
+    adj, m, A, it, blur, spec_t, r = _adjoint_case(orc)
+    spec_c = orc.forward(1.0 + np.tensordot(m.values / A * (A.sum() / m.values.sum()) - 1.0, orc.coverage(m), 1), blur)
+    s = spec_t.numpy()
+    assert np.max(np.abs(s.ravel()[1:] - spec_c.ravel()[1:])) < 1e-11 * np.max(np.abs(spec_c))
+    steps = adj.accepted_steps(r.sched_h, r.sched_acc)
+    assert len(steps) == r.accepted
+    with torch.no_grad():
+        X, Y = it.integrate(spec_t, steps)
+    assert np.max(np.abs(X.numpy() - r.X)) < 1e-10 and np.max(np.abs(Y.numpy() - r.Y)) < 1e-10
+    # the loss as the oracle's own functions give it
+    lam = 1e-3
+    xy1 = orc.map_points(r.X, r.Y, m.xy)
+    A1 = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, xy1)
+    target = m.values * A1.sum() / m.values.sum()
+    ref = np.sum((np.log(A1) - np.log(target)) ** 2) + lam * np.sum((xy1 - m.xy) ** 2)
+    with torch.no_grad():
+        L, _ = it.loss(torch.tensor(m.values), torch.tensor(blur, dtype=torch.float64), steps, lam)
+    assert abs(float(L) - ref) < 1e-10 * abs(ref)
+
+
+def test_adjoint_gradient_matches_central_differences(orc):
+    import torch
+    adj, m, A, it, blur, spec_t, r = _adjoint_case(orc)
+    steps = adj.accepted_steps(r.sched_h, r.sched_acc)
+    lam = 1e-3
+    L, gv, gs = adj.gradient(it, m.values, blur, steps, lam)
+
+    def loss(values, b):
+        with torch.no_grad():
+            return float(it.loss(torch.tensor(values), torch.tensor(b, dtype=torch.float64), steps, lam)[0])
+
+    for i in (0, 3, m.n_regions - 1):
+        h = 1e-6 * m.values[i]
+        vp, vm = m.values.copy(), m.values.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (loss(vp, blur) - loss(vm, blur)) / (2 * h)
+        assert abs(fd - gv[i]) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gv))), (i, fd, gv[i])
+    h = 1e-6
+    fd = (loss(m.values, blur + h) - loss(m.values, blur - h)) / (2 * h)
+    assert abs(fd - gs) <= 1e-6 * abs(fd)
+    assert np.max(np.abs(gv)) > 0 and gs != 0
