@@ -25,7 +25,8 @@ __all__ = [
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
     "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
-    "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion", "cartogram_last_error",
+    "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion",
+    "cartogram_iteration_gradient", "cartogram_last_error",
     "cartogram_destroy", "cartogram_batch_create",
     "cartogram_batch_integrate", "cartogram_batch_last_error", "cartogram_batch_destroy", "Cartogram", "Batch",
 ]
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
         "cartogram_velocity_noalloc": (i, [i, i, _P, d, _P, _P]),
         "cartogram_inverse_project": (i, [_P, ll, _P, _P]),
         "cartogram_distortion": (i, [_P, _P]),
+        "cartogram_iteration_gradient": (i, [_P, _P, d, d, i, i, _P, _P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
         "cartogram_batch_create": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P)]),
@@ -323,6 +325,19 @@ def cartogram_distortion(ctx) -> dict:
     return {"e_a": out[0], "e_inf": out[1], "et_a": out[2], "et_inf": out[3]}
 
 
+def cartogram_iteration_gradient(ctx, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True):
+    """Loss of one outer iteration and (grad=True) its gradient w.r.t. values and blur."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    loss = ctypes.c_double()
+    gv = np.zeros_like(v) if grad else None
+    gb = ctypes.c_double()
+    _check(ctx, load().cartogram_iteration_gradient(ctx, v.ctypes.data, float(blur), float(lam), int(bool(replay)),
+                                                   int(checkpoint), ctypes.byref(loss),
+                                                   gv.ctypes.data if grad else None,
+                                                   ctypes.byref(gb) if grad else None))
+    return (loss.value, gv, gb.value) if grad else loss.value
+
+
 def cartogram_last_error(ctx) -> str:
     return (load().cartogram_last_error(ctx) or b"").decode()
 
@@ -431,6 +446,9 @@ class Cartogram:
 
     def distortion(self):
         return cartogram_distortion(self.ctx)
+
+    def iteration_gradient(self, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True):
+        return cartogram_iteration_gradient(self.ctx, values, blur, lam, replay, checkpoint, grad)
 
     def area_errors(self):
         return cartogram_area_errors(self.ctx, np.empty(self._map.n_regions))

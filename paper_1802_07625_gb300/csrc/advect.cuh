@@ -73,6 +73,10 @@ __device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
   if (st->bad) {
     status = kStepFail;
   } else if (e <= sp.atol) {
+    if (sp.sched) {
+      sp.sched[2 * st->accepted] = st->t;
+      sp.sched[2 * st->accepted + 1] = h;
+    }
     st->parity ^= 1;
     st->t += h;
     st->accepted += 1;

@@ -20,6 +20,31 @@ using cg::IterInfo;
 using cg::StepParams;
 using cg::V2;
 
+// Device workspace of the iteration gradient (FP64), allocated on first use.
+struct AdjWork {
+  int C = 0;                     // steps between checkpoints
+  double2* lam = nullptr;        // adjoint of the displacements [N]
+  double* L[2] = {nullptr, nullptr};  // field adjoints of two time levels [N][2]
+  double *a_rho = nullptr, *a_gx = nullptr, *a_gy = nullptr;  // node adjoints [N]
+  double *Crho = nullptr, *Cx = nullptr, *Cy = nullptr;       // their DCT-II [N]
+  double *lam_spec = nullptr, *specp = nullptr, *R = nullptr, *dens = nullptr;  // [N]
+  double2* AB = nullptr;         // inverse-pass intermediate [N]
+  double2* flux = nullptr;       // inverse-pass side output [N]
+  std::vector<double2*> v;       // fields of a segment's levels [C + 1][N]
+  std::vector<double*> rho;      // densities of a segment's levels [C + 1][N]
+  std::vector<double2*> D;       // displacements of a segment's levels [C + 1][N]
+  std::vector<double2*> ckpt;    // checkpointed displacements
+  double* sched = nullptr;       // recorded (t, h), [max_steps][2]
+  double* vals = nullptr;        // target values of the call [R]
+  double* dLdA = nullptr;        // [R]
+  double* gw = nullptr;          // d L / d w [R]
+  double* dsig = nullptr;        // [1]
+  double2* xy1 = nullptr;        // mapped vertices [n_vert]
+  double2* gv = nullptr;         // their adjoints [n_vert]
+  long long n_vert = 0;
+  int n_regions = 0;
+};
+
 struct cg_ctx {
   int Lx = 0, Ly = 0, log2Lx = 0, log2Ly = 0;
   double blur = 0.0;
@@ -76,6 +101,11 @@ struct cg_ctx {
   double2* pts = nullptr;
   long long pts_cap = 0;
   double* diag = nullptr;  // distortion scratch: per-block sums, maxima, results
+  int* prev = nullptr;     // ring predecessor of every vertex
+  double* sched_rec = nullptr;      // while recording: (t, h) of the accepted steps (device)
+  std::vector<double> sched;        // the last recorded schedule, [n][2]
+  bool sched_len_zero = false;      // the last recorded integration took no step
+  AdjWork* adj = nullptr;           // workspace of the iteration gradient
 
   // persistent integration kernel
   cg::GridBarrier* gb = nullptr;
@@ -160,6 +190,7 @@ StepParams step_params(const cg_ctx* c) {
   sp.rho_tol = c->opt.rho_tol;
   sp.h_min = 0.0;
   sp.max_steps = c->opt.max_steps;
+  sp.sched = c->sched_rec;
   return sp;
 }
 
@@ -563,6 +594,9 @@ void drop_outer_graph(cg_ctx* c) {
   ++c->gen;
 }
 
+template <typename T>
+int run_integration_host(cg_ctx* c);
+
 // Run one integration of the current spectrum; the projected grid ends in dres and
 // the outcome in info (device). Records the step-loop time between ev0 and ev1.
 template <typename T>
@@ -610,7 +644,14 @@ int run_integration(cg_ctx* c) {
     CG_CUDA(c, cudaEventRecord(c->ev1, s));
     return CG_OK;
   }
-  // host-driven loop: the same kernels; the kernels return at once after the end
+  return run_integration_host<T>(c);
+}
+
+// One integration with the step loop driven from the host (the same kernels; the
+// kernels of an attempt after the end return at once).
+template <typename T>
+int run_integration_host(cg_ctx* c) {
+  cudaStream_t s = c->stream;
   CG_CUDA(c, cudaEventRecord(c->ev0, s));
   const bool lin = c->opt.flow == CG_FLOW_LINEAR;
   if (lin) enqueue_init_linear<T>(c, 0, 0, s);
@@ -1040,6 +1081,254 @@ int do_inverse_project(cg_ctx* c, int64_t n, const double* in, double* out) {
   return CG_OK;
 }
 
+// ---- gradient of one outer iteration (FP64) -----------------------------------
+
+void free_adj(cg_ctx* c) {
+  AdjWork* a = c->adj;
+  if (!a) return;
+  std::vector<void*> ps = {a->lam, a->L[0], a->L[1], a->a_rho, a->a_gx, a->a_gy, a->Crho, a->Cx, a->Cy,
+                           a->lam_spec, a->specp, a->R, a->dens, a->AB, a->flux, a->sched, a->vals, a->dLdA,
+                           a->gw, a->dsig, a->xy1, a->gv};
+  for (auto p : a->v) ps.push_back(p);
+  for (auto p : a->rho) ps.push_back(p);
+  for (auto p : a->D) ps.push_back(p);
+  for (auto p : a->ckpt) ps.push_back(p);
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete a;
+  c->adj = nullptr;
+}
+
+int adj_alloc(cg_ctx* c, int C) {
+  if (c->adj && c->adj->C == C) return CG_OK;
+  free_adj(c);
+  AdjWork* a = new AdjWork();
+  c->adj = a;
+  a->C = C;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  CG_CUDA(c, cudaMalloc((void**)&a->lam, sizeof(double2) * N));
+  for (int k = 0; k < 2; ++k) CG_CUDA(c, cudaMalloc((void**)&a->L[k], sizeof(double) * 2 * N));
+  double** ds[] = {&a->a_rho, &a->a_gx, &a->a_gy, &a->Crho, &a->Cx, &a->Cy, &a->lam_spec, &a->specp, &a->R, &a->dens};
+  for (double** p : ds) CG_CUDA(c, cudaMalloc((void**)p, sizeof(double) * N));
+  CG_CUDA(c, cudaMalloc((void**)&a->AB, sizeof(double2) * N));
+  CG_CUDA(c, cudaMalloc((void**)&a->flux, sizeof(double2) * N));
+  a->v.assign(C + 1, nullptr);
+  a->rho.assign(C + 1, nullptr);
+  a->D.assign(C + 1, nullptr);
+  for (int k = 0; k <= C; ++k) {
+    CG_CUDA(c, cudaMalloc((void**)&a->v[k], sizeof(double2) * N));
+    CG_CUDA(c, cudaMalloc((void**)&a->rho[k], sizeof(double) * N));
+    CG_CUDA(c, cudaMalloc((void**)&a->D[k], sizeof(double2) * N));
+  }
+  CG_CUDA(c, cudaMalloc((void**)&a->sched, sizeof(double) * 2 * (size_t)c->opt.max_steps));
+  a->n_regions = c->R_n;
+  a->n_vert = c->n_vert;
+  CG_CUDA(c, cudaMalloc((void**)&a->vals, sizeof(double) * c->R_n));
+  CG_CUDA(c, cudaMalloc((void**)&a->dLdA, sizeof(double) * c->R_n));
+  CG_CUDA(c, cudaMalloc((void**)&a->gw, sizeof(double) * c->R_n));
+  CG_CUDA(c, cudaMalloc((void**)&a->dsig, sizeof(double)));
+  CG_CUDA(c, cudaMalloc((void**)&a->xy1, sizeof(double2) * std::max<long long>(1, c->n_vert)));
+  CG_CUDA(c, cudaMalloc((void**)&a->gv, sizeof(double2) * std::max<long long>(1, c->n_vert)));
+  return CG_OK;
+}
+
+// Field v (and density) of the FP64 path at time tau, from the iteration's spectrum.
+void adj_field(cg_ctx* c, double tau, double2* v, double* rho) {
+  AdjWork* a = c->adj;
+  cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, c->spec64, a->AB, (const double2*)c->Wx,
+                              (const double2*)c->Ex, c->st, cg::kModeFixed, tau, 0, 0, 0u, c->stream);
+  cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, v, nullptr, rho, (const double2*)c->Wy,
+                              (const double2*)c->Ey, c->st, cg::kModeFixed, c->stream);
+}
+
+// One predictor-corrector step of all points with the fixed step h (the step kernel).
+void adj_step(cg_ctx* c, const double2* v0, const double2* v1, const double2* din, double2* dout, double h) {
+  cg::launch_heun<double>(c->st, step_params(c), v0, v1, (double2*)din, dout, c->Lx, c->Ly, cg::kModeFixed, h, 0,
+                          0, c->tune.heun_bps, c->stream);
+}
+
+// Level times of the schedule: tau_0 = 0, tau_{n+1} = tau_n + h_n (the device's sums).
+double adj_tau(const std::vector<double>& sch, int n) {
+  const int N = (int)sch.size() / 2;
+  if (n < N) return sch[2 * n];
+  return sch[2 * (N - 1)] + sch[2 * (N - 1) + 1];
+}
+
+// Process one time level's field adjoint: through v = -g/rho and the transposed
+// transforms into the spectrum adjoint; clears the level's buffer.
+void adj_level(cg_ctx* c, double* L, const double2* v, const double* rho, double tau) {
+  AdjWork* a = c->adj;
+  cudaStream_t s = c->stream;
+  cg::launch_node_adjoint(L, v, rho, a->a_rho, a->a_gx, a->a_gy, c->Lx, c->Ly, s);
+  double* ins[3] = {a->a_rho, a->a_gx, a->a_gy};
+  double* outs[3] = {a->Crho, a->Cx, a->Cy};
+  for (int k = 0; k < 3; ++k)
+    cg::launch_fwd<double>(c->log2Lx, c->log2Ly, ins[k], a->R, outs[k], nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                           nullptr, nullptr, s);
+  cg::launch_spec_accumulate(a->Crho, a->Cx, a->Cy, a->lam_spec, tau, c->Lx, c->Ly, s);
+  cudaMemsetAsync(L, 0, sizeof(double) * 2 * (size_t)c->Lx * c->Ly, s);
+}
+
+int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, double lam, int replay, int C,
+                          double* loss_out, double* grad_values, double* grad_blur) {
+  cudaStream_t s = c->stream;
+  const int R = c->R_n;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  std::vector<double> V(R);
+  CG_CUDA(c, cudaMemcpy(V.data(), values_in, sizeof(double) * R, cudaMemcpyDefault));
+  for (int i = 0; i < R; ++i)
+    if (!is_finite(V[i]) || !(V[i] > 0.0)) return fail(c, CG_EINVAL, "value %d is not positive and finite", i);
+  if (replay && c->sched.empty() && !(c->sched_len_zero))
+    return fail(c, CG_ESTATE, "no recorded schedule: call with replay = 0 first");
+  int r = adj_alloc(c, C);
+  if (r) return r;
+  AdjWork* a = c->adj;
+  CG_CUDA(c, cudaMemcpyAsync(a->vals, V.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
+  // areas of the current map and the rasterisation weights of these values
+  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
+                   c->err_d, c->w, c->info, s);
+  std::vector<double> A(R);
+  CG_CUDA(c, cudaMemcpyAsync(A.data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  // density and spectrum with the blur of this iteration
+  const double decay_k = std::pow(c->opt.blur_decay, (double)c->hist_len);
+  const double sigma = blur * decay_k;
+  CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * N, s));
+  cg::launch_raster(c->xy, c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, (int)c->n_vert, s);
+  cg::launch_blur_tables(nullptr, sigma, c->bx, c->by, c->Lx, c->Ly, s);
+  c->blur_tab_sigma = -1.0;
+  cg::launch_fwd<double>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                         c->bx, c->by, s);
+  c->have_spectrum = true;
+  CG_CUDA(c, cudaGetLastError());
+  // the step schedule: recorded by an adaptive integration, or the last one reused
+  if (!replay) {
+    c->sched_rec = a->sched;
+    r = run_integration_host<double>(c);
+    c->sched_rec = nullptr;
+    if (r || (r = read_info(c))) return r;
+    const IterInfo inf = *c->info_h;
+    if (inf.status != cg::kDone)
+      return fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
+                  "integration ended with status %d after %lld/%lld steps", inf.status, inf.accepted, inf.rejected);
+    c->sched.assign(2 * (size_t)inf.accepted, 0.0);
+    if (inf.accepted > 0)
+      CG_CUDA(c, cudaMemcpy(c->sched.data(), a->sched, sizeof(double) * 2 * inf.accepted, cudaMemcpyDeviceToHost));
+    c->sched_len_zero = inf.accepted == 0;
+  }
+  const std::vector<double>& sch = c->sched;
+  const int NS = (int)sch.size() / 2;
+  // forward replay with checkpoints every C steps
+  const int nck = NS / C + 1;
+  while ((int)a->ckpt.size() < nck) {
+    double2* p = nullptr;
+    CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double2) * N));
+    a->ckpt.push_back(p);
+  }
+  CG_CUDA(c, cudaMemsetAsync(a->ckpt[0], 0, sizeof(double2) * N, s));
+  CG_CUDA(c, cudaMemsetAsync(a->D[0], 0, sizeof(double2) * N, s));
+  {
+    int cur = 0;  // v[cur] holds the field of level n
+    adj_field(c, 0.0, a->v[0], a->rho[0]);
+    double2* din = a->D[0];
+    double2* dout = a->D[1];
+    for (int n = 0; n < NS; ++n) {
+      adj_field(c, adj_tau(sch, n + 1), a->v[1 - cur], a->rho[1 - cur]);
+      adj_step(c, a->v[cur], a->v[1 - cur], din, dout, sch[2 * n + 1]);
+      std::swap(din, dout);
+      cur = 1 - cur;
+      if ((n + 1) % C == 0 && (n + 1) / C < nck)
+        CG_CUDA(c, cudaMemcpyAsync(a->ckpt[(n + 1) / C], din, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+    }
+    // the vertices through the final grid, and their areas
+    cg::launch_map_points<double>(c->xy, a->xy1, c->n_vert, din, c->Lx, c->Ly, s);
+  }
+  CG_CUDA(c, cudaGetLastError());
+  cg::launch_areas(a->xy1, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
+                   c->err_d, c->w, c->info, s);
+  std::vector<double> A1(R);
+  std::vector<double2> X0(c->n_vert), X1(c->n_vert);
+  CG_CUDA(c, cudaMemcpyAsync(A1.data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  CG_CUDA(c, cudaMemcpyAsync(X1.data(), a->xy1, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToHost, s));
+  CG_CUDA(c, cudaMemcpyAsync(X0.data(), c->xy, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToHost, s));
+  CG_CUDA(c, cudaStreamSynchronize(s));
+  // loss: sum_i (ln A'_i - ln A^_i)^2 + lam sum_v |X'_v - X_v|^2, A^_i = V_i sum A' / sum V
+  double sV = 0.0, sA1 = 0.0, sA = 0.0;
+  for (int i = 0; i < R; ++i) {
+    sV += V[i];
+    sA1 += A1[i];
+    sA += A[i];
+  }
+  std::vector<double> res(R);
+  double L = 0.0, sres = 0.0;
+  for (int i = 0; i < R; ++i) {
+    if (!(A1[i] > 0.0)) return fail(c, CG_EFOLD, "region %d has non-positive mapped area %g", i, A1[i]);
+    res[i] = std::log(A1[i]) - std::log(V[i] * sA1 / sV);
+    L += res[i] * res[i];
+    sres += res[i];
+  }
+  double pen = 0.0;
+  for (long long v = 0; v < c->n_vert; ++v) {
+    const double dx = X1[v].x - X0[v].x, dy = X1[v].y - X0[v].y;
+    pen += dx * dx + dy * dy;
+  }
+  L += lam * pen;
+  if (loss_out) *loss_out = L;
+  if (grad_values || grad_blur) {
+    // d L / d A'_j and the direct d L / d V_j through A^
+    std::vector<double> dLdA(R), gV(R);
+    for (int j = 0; j < R; ++j) {
+      dLdA[j] = 2.0 * res[j] / A1[j] - 2.0 * sres / sA1;
+      gV[j] = -2.0 * res[j] / V[j] + 2.0 * sres / sV;
+    }
+    CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dLdA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
+    cg::launch_vertex_adjoint(a->xy1, c->xy, c->next, c->prev, c->vreg, a->dLdA, lam, a->gv, (double*)a->lam, c->Lx,
+                              c->Ly, (int)c->n_vert, s);
+    CG_CUDA(c, cudaMemsetAsync(a->lam_spec, 0, sizeof(double) * N, s));
+    CG_CUDA(c, cudaMemsetAsync(a->L[0], 0, sizeof(double) * 2 * N, s));
+    CG_CUDA(c, cudaMemsetAsync(a->L[1], 0, sizeof(double) * 2 * N, s));
+    // backwards over the segments; L[hi] holds level n + 1, L[lo] level n
+    int hi = 0, lo = 1;
+    const int nseg = (NS + C - 1) / C;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int n0 = sg * C, n1 = std::min(n0 + C, NS);
+      CG_CUDA(c, cudaMemcpyAsync(a->D[0], a->ckpt[sg], sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+      for (int k = 0; k <= n1 - n0; ++k) adj_field(c, adj_tau(sch, n0 + k), a->v[k], a->rho[k]);
+      for (int k = 0; k < n1 - n0 - 1; ++k) adj_step(c, a->v[k], a->v[k + 1], a->D[k], a->D[k + 1], sch[2 * (n0 + k) + 1]);
+      for (int n = n1 - 1; n >= n0; --n) {
+        const int k = n - n0;
+        cg::launch_heun_adjoint(a->D[k], a->v[k], a->v[k + 1], sch[2 * n + 1], a->lam, a->L[lo], a->L[hi], c->Lx,
+                                c->Ly, s);
+        adj_level(c, a->L[hi], a->v[k + 1], a->rho[k + 1], adj_tau(sch, n + 1));
+        std::swap(hi, lo);
+      }
+    }
+    // level 0 (its field is the first segment's level 0, still in place)
+    if (NS > 0) adj_level(c, a->L[hi], a->v[0], a->rho[0], 0.0);
+    CG_CUDA(c, cudaGetLastError());
+    // blur derivative, then the density adjoint by an inverse-type cosine sum
+    cg::launch_spec_tail(a->lam_spec, c->spec64, c->bx, c->by, sigma, a->specp, a->dsig, c->Lx, c->Ly, s);
+    cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, a->specp, a->AB, (const double2*)c->Wx,
+                                (const double2*)c->Ex, c->st, cg::kModeFlux, 0.0, 0, 0, 0u, s);
+    cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, a->flux, nullptr, a->dens,
+                                (const double2*)c->Wy, (const double2*)c->Ey, c->st, cg::kModeFlux, s);
+    cg::launch_raster_adjoint(c->xy, c->next, c->vreg, a->dens, a->gw, R, c->Lx, c->Ly, (int)c->n_vert, s);
+    CG_CUDA(c, cudaGetLastError());
+    std::vector<double> gw(R);
+    double dsig = 0.0;
+    CG_CUDA(c, cudaMemcpyAsync(gw.data(), a->gw, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    CG_CUDA(c, cudaMemcpyAsync(&dsig, a->dsig, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CG_CUDA(c, cudaStreamSynchronize(s));
+    // w_i = (V_i / A_i)(sum A / sum V) - 1
+    double sgw = 0.0;
+    for (int i = 0; i < R; ++i) sgw += gw[i] * V[i] / A[i];
+    for (int j = 0; j < R; ++j) gV[j] += gw[j] * sA / (A[j] * sV) - sA / (sV * sV) * sgw;
+    if (grad_values) CG_CUDA(c, cudaMemcpy(grad_values, gV.data(), sizeof(double) * R, cudaMemcpyDefault));
+    if (grad_blur) *grad_blur = dsig * decay_k;
+  }
+  // leave the context's areas and weights those of its current map and values
+  return run_areas(c);
+}
+
 template <typename T>
 int do_profile(cg_ctx* c, int reps, double* ms_out) {
   cudaStream_t s = c->stream;
@@ -1102,8 +1391,14 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
   return CG_OK;
 }
 
+void free_adj(cg_ctx* c);
+
 void free_regions(cg_ctx* c) {
   drop_outer_graph(c);  // it holds the map's buffers
+  free_adj(c);
+  if (c->prev) cudaFree(c->prev);
+  c->prev = nullptr;
+  c->sched.clear();
   void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
                 c->xy, c->xy0, c->ring_area, c->area, c->err_d, c->w};
   for (void* p : ps)
@@ -1325,6 +1620,12 @@ int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values,
   CG_CUDA(c, cudaMemcpy(c->reg_rings, reg_rings.data(), sizeof(int) * n_rings, cudaMemcpyHostToDevice));
   CG_CUDA(c, cudaMemcpy(c->next, next.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
   CG_CUDA(c, cudaMemcpy(c->vreg, vreg.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+  {
+    std::vector<int> prev(nv);
+    for (long long v = 0; v < nv; ++v) prev[next[v]] = (int)v;
+    CG_CUDA(c, cudaMalloc((void**)&c->prev, sizeof(int) * nv));
+    CG_CUDA(c, cudaMemcpy(c->prev, prev.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+  }
   CG_CUDA(c, cudaMemcpy(c->xy, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
   CG_CUDA(c, cudaMemcpy(c->xy0, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
   c->have_regions = true;
@@ -1504,6 +1805,18 @@ int cartogram_inverse_project(cg_ctx* c, int64_t n, const double* xy_in, double*
   return c->mixed ? do_inverse_project<float>(c, n, xy_in, xy_out) : do_inverse_project<double>(c, n, xy_in, xy_out);
 }
 
+int cartogram_iteration_gradient(cg_ctx* c, const double* values, double blur_width, double lambda, int replay,
+                                 int checkpoint, double* loss, double* grad_values, double* grad_blur) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (c->mixed || c->opt.flow != CG_FLOW_DIFFUSION)
+    return fail(c, CG_EINVAL, "the gradient needs the FP64 path and the diffusion flow");
+  if (!values || !is_finite(blur_width) || blur_width < 0.0 || !is_finite(lambda) || lambda < 0.0 || checkpoint < 1)
+    return fail(c, CG_EINVAL, "bad gradient arguments");
+  if (!loss && !grad_values && !grad_blur) return fail(c, CG_EINVAL, "no output");
+  return do_iteration_gradient(c, values, blur_width, lambda, replay, checkpoint, loss, grad_values, grad_blur);
+}
+
 const char* cartogram_last_error(const cg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
 void cartogram_destroy(cg_ctx* c) {
@@ -1522,6 +1835,7 @@ void cartogram_destroy(cg_ctx* c) {
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);
   for (void* p : c->hist) cudaFree(p);
   if (c->info_h) cudaFreeHost(c->info_h);
+  free_adj(c);
   if (c->outer) cudaFree(c->outer);
   if (c->outer_h) cudaFreeHost(c->outer_h);
   if (c->sigma_d) cudaFree(c->sigma_d);

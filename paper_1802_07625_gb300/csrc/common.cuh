@@ -119,6 +119,7 @@ struct StepAcc {
 struct StepParams {
   double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
   long long max_steps;
+  double* sched;  // if not null: (t, h) of every accepted step, [max_steps][2]
 };
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {

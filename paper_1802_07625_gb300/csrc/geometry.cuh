@@ -35,48 +35,56 @@ __device__ __forceinline__ void raster_piece(double ax, double ay, double bx, do
   }
 }
 
+// The pieces of edge P -> Q cut at the grid lines (each inside one cell), in order:
+// piece(ax, ay, bx, by) for every piece.
+template <typename F>
+__device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly, F&& piece) {
+  const double dx = Q.x - P.x, dy = Q.y - P.y;
+  // next grid line crossed along x and along y, as edge parameters in (0, 1]
+  double gx = 0.0, gy = 0.0, sx = 2.0, sy = 2.0;
+  const double stx = dx > 0.0 ? 1.0 : -1.0, sty = dy > 0.0 ? 1.0 : -1.0;
+  if (dx != 0.0) {
+    gx = dx > 0.0 ? floor(P.x) + 1.0 : ceil(P.x) - 1.0;
+    sx = (gx - P.x) / dx;
+  }
+  gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
+  sy = (gy - P.y) / dy;
+  double ax = P.x, ay = P.y;
+  const int guard = Lx + Ly + 4;
+  for (int it = 0; it < guard; ++it) {
+    const double s1 = fmin(fmin(sx, sy), 1.0);
+    double bx, by;
+    if (s1 >= 1.0) {
+      bx = Q.x;
+      by = Q.y;
+    } else {
+      bx = P.x + s1 * dx;
+      by = P.y + s1 * dy;
+    }
+    piece(ax, ay, bx, by);
+    if (s1 >= 1.0) break;
+    if (sx <= s1) {
+      gx += stx;
+      sx = (gx - P.x) / dx;
+    }
+    if (sy <= s1) {
+      gy += sty;
+      sy = (gy - P.y) / dy;
+    }
+    ax = bx;
+    ay = by;
+  }
+}
+
 __global__ void raster_edges_kernel(const double2* __restrict__ xy, const int* __restrict__ next,
                                     const int* __restrict__ vreg, const double* __restrict__ w,
                                     double* __restrict__ acc, int Lx, int Ly, int n) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const double wt = w[vreg[v]];
     const double2 P = xy[v], Q = xy[next[v]];
-    const double dx = Q.x - P.x, dy = Q.y - P.y;
-    if (wt == 0.0 || dy == 0.0) continue;
-    // next grid line crossed along x and along y, as edge parameters in (0, 1]
-    double gx = 0.0, gy = 0.0, sx = 2.0, sy = 2.0;
-    const double stx = dx > 0.0 ? 1.0 : -1.0, sty = dy > 0.0 ? 1.0 : -1.0;
-    if (dx != 0.0) {
-      gx = dx > 0.0 ? floor(P.x) + 1.0 : ceil(P.x) - 1.0;
-      sx = (gx - P.x) / dx;
-    }
-    gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
-    sy = (gy - P.y) / dy;
-    double ax = P.x, ay = P.y;
-    const int guard = Lx + Ly + 4;
-    for (int it = 0; it < guard; ++it) {
-      const double s1 = fmin(fmin(sx, sy), 1.0);
-      double bx, by;
-      if (s1 >= 1.0) {
-        bx = Q.x;
-        by = Q.y;
-      } else {
-        bx = P.x + s1 * dx;
-        by = P.y + s1 * dy;
-      }
-      raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly);
-      if (s1 >= 1.0) break;
-      if (sx <= s1) {
-        gx += stx;
-        sx = (gx - P.x) / dx;
-      }
-      if (sy <= s1) {
-        gy += sty;
-        sy = (gy - P.y) / dy;
-      }
-      ax = bx;
-      ay = by;
-    }
+    if (wt == 0.0 || Q.y - P.y == 0.0) continue;
+    edge_pieces(P, Q, Lx, Ly,
+                [&](double ax, double ay, double bx, double by) { raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly); });
   }
 }
 

@@ -185,6 +185,26 @@ void launch_distortion(const void* const* hist, int K, int Lx, int Ly, double* p
 template <typename T>
 void launch_inverse_points(const void* const* hist, int K, int Lx, int Ly, long long n, double2* pts,
                            cudaStream_t s);
+// Adjoint of one outer iteration (FP64): one predictor-corrector step backwards
+// (positions d before the step, fields v0, v1; lam in place; field adjoints scattered
+// into L0, L1 [N][2]); a level's field adjoint through v = -g/rho; its transposed
+// transforms accumulated into the spectrum adjoint; the blur derivative and the input of
+// the density adjoint; the rasteriser's adjoint (lam: density adjoint, overwritten by its
+// row suffix sums); the loss adjoint of the mapped vertices scattered into the final
+// displacements' adjoint lamD [N][2].
+void launch_heun_adjoint(const double2* d, const double2* v0, const double2* v1, double h, double2* lam, double* L0,
+                         double* L1, int Lx, int Ly, cudaStream_t s);
+void launch_node_adjoint(const double* L, const double2* v, const double* rho, double* a_rho, double* a_gx,
+                         double* a_gy, int Lx, int Ly, cudaStream_t s);
+void launch_spec_accumulate(const double* Crho, const double* Cx, const double* Cy, double* lam_spec, double tau,
+                            int Lx, int Ly, cudaStream_t s);
+void launch_spec_tail(const double* lam_spec, const double* spec, const double* bx, const double* by, double sigma,
+                      double* specp, double* dsigma, int Lx, int Ly, cudaStream_t s);
+void launch_raster_adjoint(const double2* xy, const int* next, const int* vreg, double* lam, double* grad_w,
+                           int n_regions, int Lx, int Ly, int n_vert, cudaStream_t s);
+void launch_vertex_adjoint(const double2* xy1, const double2* xy0, const int* next, const int* prev,
+                           const int* vreg, const double* dLdA, double lam, double2* g, double* lamD, int Lx,
+                           int Ly, int n_vert, cudaStream_t s);
 template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>

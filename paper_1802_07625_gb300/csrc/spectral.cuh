@@ -253,7 +253,7 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     const T vx = -gx * inv, vy = -gy * inv;
     const size_t o = (size_t)j * Lx + c0 + cc;
     out[o] = mk2<T>(vx, vy);
-    if (rho_out) rho_out[o] = rho;
+    if (rho_out) rho_out[o] = raw ? rp : rho;  // flux mode: the plain cosine sum
     dev = max(dev, fabs(rp));
     v2max = max(v2max, vx * vx + vy * vy);
   }

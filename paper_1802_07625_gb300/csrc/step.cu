@@ -4,6 +4,7 @@
 #include "linear.cuh"
 #include "outer.cuh"
 #include "diagnostics.cuh"
+#include "adjoint.cuh"
 #include "kernels.h"
 
 namespace cg {
@@ -144,6 +145,54 @@ void launch_inverse_points(const void* const* hist, int K, int Lx, int Ly, long 
                            cudaStream_t s) {
   if (n <= 0) return;
   inverse_points_kernel<T><<<blocks_for(n, 128, 1 << 16), 128, 0, s>>>(hist, K, Lx, Ly, n, pts);
+}
+
+// ---- adjoint of one outer iteration (FP64) ----------------------------------------
+
+void launch_heun_adjoint(const double2* d, const double2* v0, const double2* v1, double h, double2* lam, double* L0,
+                         double* L1, int Lx, int Ly, cudaStream_t s) {
+  int log2Lx = 0;
+  while ((1 << log2Lx) < Lx) ++log2Lx;
+  heun_adjoint_kernel<<<blocks_for((long long)Lx * Ly, 256, sm_count() * 8), 256, 0, s>>>(d, v0, v1, h, lam, L0, L1,
+                                                                                          Lx, Ly, log2Lx);
+}
+
+void launch_node_adjoint(const double* L, const double2* v, const double* rho, double* a_rho, double* a_gx,
+                         double* a_gy, int Lx, int Ly, cudaStream_t s) {
+  node_adjoint_kernel<<<blocks_for((long long)Lx * Ly, 256, 4096), 256, 0, s>>>(L, v, rho, a_rho, a_gx, a_gy, Lx,
+                                                                               Lx * Ly);
+}
+
+void launch_spec_accumulate(const double* Crho, const double* Cx, const double* Cy, double* lam_spec, double tau,
+                            int Lx, int Ly, cudaStream_t s) {
+  spec_accumulate_kernel<<<blocks_for((long long)Lx * Ly, 256, 4096), 256, 0, s>>>(Crho, Cx, Cy, lam_spec, tau, Lx,
+                                                                                  Ly);
+}
+
+void launch_spec_tail(const double* lam_spec, const double* spec, const double* bx, const double* by, double sigma,
+                      double* specp, double* dsigma, int Lx, int Ly, cudaStream_t s) {
+  cudaMemsetAsync(dsigma, 0, sizeof(double), s);
+  spec_tail_kernel<<<blocks_for((long long)Lx * Ly, 256, 1024), 256, 0, s>>>(lam_spec, spec, bx, by, sigma, specp,
+                                                                            dsigma, Lx, Ly);
+}
+
+void launch_raster_adjoint(const double2* xy, const int* next, const int* vreg, double* lam, double* grad_w,
+                           int n_regions, int Lx, int Ly, int n_vert, cudaStream_t s) {
+  row_suffix_kernel<<<Ly, 32, 0, s>>>(lam, Lx);
+  cudaMemsetAsync(grad_w, 0, sizeof(double) * n_regions, s);
+  if (n_vert > 0)
+    raster_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy, next, vreg, lam, grad_w, Lx, Ly,
+                                                                          n_vert);
+}
+
+void launch_vertex_adjoint(const double2* xy1, const double2* xy0, const int* next, const int* prev,
+                           const int* vreg, const double* dLdA, double lam, double2* g, double* lamD, int Lx,
+                           int Ly, int n_vert, cudaStream_t s) {
+  cudaMemsetAsync(lamD, 0, sizeof(double) * 2 * (size_t)Lx * Ly, s);
+  if (n_vert <= 0) return;
+  vertex_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy1, xy0, next, prev, vreg, dLdA, lam, g,
+                                                                        n_vert);
+  map_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy0, g, lamD, Lx, Ly, n_vert);
 }
 
 #define CG_INSTANTIATE_STEP(T)                                                                      \
