@@ -294,6 +294,37 @@ def run_batched(args, P, synth, flush, stream):
             c.close()
 
 
+def run_gradient(args, P, synth):
+    """The differentiation workload: one outer iteration of the 512^2 clustered map (FP64
+    path, blur 2) with the gradient of the area/displacement loss w.r.t. its 300 target
+    values and the blur width, checkpoints every 8 steps. Host clock around the
+    synchronous calls (forward with schedule recording; forward + reverse)."""
+    import torch
+    m = synth.make_workload("clustered300_512")
+    blur = synth.WORKLOADS["clustered300_512"]["blur"]
+    c = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64")
+    try:
+        c.set_map(m)
+        c.iteration_gradient(m.values, blur, 1e-3)  # warm-up (allocations, launch shapes)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.grad_steps):
+            c.iteration_gradient(m.values, blur, 1e-3, replay=True, grad=False)
+        fwd = (time.perf_counter() - t) / args.grad_steps
+        t = time.perf_counter()
+        for _ in range(args.grad_steps):
+            loss, gv, gb = c.iteration_gradient(m.values, blur, 1e-3, replay=True)
+        both = (time.perf_counter() - t) / args.grad_steps
+        return {"workload": "clustered300_512, one outer iteration, FP64, checkpoints every 8 steps",
+                "loss": loss, "grad_norm": float(np.linalg.norm(gv)), "grad_blur": gb,
+                "s_forward_replay": fwd, "s_forward_and_gradient": both, "reverse_over_forward": both / fwd - 1.0,
+                "timing": "host wall clock around cartogram_iteration_gradient, mean of %d" % args.grad_steps}
+    except P.CartogramError as e:
+        return {"error": str(e)}
+    finally:
+        c.close()
+
+
 def run_ours(args):
     import torch
 
@@ -462,6 +493,7 @@ def run_ours(args):
         lc.close()
 
     batched = run_batched(args, P, synth, flush, stream) if args.batch_steps > 0 else None
+    gradient = run_gradient(args, P, synth) if args.grad_steps > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -489,6 +521,7 @@ def run_ours(args):
             "linear_flow": linear,
             "distortion": dist,
             "batched": batched,
+            "gradient": gradient,
             "kernel_ms": prof,
             "launch_shapes": tune,
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -519,6 +552,8 @@ def main():
     ap.add_argument("--ref-attempts", type=int, default=20,
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--grad-steps", type=int, default=2,
+                    help="timed gradients of the 512^2 differentiation workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=2,
                     help="timed launches of the 64-frame batched workload (0: skip)")
     ap.add_argument("--linear-steps", type=int, default=2,
