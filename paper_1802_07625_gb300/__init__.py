@@ -29,6 +29,7 @@ __all__ = [
     "cartogram_iteration_gradient", "cartogram_last_error",
     "cartogram_destroy", "cartogram_batch_create",
     "cartogram_batch_integrate", "cartogram_batch_last_error", "cartogram_batch_destroy", "Cartogram", "Batch",
+    "iteration_loss",
 ]
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
@@ -524,3 +525,31 @@ class Batch:
         except Exception:
             pass
 
+
+
+def iteration_loss(values, blur, cartogram, lam=1e-3, checkpoint=8):
+    """The one-iteration loss of `cartogram` (see cartogram_iteration_gradient) as a
+    differentiable torch function of the target values (1-D float64 tensor) and the blur
+    width (0-D tensor or float). The forward records the step schedule; the backward asks
+    the library for the gradient of that same function (replaying the schedule). The
+    context must not run anything else between the two."""
+    import torch
+
+    class _IterationLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v, b):
+            loss = cartogram.iteration_gradient(v.detach().cpu().double().numpy(), float(b), lam, replay=False,
+                                                checkpoint=checkpoint, grad=False)
+            ctx.args = (v.detach().cpu().double().numpy(), float(b), v.device, v.dtype)
+            return torch.tensor(loss, dtype=torch.float64, device=v.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            vals, b, dev, dt = ctx.args
+            _, gv, gb = cartogram.iteration_gradient(vals, b, lam, replay=True, checkpoint=checkpoint)
+            gvt = torch.as_tensor(gv, device=dev).to(dt) * g
+            gbt = torch.tensor(gb, dtype=torch.float64, device=dev) * g
+            return gvt, gbt
+
+    b = blur if isinstance(blur, torch.Tensor) else torch.tensor(float(blur), dtype=torch.float64)
+    return _IterationLoss.apply(values, b)

@@ -98,3 +98,18 @@ def test_gradient_rejects_what_it_cannot_do():
         with pytest.raises(P.CartogramError) as e:
             c.iteration_gradient(-m.values, 1.0)
         assert e.value.code == P.CG_EINVAL
+
+
+def test_torch_autograd_function_gives_the_librarys_gradient():
+    import torch
+    m = synth.make_workload("voronoi16_64")
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64") as c:
+        c.set_map(m)
+        ref_loss, ref_gv, ref_gb = c.iteration_gradient(m.values, 1.0, LAM)
+        v = torch.tensor(m.values, dtype=torch.float64, requires_grad=True)
+        b = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        loss = P.iteration_loss(v, b, c, lam=LAM)
+        loss.backward()
+    assert abs(float(loss) - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert np.max(np.abs(v.grad.numpy() - ref_gv)) <= 1e-12 * np.max(np.abs(ref_gv))
+    assert abs(float(b.grad) - ref_gb) <= 1e-12 * abs(ref_gb)
