@@ -112,8 +112,10 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   }
   __syncthreads();
   block_fft<T, LOG2N, true>(buf, S, W);
+  // S is a power of two: a runtime integer division here costs as much as the FFT
+  const int ls = __ffs(S) - 1;
   for (int task = threadIdx.x; task < S * N; task += blockDim.x) {
-    const int i = task / S, s = task - i * S;
+    const int i = task >> ls, s = task & (S - 1);
     const C u = buf[s * F::SSTRIDE + F::out_slot(dct3_src(i, N))];
     ABt[(size_t)i * Ly + n0 + s] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
   }
@@ -239,8 +241,9 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
 
   T dev = T(0), v2max = T(0);
   bool bad = false;
+  const int lw = __ffs(Wc) - 1;  // Wc is a power of two (no runtime integer division)
   for (int task = threadIdx.x; task < N * Wc; task += blockDim.x) {
-    const int j = task / Wc, cc = task - j * Wc;
+    const int j = task >> lw, cc = task & (Wc - 1);
     const int slot = F::out_slot(dct3_src(j, N));
     const C u1 = buf[cc * F::SSTRIDE + slot];
     const C u2 = buf[(Wc + (cc >> 1)) * F::SSTRIDE + slot];
@@ -417,8 +420,9 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
   const int c0 = blockIdx.x * Wc;
   const int Wp = Wc / 2;
+  const int lp = __ffs(Wp) - 1;  // Wp is a power of two
   for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
-    const int k = task / Wp, p = task - k * Wp;
+    const int k = task >> lp, p = task & (Wp - 1);
     const double2 e = *reinterpret_cast<const double2*>(R + (size_t)(2 * k) * Lx + c0 + 2 * p);
     const double2 o = *reinterpret_cast<const double2*>(R + (size_t)(2 * k + 1) * Lx + c0 + 2 * p);
     C* x = buf + p * F::SSTRIDE;
@@ -428,7 +432,7 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   __syncthreads();
   block_fft<double, LOG2N, false>(buf, Wp, W);
   for (int task = threadIdx.x; task < N * Wp; task += blockDim.x) {
-    const int n = task / Wp, p = task - n * Wp;
+    const int n = task >> lp, p = task & (Wp - 1);
     const C* x = buf + p * F::SSTRIDE;
     const C Vn = x[F::out_slot(n)];
     const C Vq = x[F::out_slot((N - n) & (N - 1))];
