@@ -194,7 +194,7 @@ def launches_per_cartogram(iterations, attempted):
 
 
 def bytes_per_point(esz):
-    """Algorithmic bytes per grid point per launch of each hot kernel class (see DESIGN.md):
+    """Algorithmic bytes per grid point per launch of each hot kernel class:
     pass 1 reads the spectrum (1 value) and writes (A, B); pass 2 reads (A, B) and writes v;
     the step reads and writes the displacement and gathers v(t) and v(t+h) once each."""
     return {"inverse_rows": 3 * esz, "inverse_cols_velocity": 4 * esz, "heun_step": 8 * esz}

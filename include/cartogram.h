@@ -187,25 +187,27 @@ int cartogram_inverse_project(cg_ctx* ctx, int64_t n, const double* xy_in, doubl
  * stored displacements. Errors: CG_EINVAL, CG_ECUDA. */
 int cartogram_distortion(cg_ctx* ctx, double* out);
 
-/* Loss of one outer iteration and its gradient with respect to the regions' target values
- * and the blur width (reverse mode through the whole iteration: rasterisation, blurred
- * forward transform, every predictor-corrector step with its interpolations and transforms,
- * the vertex map and the areas). From the current vertices X (left unchanged; no history
- * entry is added) with target values V = values[n_regions] and blur width blur_width (the
- * iteration blurs with blur_width * blur_decay^k, k = history length, as
- * cartogram_integrate does): X' = X mapped through the integration's projected grid, A'
- * its region areas, A^_i = V_i sum(A') / sum(V), and
+/* Loss of `iterations` outer iterations and its gradient with respect to the regions'
+ * target values and the blur width (reverse mode through the whole method: region areas
+ * and weights, rasterisation (the exact coverage, also as a function of the vertices
+ * entering each later iteration), blurred forward transform, every predictor-corrector step
+ * with its interpolations and transforms, the vertex maps and the areas). From the current
+ * vertices X (left unchanged; no history entry is added) with target values
+ * V = values[n_regions] and blur width blur_width (iteration k blurs with
+ * blur_width * blur_decay^(h + k), h = history length, as cartogram_integrate does):
+ * X' = X carried through the iterations, A' its region areas, A^_i = V_i sum(A') / sum(V),
  *   loss = sum_i (ln A'_i - ln A^_i)^2 + lambda * sum_v |X'_v - X_v|^2.
- * The integration's accepted steps form a schedule: replay = 0 integrates adaptively (with
- * these values) and records it; replay = 1 reuses the last recorded schedule (same steps
- * and sizes), so that the loss is a smooth function of (values, blur_width), e.g. for finite
- * differences. Positions are stored every `checkpoint` steps (>= 1) and recomputed in
- * between on the way back. loss, grad_values[n_regions] and grad_blur may each be NULL (with
- * both gradients NULL only the forward runs). Needs the FP64 path and the diffusion flow.
- * Errors: CG_EINVAL, CG_ESTATE (no map; replay without a recorded schedule), CG_ESTEPFAIL,
- * CG_EFOLD (a mapped region with non-positive area), CG_ENOMEM, CG_ECUDA. */
-int cartogram_iteration_gradient(cg_ctx* ctx, const double* values, double blur_width, double lambda, int replay,
-                                 int checkpoint, double* loss, double* grad_values, double* grad_blur);
+ * Each integration's accepted steps form a schedule: replay = 0 integrates adaptively (with
+ * these values) and records the schedules; replay = 1 reuses the last recorded ones (same
+ * number of iterations, steps and sizes), so that the loss is a smooth function of
+ * (values, blur_width), e.g. for finite differences. Positions are stored every `checkpoint`
+ * steps (>= 1) and recomputed in between on the way back. loss, grad_values[n_regions] and
+ * grad_blur may each be NULL (with both gradients NULL only the forward runs). Needs the
+ * FP64 path and the diffusion flow. Errors: CG_EINVAL, CG_ESTATE (no map; replay without a
+ * recorded schedule of as many iterations), CG_ESTEPFAIL, CG_EFOLD (a mapped region with
+ * non-positive area), CG_ENOMEM, CG_ECUDA. */
+int cartogram_iteration_gradient(cg_ctx* ctx, const double* values, double blur_width, double lambda, int iterations,
+                                 int replay, int checkpoint, double* loss, double* grad_values, double* grad_blur);
 
 /* Signed relative area errors A_i / A^_i - 1 of the current vertices, [n_regions]. */
 int cartogram_area_errors(cg_ctx* ctx, double* err);

@@ -97,6 +97,7 @@ def lib():
         L.orc_flux_linear.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.orc_integrate_linear.argtypes = [ctypes.POINTER(Params), _D, _D, _D, _LL, _LL, _D]
         L.orc_distortion.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        L.orc_integrate_replay.argtypes = [ctypes.POINTER(Params), _D, _D, ctypes.c_int, _D, _D]
         L.orc_coverage.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _LL, _I, _D, _D]
         L.orc_inverse_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_longlong, _D, _D]
         L.orc_num_threads.restype = ctypes.c_int
@@ -195,6 +196,18 @@ def integrate(spec: np.ndarray, blur: float = 0.0, sched_cap: int = 20000, **kw)
                              ctypes.byref(t), _d(sh), sa.ctypes.data_as(_I), sched_cap)
     n = min(a.value + r.value, sched_cap)
     return IntegrateResult(X, Y, a.value, r.value, t.value, st, sh[:n], sa[:n])
+
+
+def integrate_replay(spec: np.ndarray, steps, **kw):
+    """Integration with the fixed accepted step sizes `steps` (no acceptance test)."""
+    spec = _f64(spec)
+    Ly, Lx = spec.shape
+    P = params(Lx, Ly, 0.0, **kw)
+    X = np.empty((Ly, Lx))
+    Y = np.empty((Ly, Lx))
+    h = _f64(np.asarray(steps, dtype=np.float64))
+    lib().orc_integrate_replay(ctypes.byref(P), _d(spec), _d(h), int(h.size), _d(X), _d(Y))
+    return X, Y
 
 
 def flux_linear(spec: np.ndarray):

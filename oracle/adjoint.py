@@ -174,3 +174,34 @@ def gradient(it: Iteration, values, blur, steps, lam):
     L, _ = it.loss(v, s, steps, lam)
     L.backward()
     return float(L.detach()), v.grad.numpy().copy(), float(s.grad)
+
+
+def adaptive_schedules(orc, m, values, blur, decay, K):
+    """The accepted step sizes of K adaptive outer iterations with the C oracle (the
+    schedule that the FP64 GPU path records too)."""
+    xy = np.array(m.xy, dtype=np.float64)
+    out = []
+    for k in range(K):
+        A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, xy)
+        rho = orc.rasterize(m.Lx, m.Ly, values, A, m.ring_offsets, m.ring_region, xy) / (np.sum(values) / A.sum())
+        r = orc.integrate(orc.forward(rho, blur * decay ** k))
+        out.append(accepted_steps(r.sched_h, r.sched_acc))
+        xy = orc.map_points(r.X, r.Y, xy)
+    return out
+
+
+def cartogram_loss(orc, m, values, blur, decay, schedules, lam):
+    """The loss after len(schedules) outer iterations of the C oracle with those fixed step
+    schedules (rasterisation, blurred transform, replayed integration, point map), in FP64;
+    its central differences give the FP64 reference gradient through several iterations
+    (where the rasteriser's dependence on the moved vertices enters)."""
+    values = np.asarray(values, dtype=np.float64)
+    xy = np.array(m.xy, dtype=np.float64)
+    for k, steps in enumerate(schedules):
+        A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, xy)
+        rho = orc.rasterize(m.Lx, m.Ly, values, A, m.ring_offsets, m.ring_region, xy) / (values.sum() / A.sum())
+        X, Y = orc.integrate_replay(orc.forward(rho, blur * decay ** k), steps)
+        xy = orc.map_points(X, Y, xy)
+    A1 = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, xy)
+    r = np.log(A1) - np.log(values * A1.sum() / values.sum())
+    return float(np.sum(r * r) + lam * np.sum((xy - m.xy) ** 2))

@@ -26,7 +26,7 @@
  *  orc_velocity, orc_interp       closed-form single-mode velocity, no-flux walls,
  *                                 exact reproduction of linear fields (pinned)
  *  orc_heun_step                  closed form of Heun's method for linear fields (pinned)
- *  orc_integrate                  uniform density -> identity; x-only density ->
+ *  orc_integrate, orc_integrate_replay   uniform density -> identity; x-only density ->
  *                                 closed-form 1-D equalising map (pinned to the
  *                                 discretisation error only)
  *  orc_rasterize, orc_coverage    hand-computed coverages, total mass; the density as
@@ -381,6 +381,44 @@ int orc_integrate(const orc_params* P, const double* spec, double* X, double* Y,
     return status;
 }
 
+
+/* The integration with a fixed step schedule: the accepted step sizes h[0..n) of an
+ * adaptive run, taken in order with no acceptance test (the function whose derivative
+ * the gradient entry point computes). */
+void orc_integrate_replay(const orc_params* P, const double* spec, const double* h, int n, double* X,
+                          double* Y) {
+    const int Lx = P->Lx, Ly = P->Ly;
+    const size_t N = (size_t)Lx * Ly;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* gx = (double*)malloc(sizeof(double) * N);
+    double* gy = (double*)malloc(sizeof(double) * N);
+    double* v0x = (double*)malloc(sizeof(double) * N);
+    double* v0y = (double*)malloc(sizeof(double) * N);
+    double* v1x = (double*)malloc(sizeof(double) * N);
+    double* v1y = (double*)malloc(sizeof(double) * N);
+    double* cx = (double*)malloc(sizeof(double) * N);
+    double* cy = (double*)malloc(sizeof(double) * N);
+    const double rho_bar = spec[0] / ((double)Lx * Ly);
+    for (int j = 0; j < Ly; ++j)
+        for (int i = 0; i < Lx; ++i) {
+            X[(size_t)j * Lx + i] = i + 0.5;
+            Y[(size_t)j * Lx + i] = j + 0.5;
+        }
+    double dev;
+    double t = 0.0;
+    field_at(Lx, Ly, spec, 0.0, rho_bar, rho, gx, gy, v0x, v0y, &dev);
+    for (int k = 0; k < n; ++k) {
+        field_at(Lx, Ly, spec, t + h[k], rho_bar, rho, gx, gy, v1x, v1y, &dev);
+        orc_heun_step(Lx, Ly, v0x, v0y, v1x, v1y, (long long)N, X, Y, h[k], NULL, NULL, cx, cy);
+        memcpy(X, cx, sizeof(double) * N);
+        memcpy(Y, cy, sizeof(double) * N);
+        double* s;
+        s = v0x; v0x = v1x; v1x = s;
+        s = v0y; v0y = v1y; v1y = s;
+        t = t + h[k];
+    }
+    free(rho); free(gx); free(gy); free(v0x); free(v0y); free(v1x); free(v1y); free(cx); free(cy);
+}
 
 /* Flux of the linear-equalisation flow (SI Eq. fmn_fast, f_mn = 1 - t for t <= 1): with
  * f'_mn = -1, SI Eqs. Jxmn and Jymn give the t-independent coefficients

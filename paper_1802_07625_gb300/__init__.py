@@ -108,7 +108,7 @@ def load(build_if_missing: bool = True):
         "cartogram_velocity_noalloc": (i, [i, i, _P, d, _P, _P]),
         "cartogram_inverse_project": (i, [_P, ll, _P, _P]),
         "cartogram_distortion": (i, [_P, _P]),
-        "cartogram_iteration_gradient": (i, [_P, _P, d, d, i, i, _P, _P, _P]),
+        "cartogram_iteration_gradient": (i, [_P, _P, d, d, i, i, i, _P, _P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
         "cartogram_batch_create": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P)]),
@@ -326,13 +326,14 @@ def cartogram_distortion(ctx) -> dict:
     return {"e_a": out[0], "e_inf": out[1], "et_a": out[2], "et_inf": out[3]}
 
 
-def cartogram_iteration_gradient(ctx, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True):
-    """Loss of one outer iteration and (grad=True) its gradient w.r.t. values and blur."""
+def cartogram_iteration_gradient(ctx, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True, iterations=1):
+    """Loss of `iterations` outer iterations and (grad=True) its gradient w.r.t. values and blur."""
     v = np.ascontiguousarray(values, dtype=np.float64)
     loss = ctypes.c_double()
     gv = np.zeros_like(v) if grad else None
     gb = ctypes.c_double()
-    _check(ctx, load().cartogram_iteration_gradient(ctx, v.ctypes.data, float(blur), float(lam), int(bool(replay)),
+    _check(ctx, load().cartogram_iteration_gradient(ctx, v.ctypes.data, float(blur), float(lam), int(iterations),
+                                                   int(bool(replay)),
                                                    int(checkpoint), ctypes.byref(loss),
                                                    gv.ctypes.data if grad else None,
                                                    ctypes.byref(gb) if grad else None))
@@ -448,8 +449,8 @@ class Cartogram:
     def distortion(self):
         return cartogram_distortion(self.ctx)
 
-    def iteration_gradient(self, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True):
-        return cartogram_iteration_gradient(self.ctx, values, blur, lam, replay, checkpoint, grad)
+    def iteration_gradient(self, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True, iterations=1):
+        return cartogram_iteration_gradient(self.ctx, values, blur, lam, replay, checkpoint, grad, iterations)
 
     def area_errors(self):
         return cartogram_area_errors(self.ctx, np.empty(self._map.n_regions))
@@ -527,7 +528,7 @@ class Batch:
 
 
 
-def iteration_loss(values, blur, cartogram, lam=1e-3, checkpoint=8):
+def iteration_loss(values, blur, cartogram, lam=1e-3, checkpoint=8, iterations=1):
     """The one-iteration loss of `cartogram` (see cartogram_iteration_gradient) as a
     differentiable torch function of the target values (1-D float64 tensor) and the blur
     width (0-D tensor or float). The forward records the step schedule; the backward asks
@@ -539,14 +540,15 @@ def iteration_loss(values, blur, cartogram, lam=1e-3, checkpoint=8):
         @staticmethod
         def forward(ctx, v, b):
             loss = cartogram.iteration_gradient(v.detach().cpu().double().numpy(), float(b), lam, replay=False,
-                                                checkpoint=checkpoint, grad=False)
+                                                checkpoint=checkpoint, grad=False, iterations=iterations)
             ctx.args = (v.detach().cpu().double().numpy(), float(b), v.device, v.dtype)
             return torch.tensor(loss, dtype=torch.float64, device=v.device)
 
         @staticmethod
         def backward(ctx, g):
             vals, b, dev, dt = ctx.args
-            _, gv, gb = cartogram.iteration_gradient(vals, b, lam, replay=True, checkpoint=checkpoint)
+            _, gv, gb = cartogram.iteration_gradient(vals, b, lam, replay=True, checkpoint=checkpoint,
+                                                     iterations=iterations)
             gvt = torch.as_tensor(gv, device=dev).to(dt) * g
             gbt = torch.tensor(gb, dtype=torch.float64, device=dev) * g
             return gvt, gbt

@@ -233,7 +233,7 @@ __global__ void raster_adjoint_kernel(const double2* __restrict__ xy, const int*
     const double2 P = xy[v], Q = xy[next[v]];
     if (Q.y - P.y == 0.0) continue;
     double g = 0.0;
-    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by) {
+    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double, double) {
       const double pdy = by - ay;
       if (pdy == 0.0) return;
       const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
@@ -288,6 +288,76 @@ __global__ void map_adjoint_kernel(const double2* __restrict__ xy0, const double
       atomicAdd(lamD + 2 * kk[t], c[t] * gg.x);
       atomicAdd(lamD + 2 * kk[t] + 1, c[t] * gg.y);
     }
+  }
+}
+
+// ---- vertex adjoints (gradients through several outer iterations) -----------------
+
+// Adjoint of the exact coverage with respect to the ring vertices: moving an edge sweeps
+// area across its outward normal (d.y, -d.x)/|d| of a counter-clockwise ring, so
+// d/dP sum_c lam_c w_r cov_r(c) = w_r sum over the edge's pieces of lam_c (d.y, -d.x)
+// times the integral of the hat function of P (1 - s) over the piece, and likewise for
+// Q with s. lam is the density adjoint per cell (before the suffix sums).
+__global__ void coverage_vertex_adjoint_kernel(const double2* __restrict__ xy, const int* __restrict__ next,
+                                               const int* __restrict__ vreg, const double* __restrict__ w,
+                                               const double* __restrict__ lam, double* g, int Lx, int Ly, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double2 P = xy[v], Q = xy[next[v]];
+    const double dx = Q.x - P.x, dy = Q.y - P.y;
+    if (dx == 0.0 && dy == 0.0) continue;
+    const double wr = w[vreg[v]];
+    double aP = 0.0, aQ = 0.0;  // sum of lam_c times the hat integrals
+    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double s0, double s1) {
+      const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
+      const int jj = (int)floor(my), ii = (int)floor(mx);
+      if (jj < 0 || jj >= Ly || ii < 0 || ii >= Lx) return;
+      const double lc = lam[(size_t)jj * Lx + ii];
+      const double q = 0.5 * (s1 * s1 - s0 * s0);
+      aP += lc * ((s1 - s0) - q);
+      aQ += lc * q;
+    });
+    const double nx = wr * dy, ny = -wr * dx;
+    atomicAdd(g + 2 * v, aP * nx);
+    atomicAdd(g + 2 * v + 1, aP * ny);
+    atomicAdd(g + 2 * next[v], aQ * nx);
+    atomicAdd(g + 2 * next[v] + 1, aQ * ny);
+  }
+}
+
+// Vertex adjoint through the map X' = X + (bilinear interpolation of the grid
+// displacements D at X): lam_out = lam + (d D(X)/d X)^T lam.
+__global__ void map_jacobian_adjoint_kernel(const double2* __restrict__ xy, const double2* __restrict__ D,
+                                            const double2* __restrict__ lam, double2* lam_out, int Lx, int Ly,
+                                            int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double2 q = xy[v];
+    const double u = q.x - 0.5, wv = q.y - 0.5;
+    int i0 = (int)floor(u), j0 = (int)floor(wv);
+    i0 = i0 < 0 ? 0 : (i0 > Lx - 2 ? Lx - 2 : i0);
+    j0 = j0 < 0 ? 0 : (j0 > Ly - 2 ? Ly - 2 : j0);
+    const double fx = u - i0, fy = wv - j0;
+    const size_t k = (size_t)j0 * Lx + i0;
+    const double2 a = D[k], b = D[k + 1], c = D[k + Lx], d = D[k + Lx + 1];
+    const double dxx = (1 - fy) * (b.x - a.x) + fy * (d.x - c.x);  // d Dx / dx
+    const double dyx = (1 - fy) * (b.y - a.y) + fy * (d.y - c.y);  // d Dy / dx
+    const double dxy = (1 - fx) * (c.x - a.x) + fx * (d.x - b.x);  // d Dx / dy
+    const double dyy = (1 - fx) * (c.y - a.y) + fx * (d.y - b.y);  // d Dy / dy
+    const double2 l = lam[v];
+    lam_out[v] = make_double2(l.x + l.x * dxx + l.y * dyx, l.y + l.x * dxy + l.y * dyy);
+  }
+}
+
+// g[v] += dL/dA_(region of v) times the shoelace derivative of the region's area.
+__global__ void shoelace_adjoint_kernel(const double2* __restrict__ xy, const int* __restrict__ next,
+                                        const int* __restrict__ prev, const int* __restrict__ vreg,
+                                        const double* __restrict__ dLdA, double2* g, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double2 a = xy[next[v]], b = xy[prev[v]];
+    const double gA = dLdA[vreg[v]];
+    double2 t = g[v];
+    t.x += gA * 0.5 * (a.y - b.y);
+    t.y += gA * 0.5 * (b.x - a.x);
+    g[v] = t;
   }
 }
 

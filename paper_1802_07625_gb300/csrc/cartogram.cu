@@ -29,6 +29,7 @@ struct AdjWork {
   double *Crho = nullptr, *Cx = nullptr, *Cy = nullptr;       // their DCT-II [N]
   double *lam_spec = nullptr, *specp = nullptr, *R = nullptr, *dens = nullptr;  // [N]
   double2* AB = nullptr;         // inverse-pass intermediate [N]
+  double2* Dk = nullptr;         // final displacements of the iteration being reversed [N]
   double2* flux = nullptr;       // inverse-pass side output [N]
   std::vector<double2*> v;       // fields of a segment's levels [C + 1][N]
   std::vector<double*> rho;      // densities of a segment's levels [C + 1][N]
@@ -41,6 +42,9 @@ struct AdjWork {
   double* dsig = nullptr;        // [1]
   double2* xy1 = nullptr;        // mapped vertices [n_vert]
   double2* gv = nullptr;         // their adjoints [n_vert]
+  double2* gv2 = nullptr;        // [n_vert]
+  std::vector<double2*> X;       // vertices entering each iteration, [K + 1][n_vert]
+  std::vector<double*> spec;     // each iteration's spectrum, [K][N]
   long long n_vert = 0;
   int n_regions = 0;
 };
@@ -103,8 +107,7 @@ struct cg_ctx {
   double* diag = nullptr;  // distortion scratch: per-block sums, maxima, results
   int* prev = nullptr;     // ring predecessor of every vertex
   double* sched_rec = nullptr;      // while recording: (t, h) of the accepted steps (device)
-  std::vector<double> sched;        // the last recorded schedule, [n][2]
-  bool sched_len_zero = false;      // the last recorded integration took no step
+  std::vector<std::vector<double>> scheds;  // the last recorded schedules, per iteration [n][2]
   AdjWork* adj = nullptr;           // workspace of the iteration gradient
 
   // persistent integration kernel
@@ -1086,9 +1089,11 @@ int do_inverse_project(cg_ctx* c, int64_t n, const double* in, double* out) {
 void free_adj(cg_ctx* c) {
   AdjWork* a = c->adj;
   if (!a) return;
-  std::vector<void*> ps = {a->lam, a->L[0], a->L[1], a->a_rho, a->a_gx, a->a_gy, a->Crho, a->Cx, a->Cy,
+  std::vector<void*> ps = {a->Dk, a->lam, a->L[0], a->L[1], a->a_rho, a->a_gx, a->a_gy, a->Crho, a->Cx, a->Cy,
                            a->lam_spec, a->specp, a->R, a->dens, a->AB, a->flux, a->sched, a->vals, a->dLdA,
-                           a->gw, a->dsig, a->xy1, a->gv};
+                           a->gw, a->dsig, a->xy1, a->gv, a->gv2};
+  for (auto p : a->X) ps.push_back(p);
+  for (auto p : a->spec) ps.push_back(p);
   for (auto p : a->v) ps.push_back(p);
   for (auto p : a->rho) ps.push_back(p);
   for (auto p : a->D) ps.push_back(p);
@@ -1111,6 +1116,7 @@ int adj_alloc(cg_ctx* c, int C) {
   double** ds[] = {&a->a_rho, &a->a_gx, &a->a_gy, &a->Crho, &a->Cx, &a->Cy, &a->lam_spec, &a->specp, &a->R, &a->dens};
   for (double** p : ds) CG_CUDA(c, cudaMalloc((void**)p, sizeof(double) * N));
   CG_CUDA(c, cudaMalloc((void**)&a->AB, sizeof(double2) * N));
+  CG_CUDA(c, cudaMalloc((void**)&a->Dk, sizeof(double2) * N));
   CG_CUDA(c, cudaMalloc((void**)&a->flux, sizeof(double2) * N));
   a->v.assign(C + 1, nullptr);
   a->rho.assign(C + 1, nullptr);
@@ -1129,6 +1135,24 @@ int adj_alloc(cg_ctx* c, int C) {
   CG_CUDA(c, cudaMalloc((void**)&a->dsig, sizeof(double)));
   CG_CUDA(c, cudaMalloc((void**)&a->xy1, sizeof(double2) * std::max<long long>(1, c->n_vert)));
   CG_CUDA(c, cudaMalloc((void**)&a->gv, sizeof(double2) * std::max<long long>(1, c->n_vert)));
+  CG_CUDA(c, cudaMalloc((void**)&a->gv2, sizeof(double2) * std::max<long long>(1, c->n_vert)));
+  return CG_OK;
+}
+
+// Per-iteration storage of a K-iteration gradient.
+int adj_alloc_iters(cg_ctx* c, int K) {
+  AdjWork* a = c->adj;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  while ((int)a->X.size() < K + 1) {
+    double2* p = nullptr;
+    CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double2) * std::max<long long>(1, c->n_vert)));
+    a->X.push_back(p);
+  }
+  while ((int)a->spec.size() < K) {
+    double* p = nullptr;
+    CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double) * N));
+    a->spec.push_back(p);
+  }
   return CG_OK;
 }
 
@@ -1169,95 +1193,135 @@ void adj_level(cg_ctx* c, double* L, const double2* v, const double* rho, double
   cudaMemsetAsync(L, 0, sizeof(double) * 2 * (size_t)c->Lx * c->Ly, s);
 }
 
-int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, double lam, int replay, int C,
+// Forward replay of one integration from the spectrum in spec64 with schedule sch:
+// positions every C steps into the checkpoints (if ck), the final displacements returned.
+double2* adj_replay(cg_ctx* c, const std::vector<double>& sch, int C, bool ck) {
+  AdjWork* a = c->adj;
+  cudaStream_t s = c->stream;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  const int NS = (int)sch.size() / 2;
+  if (ck) cudaMemsetAsync(a->ckpt[0], 0, sizeof(double2) * N, s);
+  cudaMemsetAsync(a->D[0], 0, sizeof(double2) * N, s);
+  int cur = 0;  // v[cur] holds the field of level n
+  adj_field(c, 0.0, a->v[0], a->rho[0]);
+  double2* din = a->D[0];
+  double2* dout = a->D[1];
+  for (int n = 0; n < NS; ++n) {
+    adj_field(c, adj_tau(sch, n + 1), a->v[1 - cur], a->rho[1 - cur]);
+    adj_step(c, a->v[cur], a->v[1 - cur], din, dout, sch[2 * n + 1]);
+    std::swap(din, dout);
+    cur = 1 - cur;
+    if (ck && (n + 1) % C == 0 && (n + 1) / C < (int)a->ckpt.size())
+      cudaMemcpyAsync(a->ckpt[(n + 1) / C], din, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
+  }
+  return din;
+}
+
+// Reverse of one integration: a->lam holds the final displacements' adjoint on entry;
+// the spectrum adjoint accumulates into lam_spec (zeroed here).
+void adj_reverse(cg_ctx* c, const std::vector<double>& sch, int C) {
+  AdjWork* a = c->adj;
+  cudaStream_t s = c->stream;
+  const size_t N = (size_t)c->Lx * c->Ly;
+  const int NS = (int)sch.size() / 2;
+  cudaMemsetAsync(a->lam_spec, 0, sizeof(double) * N, s);
+  cudaMemsetAsync(a->L[0], 0, sizeof(double) * 2 * N, s);
+  cudaMemsetAsync(a->L[1], 0, sizeof(double) * 2 * N, s);
+  // backwards over the segments; L[hi] holds level n + 1, L[lo] level n
+  int hi = 0, lo = 1;
+  const int nseg = (NS + C - 1) / C;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int n0 = sg * C, n1 = std::min(n0 + C, NS);
+    cudaMemcpyAsync(a->D[0], a->ckpt[sg], sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k <= n1 - n0; ++k) adj_field(c, adj_tau(sch, n0 + k), a->v[k], a->rho[k]);
+    for (int k = 0; k < n1 - n0 - 1; ++k) adj_step(c, a->v[k], a->v[k + 1], a->D[k], a->D[k + 1], sch[2 * (n0 + k) + 1]);
+    for (int n = n1 - 1; n >= n0; --n) {
+      const int k = n - n0;
+      cg::launch_heun_adjoint(a->D[k], a->v[k], a->v[k + 1], sch[2 * n + 1], a->lam, a->L[lo], a->L[hi], c->Lx,
+                              c->Ly, s);
+      adj_level(c, a->L[hi], a->v[k + 1], a->rho[k + 1], adj_tau(sch, n + 1));
+      std::swap(hi, lo);
+    }
+  }
+  // level 0 (its field is the first segment's level 0, still in place)
+  if (NS > 0) adj_level(c, a->L[hi], a->v[0], a->rho[0], 0.0);
+}
+
+int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, double lam, int K, int replay, int C,
                           double* loss_out, double* grad_values, double* grad_blur) {
   cudaStream_t s = c->stream;
   const int R = c->R_n;
   const size_t N = (size_t)c->Lx * c->Ly;
+  const int nv = (int)c->n_vert;
   std::vector<double> V(R);
   CG_CUDA(c, cudaMemcpy(V.data(), values_in, sizeof(double) * R, cudaMemcpyDefault));
   for (int i = 0; i < R; ++i)
     if (!is_finite(V[i]) || !(V[i] > 0.0)) return fail(c, CG_EINVAL, "value %d is not positive and finite", i);
-  if (replay && c->sched.empty() && !(c->sched_len_zero))
-    return fail(c, CG_ESTATE, "no recorded schedule: call with replay = 0 first");
+  if (replay && (int)c->scheds.size() != K)
+    return fail(c, CG_ESTATE, "no recorded schedule of %d iterations: call with replay = 0 first", K);
   int r = adj_alloc(c, C);
-  if (r) return r;
+  if (r || (r = adj_alloc_iters(c, K))) return r;
   AdjWork* a = c->adj;
   CG_CUDA(c, cudaMemcpyAsync(a->vals, V.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
-  // areas of the current map and the rasterisation weights of these values
-  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
-                   c->err_d, c->w, c->info, s);
-  std::vector<double> A(R);
-  CG_CUDA(c, cudaMemcpyAsync(A.data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-  // density and spectrum with the blur of this iteration
-  const double decay_k = std::pow(c->opt.blur_decay, (double)c->hist_len);
-  const double sigma = blur * decay_k;
-  CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * N, s));
-  cg::launch_raster(c->xy, c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, (int)c->n_vert, s);
-  cg::launch_blur_tables(nullptr, sigma, c->bx, c->by, c->Lx, c->Ly, s);
-  c->blur_tab_sigma = -1.0;
-  cg::launch_fwd<double>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
-                         c->bx, c->by, s);
-  c->have_spectrum = true;
-  CG_CUDA(c, cudaGetLastError());
-  // the step schedule: recorded by an adaptive integration, or the last one reused
-  if (!replay) {
-    c->sched_rec = a->sched;
-    r = run_integration_host<double>(c);
-    c->sched_rec = nullptr;
-    if (r || (r = read_info(c))) return r;
-    const IterInfo inf = *c->info_h;
-    if (inf.status != cg::kDone)
-      return fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
-                  "integration ended with status %d after %lld/%lld steps", inf.status, inf.accepted, inf.rejected);
-    c->sched.assign(2 * (size_t)inf.accepted, 0.0);
-    if (inf.accepted > 0)
-      CG_CUDA(c, cudaMemcpy(c->sched.data(), a->sched, sizeof(double) * 2 * inf.accepted, cudaMemcpyDeviceToHost));
-    c->sched_len_zero = inf.accepted == 0;
-  }
-  const std::vector<double>& sch = c->sched;
-  const int NS = (int)sch.size() / 2;
-  // forward replay with checkpoints every C steps
-  const int nck = NS / C + 1;
-  while ((int)a->ckpt.size() < nck) {
-    double2* p = nullptr;
-    CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double2) * N));
-    a->ckpt.push_back(p);
-  }
-  CG_CUDA(c, cudaMemsetAsync(a->ckpt[0], 0, sizeof(double2) * N, s));
-  CG_CUDA(c, cudaMemsetAsync(a->D[0], 0, sizeof(double2) * N, s));
-  {
-    int cur = 0;  // v[cur] holds the field of level n
-    adj_field(c, 0.0, a->v[0], a->rho[0]);
-    double2* din = a->D[0];
-    double2* dout = a->D[1];
-    for (int n = 0; n < NS; ++n) {
-      adj_field(c, adj_tau(sch, n + 1), a->v[1 - cur], a->rho[1 - cur]);
-      adj_step(c, a->v[cur], a->v[1 - cur], din, dout, sch[2 * n + 1]);
-      std::swap(din, dout);
-      cur = 1 - cur;
-      if ((n + 1) % C == 0 && (n + 1) / C < nck)
-        CG_CUDA(c, cudaMemcpyAsync(a->ckpt[(n + 1) / C], din, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  CG_CUDA(c, cudaMemcpyAsync(a->X[0], c->xy, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, s));
+  double sV = 0.0;
+  for (int i = 0; i < R; ++i) sV += V[i];
+  std::vector<std::vector<double>> A(K, std::vector<double>(R));
+  std::vector<double> sigma(K), decay(K);
+  if (!replay) c->scheds.assign(K, std::vector<double>());
+  // forward: K outer iterations from the current vertices
+  for (int k = 0; k < K; ++k) {
+    decay[k] = std::pow(c->opt.blur_decay, (double)(c->hist_len + k));
+    sigma[k] = blur * decay[k];
+    cg::launch_areas(a->X[k], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R,
+                     c->area, c->err_d, c->w, c->info, s);
+    CG_CUDA(c, cudaMemcpyAsync(A[k].data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * N, s));
+    cg::launch_raster(a->X[k], c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, nv, s);
+    cg::launch_blur_tables(nullptr, sigma[k], c->bx, c->by, c->Lx, c->Ly, s);
+    cg::launch_fwd<double>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                           c->bx, c->by, s);
+    CG_CUDA(c, cudaMemcpyAsync(a->spec[k], c->spec64, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CG_CUDA(c, cudaGetLastError());
+    if (!replay) {
+      // the step schedule of an adaptive integration
+      c->sched_rec = a->sched;
+      r = run_integration_host<double>(c);
+      c->sched_rec = nullptr;
+      if (r || (r = read_info(c))) return r;
+      const IterInfo inf = *c->info_h;
+      if (inf.status != cg::kDone)
+        return fail(c, inf.status == cg::kTimeout ? CG_ETIMEOUT : CG_ESTEPFAIL,
+                    "integration %d ended with status %d after %lld/%lld steps", k + 1, inf.status, inf.accepted,
+                    inf.rejected);
+      c->scheds[k].assign(2 * (size_t)inf.accepted, 0.0);
+      if (inf.accepted > 0)
+        CG_CUDA(c, cudaMemcpy(c->scheds[k].data(), a->sched, sizeof(double) * 2 * inf.accepted,
+                              cudaMemcpyDeviceToHost));
     }
-    // the vertices through the final grid, and their areas
-    cg::launch_map_points<double>(c->xy, a->xy1, c->n_vert, din, c->Lx, c->Ly, s);
+    const int nck = (int)c->scheds[k].size() / 2 / C + 1;
+    while ((int)a->ckpt.size() < nck) {
+      double2* p = nullptr;
+      CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double2) * N));
+      a->ckpt.push_back(p);
+    }
+    double2* Dk = adj_replay(c, c->scheds[k], C, false);
+    cg::launch_map_points<double>(a->X[k], a->X[k + 1], nv, Dk, c->Lx, c->Ly, s);
+    CG_CUDA(c, cudaGetLastError());
   }
-  CG_CUDA(c, cudaGetLastError());
-  cg::launch_areas(a->xy1, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
+  c->have_spectrum = true;
+  c->blur_tab_sigma = -1.0;
+  // the loss on the final vertices
+  cg::launch_areas(a->X[K], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
                    c->err_d, c->w, c->info, s);
   std::vector<double> A1(R);
-  std::vector<double2> X0(c->n_vert), X1(c->n_vert);
+  std::vector<double2> X0(nv), X1(nv);
   CG_CUDA(c, cudaMemcpyAsync(A1.data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-  CG_CUDA(c, cudaMemcpyAsync(X1.data(), a->xy1, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToHost, s));
-  CG_CUDA(c, cudaMemcpyAsync(X0.data(), c->xy, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToHost, s));
+  CG_CUDA(c, cudaMemcpyAsync(X1.data(), a->X[K], sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+  CG_CUDA(c, cudaMemcpyAsync(X0.data(), a->X[0], sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
   CG_CUDA(c, cudaStreamSynchronize(s));
-  // loss: sum_i (ln A'_i - ln A^_i)^2 + lam sum_v |X'_v - X_v|^2, A^_i = V_i sum A' / sum V
-  double sV = 0.0, sA1 = 0.0, sA = 0.0;
-  for (int i = 0; i < R; ++i) {
-    sV += V[i];
-    sA1 += A1[i];
-    sA += A[i];
-  }
+  double sA1 = 0.0;
+  for (int i = 0; i < R; ++i) sA1 += A1[i];
   std::vector<double> res(R);
   double L = 0.0, sres = 0.0;
   for (int i = 0; i < R; ++i) {
@@ -1267,63 +1331,71 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
     sres += res[i];
   }
   double pen = 0.0;
-  for (long long v = 0; v < c->n_vert; ++v) {
+  for (int v = 0; v < nv; ++v) {
     const double dx = X1[v].x - X0[v].x, dy = X1[v].y - X0[v].y;
     pen += dx * dx + dy * dy;
   }
   L += lam * pen;
   if (loss_out) *loss_out = L;
   if (grad_values || grad_blur) {
-    // d L / d A'_j and the direct d L / d V_j through A^
     std::vector<double> dLdA(R), gV(R);
     for (int j = 0; j < R; ++j) {
       dLdA[j] = 2.0 * res[j] / A1[j] - 2.0 * sres / sA1;
       gV[j] = -2.0 * res[j] / V[j] + 2.0 * sres / sV;
     }
     CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dLdA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
-    cg::launch_vertex_adjoint(a->xy1, c->xy, c->next, c->prev, c->vreg, a->dLdA, lam, a->gv, (double*)a->lam, c->Lx,
-                              c->Ly, (int)c->n_vert, s);
-    CG_CUDA(c, cudaMemsetAsync(a->lam_spec, 0, sizeof(double) * N, s));
-    CG_CUDA(c, cudaMemsetAsync(a->L[0], 0, sizeof(double) * 2 * N, s));
-    CG_CUDA(c, cudaMemsetAsync(a->L[1], 0, sizeof(double) * 2 * N, s));
-    // backwards over the segments; L[hi] holds level n + 1, L[lo] level n
-    int hi = 0, lo = 1;
-    const int nseg = (NS + C - 1) / C;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int n0 = sg * C, n1 = std::min(n0 + C, NS);
-      CG_CUDA(c, cudaMemcpyAsync(a->D[0], a->ckpt[sg], sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
-      for (int k = 0; k <= n1 - n0; ++k) adj_field(c, adj_tau(sch, n0 + k), a->v[k], a->rho[k]);
-      for (int k = 0; k < n1 - n0 - 1; ++k) adj_step(c, a->v[k], a->v[k + 1], a->D[k], a->D[k + 1], sch[2 * (n0 + k) + 1]);
-      for (int n = n1 - 1; n >= n0; --n) {
-        const int k = n - n0;
-        cg::launch_heun_adjoint(a->D[k], a->v[k], a->v[k + 1], sch[2 * n + 1], a->lam, a->L[lo], a->L[hi], c->Lx,
-                                c->Ly, s);
-        adj_level(c, a->L[hi], a->v[k + 1], a->rho[k + 1], adj_tau(sch, n + 1));
-        std::swap(hi, lo);
+    // adjoint of the final vertices
+    double2* lamX = a->gv;
+    double2* lamX2 = a->gv2;
+    cg::launch_loss_vertex_adjoint(a->X[K], a->X[0], c->next, c->prev, c->vreg, a->dLdA, lam, lamX, nv, s);
+    double dsig_total = 0.0;
+    for (int k = K - 1; k >= 0; --k) {
+      // the iteration's spectrum, blur factors and integration
+      CG_CUDA(c, cudaMemcpyAsync(c->spec64, a->spec[k], sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      cg::launch_blur_tables(nullptr, sigma[k], c->bx, c->by, c->Lx, c->Ly, s);
+      // (the replay's buffers are reused by the reverse pass: keep D_k aside)
+      CG_CUDA(c, cudaMemcpyAsync(a->Dk, adj_replay(c, c->scheds[k], C, true), sizeof(double2) * N,
+                                 cudaMemcpyDeviceToDevice, s));
+      // the map X_{k+1} = X_k + D_k(X_k): the displacements' adjoint
+      cg::launch_map_adjoint(a->X[k], lamX, (double*)a->lam, c->Lx, c->Ly, nv, s);
+      adj_reverse(c, c->scheds[k], C);
+      cg::launch_spec_tail(a->lam_spec, c->spec64, c->bx, c->by, sigma[k], a->specp, a->dsig, c->Lx, c->Ly, s);
+      cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, a->specp, a->AB, (const double2*)c->Wx,
+                                  (const double2*)c->Ex, c->st, cg::kModeFlux, 0.0, 0, 0, 0u, s);
+      cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, a->flux, nullptr, a->dens,
+                                  (const double2*)c->Wy, (const double2*)c->Ey, c->st, cg::kModeFlux, s);
+      // the iteration's region weights again (for the coverage adjoint of its vertices)
+      cg::launch_areas(a->X[k], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R,
+                       c->area, c->err_d, c->w, c->info, s);
+      if (k > 0)
+        cg::launch_vertex_map_coverage(a->X[k], c->next, c->vreg, c->w, a->dens, a->Dk, lamX, lamX2, c->Lx, c->Ly,
+                                       nv, s);
+      cg::launch_raster_adjoint(a->X[k], c->next, c->vreg, a->dens, a->gw, R, c->Lx, c->Ly, nv, s);
+      CG_CUDA(c, cudaGetLastError());
+      std::vector<double> gw(R);
+      double dsig = 0.0;
+      CG_CUDA(c, cudaMemcpyAsync(gw.data(), a->gw, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+      CG_CUDA(c, cudaMemcpyAsync(&dsig, a->dsig, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CG_CUDA(c, cudaStreamSynchronize(s));
+      dsig_total += dsig * decay[k];
+      // w_i = (V_i / A_i)(sum A / sum V) - 1
+      const std::vector<double>& Ak = A[k];
+      double sA = 0.0, sgw = 0.0;
+      for (int i = 0; i < R; ++i) sA += Ak[i];
+      for (int i = 0; i < R; ++i) sgw += gw[i] * V[i] / Ak[i];
+      for (int j = 0; j < R; ++j) gV[j] += gw[j] * sA / (Ak[j] * sV) - sA / (sV * sV) * sgw;
+      if (k > 0) {
+        // the areas of X_k through the weights
+        std::vector<double> dA(R);
+        for (int j = 0; j < R; ++j) dA[j] = -gw[j] * V[j] * sA / (Ak[j] * Ak[j] * sV) + sgw / sV;
+        CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
+        cg::launch_shoelace_adjoint(a->X[k], c->next, c->prev, c->vreg, a->dLdA, lamX2, nv, s);
+        std::swap(lamX, lamX2);
       }
     }
-    // level 0 (its field is the first segment's level 0, still in place)
-    if (NS > 0) adj_level(c, a->L[hi], a->v[0], a->rho[0], 0.0);
     CG_CUDA(c, cudaGetLastError());
-    // blur derivative, then the density adjoint by an inverse-type cosine sum
-    cg::launch_spec_tail(a->lam_spec, c->spec64, c->bx, c->by, sigma, a->specp, a->dsig, c->Lx, c->Ly, s);
-    cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, a->specp, a->AB, (const double2*)c->Wx,
-                                (const double2*)c->Ex, c->st, cg::kModeFlux, 0.0, 0, 0, 0u, s);
-    cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, a->flux, nullptr, a->dens,
-                                (const double2*)c->Wy, (const double2*)c->Ey, c->st, cg::kModeFlux, s);
-    cg::launch_raster_adjoint(c->xy, c->next, c->vreg, a->dens, a->gw, R, c->Lx, c->Ly, (int)c->n_vert, s);
-    CG_CUDA(c, cudaGetLastError());
-    std::vector<double> gw(R);
-    double dsig = 0.0;
-    CG_CUDA(c, cudaMemcpyAsync(gw.data(), a->gw, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-    CG_CUDA(c, cudaMemcpyAsync(&dsig, a->dsig, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CG_CUDA(c, cudaStreamSynchronize(s));
-    // w_i = (V_i / A_i)(sum A / sum V) - 1
-    double sgw = 0.0;
-    for (int i = 0; i < R; ++i) sgw += gw[i] * V[i] / A[i];
-    for (int j = 0; j < R; ++j) gV[j] += gw[j] * sA / (A[j] * sV) - sA / (sV * sV) * sgw;
     if (grad_values) CG_CUDA(c, cudaMemcpy(grad_values, gV.data(), sizeof(double) * R, cudaMemcpyDefault));
-    if (grad_blur) *grad_blur = dsig * decay_k;
+    if (grad_blur) *grad_blur = dsig_total;
   }
   // leave the context's areas and weights those of its current map and values
   return run_areas(c);
@@ -1398,7 +1470,7 @@ void free_regions(cg_ctx* c) {
   free_adj(c);
   if (c->prev) cudaFree(c->prev);
   c->prev = nullptr;
-  c->sched.clear();
+  c->scheds.clear();
   void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
                 c->xy, c->xy0, c->ring_area, c->area, c->err_d, c->w};
   for (void* p : ps)
@@ -1805,16 +1877,18 @@ int cartogram_inverse_project(cg_ctx* c, int64_t n, const double* xy_in, double*
   return c->mixed ? do_inverse_project<float>(c, n, xy_in, xy_out) : do_inverse_project<double>(c, n, xy_in, xy_out);
 }
 
-int cartogram_iteration_gradient(cg_ctx* c, const double* values, double blur_width, double lambda, int replay,
-                                 int checkpoint, double* loss, double* grad_values, double* grad_blur) {
+int cartogram_iteration_gradient(cg_ctx* c, const double* values, double blur_width, double lambda, int iterations,
+                                 int replay, int checkpoint, double* loss, double* grad_values, double* grad_blur) {
   int r = check_ctx(c, true);
   if (r) return r;
   if (c->mixed || c->opt.flow != CG_FLOW_DIFFUSION)
     return fail(c, CG_EINVAL, "the gradient needs the FP64 path and the diffusion flow");
-  if (!values || !is_finite(blur_width) || blur_width < 0.0 || !is_finite(lambda) || lambda < 0.0 || checkpoint < 1)
+  if (!values || !is_finite(blur_width) || blur_width < 0.0 || !is_finite(lambda) || lambda < 0.0 || checkpoint < 1 ||
+      iterations < 1)
     return fail(c, CG_EINVAL, "bad gradient arguments");
   if (!loss && !grad_values && !grad_blur) return fail(c, CG_EINVAL, "no output");
-  return do_iteration_gradient(c, values, blur_width, lambda, replay, checkpoint, loss, grad_values, grad_blur);
+  return do_iteration_gradient(c, values, blur_width, lambda, iterations, replay, checkpoint, loss, grad_values,
+                               grad_blur);
 }
 
 const char* cartogram_last_error(const cg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

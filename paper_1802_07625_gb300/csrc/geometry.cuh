@@ -36,7 +36,7 @@ __device__ __forceinline__ void raster_piece(double ax, double ay, double bx, do
 }
 
 // The pieces of edge P -> Q cut at the grid lines (each inside one cell), in order:
-// piece(ax, ay, bx, by) for every piece.
+// piece(ax, ay, bx, by, s0, s1) for every piece, s0 and s1 its ends as edge parameters.
 template <typename F>
 __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly, F&& piece) {
   const double dx = Q.x - P.x, dy = Q.y - P.y;
@@ -47,9 +47,11 @@ __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly
     gx = dx > 0.0 ? floor(P.x) + 1.0 : ceil(P.x) - 1.0;
     sx = (gx - P.x) / dx;
   }
-  gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
-  sy = (gy - P.y) / dy;
-  double ax = P.x, ay = P.y;
+  if (dy != 0.0) {
+    gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
+    sy = (gy - P.y) / dy;
+  }
+  double ax = P.x, ay = P.y, s0 = 0.0;
   const int guard = Lx + Ly + 4;
   for (int it = 0; it < guard; ++it) {
     const double s1 = fmin(fmin(sx, sy), 1.0);
@@ -61,7 +63,7 @@ __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly
       bx = P.x + s1 * dx;
       by = P.y + s1 * dy;
     }
-    piece(ax, ay, bx, by);
+    piece(ax, ay, bx, by, s0, fmin(s1, 1.0));
     if (s1 >= 1.0) break;
     if (sx <= s1) {
       gx += stx;
@@ -73,6 +75,7 @@ __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly
     }
     ax = bx;
     ay = by;
+    s0 = s1;
   }
 }
 
@@ -84,7 +87,9 @@ __global__ void raster_edges_kernel(const double2* __restrict__ xy, const int* _
     const double2 P = xy[v], Q = xy[next[v]];
     if (wt == 0.0 || Q.y - P.y == 0.0) continue;
     edge_pieces(P, Q, Lx, Ly,
-                [&](double ax, double ay, double bx, double by) { raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly); });
+                [&](double ax, double ay, double bx, double by, double, double) {
+                  raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly);
+                });
   }
 }
 

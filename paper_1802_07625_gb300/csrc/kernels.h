@@ -205,6 +205,22 @@ void launch_raster_adjoint(const double2* xy, const int* next, const int* vreg, 
 void launch_vertex_adjoint(const double2* xy1, const double2* xy0, const int* next, const int* prev,
                            const int* vreg, const double* dLdA, double lam, double2* g, double* lamD, int Lx,
                            int Ly, int n_vert, cudaStream_t s);
+// Vertex adjoints through several outer iterations: the input vertices X_k of iteration k
+// through the map X_{k+1} = X_k + D_k(X_k) (lam_in: adjoint of X_{k+1}) and the exact
+// coverage of the rasteriser (dens: density adjoint per cell, w: the iteration's region
+// weights) into lam_out; the region areas' adjoint dLdA added through the shoelace sums;
+// the loss's vertex adjoint (areas of xy1 and the displacement penalty from xy0); the
+// final displacements' adjoint of a map from xy_pre (lamD [N][2], zeroed first).
+void launch_vertex_map_coverage(const double2* xy, const int* next, const int* vreg, const double* w,
+                                const double* dens, const double2* D, const double2* lam_in, double2* lam_out,
+                                int Lx, int Ly, int n_vert, cudaStream_t s);
+void launch_shoelace_adjoint(const double2* xy, const int* next, const int* prev, const int* vreg,
+                             const double* dLdA, double2* g, int n_vert, cudaStream_t s);
+void launch_loss_vertex_adjoint(const double2* xy1, const double2* xy0, const int* next, const int* prev,
+                                const int* vreg, const double* dLdA, double lam, double2* g, int n_vert,
+                                cudaStream_t s);
+void launch_map_adjoint(const double2* xy_pre, const double2* g, double* lamD, int Lx, int Ly, int n_vert,
+                        cudaStream_t s);
 template <typename T>
 void launch_fold_count(const V2<T>* disp, int Lx, int Ly, unsigned long long* out, cudaStream_t s);
 template <typename T>

@@ -195,6 +195,36 @@ void launch_vertex_adjoint(const double2* xy1, const double2* xy0, const int* ne
   map_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy0, g, lamD, Lx, Ly, n_vert);
 }
 
+void launch_vertex_map_coverage(const double2* xy, const int* next, const int* vreg, const double* w,
+                                const double* dens, const double2* D, const double2* lam_in, double2* lam_out,
+                                int Lx, int Ly, int n_vert, cudaStream_t s) {
+  if (n_vert <= 0) return;
+  const int b = blocks_for(n_vert, 256, 1 << 16);
+  map_jacobian_adjoint_kernel<<<b, 256, 0, s>>>(xy, D, lam_in, lam_out, Lx, Ly, n_vert);
+  coverage_vertex_adjoint_kernel<<<b, 256, 0, s>>>(xy, next, vreg, w, dens, (double*)lam_out, Lx, Ly, n_vert);
+}
+
+void launch_shoelace_adjoint(const double2* xy, const int* next, const int* prev, const int* vreg,
+                             const double* dLdA, double2* g, int n_vert, cudaStream_t s) {
+  if (n_vert <= 0) return;
+  shoelace_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy, next, prev, vreg, dLdA, g, n_vert);
+}
+
+void launch_loss_vertex_adjoint(const double2* xy1, const double2* xy0, const int* next, const int* prev,
+                                const int* vreg, const double* dLdA, double lam, double2* g, int n_vert,
+                                cudaStream_t s) {
+  if (n_vert <= 0) return;
+  vertex_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy1, xy0, next, prev, vreg, dLdA, lam, g,
+                                                                        n_vert);
+}
+
+void launch_map_adjoint(const double2* xy_pre, const double2* g, double* lamD, int Lx, int Ly, int n_vert,
+                        cudaStream_t s) {
+  cudaMemsetAsync(lamD, 0, sizeof(double) * 2 * (size_t)Lx * Ly, s);
+  if (n_vert <= 0) return;
+  map_adjoint_kernel<<<blocks_for(n_vert, 256, 1 << 16), 256, 0, s>>>(xy_pre, g, lamD, Lx, Ly, n_vert);
+}
+
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
                                V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \

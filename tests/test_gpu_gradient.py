@@ -113,3 +113,68 @@ def test_torch_autograd_function_gives_the_librarys_gradient():
     assert abs(float(loss) - ref_loss) <= 1e-12 * abs(ref_loss)
     assert np.max(np.abs(v.grad.numpy() - ref_gv)) <= 1e-12 * np.max(np.abs(ref_gv))
     assert abs(float(b.grad) - ref_gb) <= 1e-12 * abs(ref_gb)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_gradient_through_several_iterations_matches_oracle_differences(orc, K):
+    # through K outer iterations the rasteriser also depends on the vertices moved by the
+    # earlier iterations; the FP64 reference is the central difference of the C oracle's
+    # K-iteration loss with the same replayed schedules (the FP64 path records the same
+    # schedules as the oracle's adaptive runs)
+    from oracle import adjoint as adj
+    m = synth.make_workload("voronoi16_64", L=32, n=8)
+    blur, decay = 1.0, 0.5
+    with P.Cartogram(m.Lx, m.Ly, blur, precision="fp64") as c:
+        c.set_map(m)
+        loss, gv, gb = c.iteration_gradient(m.values, blur, LAM, iterations=K)
+    sch = adj.adaptive_schedules(orc, m, m.values, blur, decay, K)
+    L_ref = adj.cartogram_loss(orc, m, m.values, blur, decay, sch, LAM)
+    assert abs(loss - L_ref) < 1e-9 * abs(L_ref)
+
+    def f(v, b):
+        return adj.cartogram_loss(orc, m, v, b, decay, sch, LAM)
+
+    # the loss is only piecewise smooth: the bilinear point map's derivative jumps where a
+    # vertex moved by an earlier iteration crosses a grid-cell boundary, and a difference
+    # step that straddles such a kink averages two one-sided slopes (at h = 1e-6 one region
+    # of this map is off by 2e-6 that way); h = 1e-7 keeps every region on one side
+    for i in range(m.n_regions):
+        h = 1e-7 * m.values[i]
+        vp, vm = m.values.copy(), m.values.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (f(vp, blur) - f(vm, blur)) / (2 * h)
+        assert abs(fd - gv[i]) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gv))), (i, fd, gv[i])
+    h = 1e-7
+    fd = (f(m.values, blur + h) - f(m.values, blur - h)) / (2 * h)
+    assert abs(fd - gb) <= 1e-6 * abs(fd), (fd, gb)
+
+
+def test_gradient_through_several_iterations_against_gpu_differences():
+    m = synth.make_workload("voronoi16_64")
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64") as c:
+        c.set_map(m)
+        loss, gv, gb = c.iteration_gradient(m.values, 1.0, LAM, iterations=3, checkpoint=6)
+
+        def f(v):
+            return c.iteration_gradient(v, 1.0, LAM, replay=True, grad=False, iterations=3)
+
+        # the loss is piecewise smooth (the point map's kinks, see above) and the GPU's loss
+        # carries ~1e-13 of rounding from the rasteriser's atomic sums, which rules out steps
+        # much below 1e-6; regions 5 and 11 of this map have a kink within 1e-6 of the point,
+        # so the difference that stays on the point's own piece (central, forward or
+        # backward) must match
+        L0 = f(m.values)
+        for i in (0, 5, 11):
+            h = 1e-6 * m.values[i]
+            vp, vm = m.values.copy(), m.values.copy()
+            vp[i] += h
+            vm[i] -= h
+            Lp, Lm = f(vp), f(vm)
+            diffs = [(Lp - Lm) / (2 * h), (Lp - L0) / h, (L0 - Lm) / h]
+            err = min(abs(d - gv[i]) for d in diffs)
+            assert err <= 1e-6 * abs(gv[i]), (i, diffs, gv[i])
+        with pytest.raises(P.CartogramError) as e:
+            c.iteration_gradient(m.values, 1.0, LAM, replay=True, iterations=2)  # recorded with 3
+        assert e.value.code == P.CG_ESTATE
+        assert np.array_equal(c.vertices(), m.xy) and c.history_length() == 0

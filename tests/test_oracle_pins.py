@@ -687,3 +687,21 @@ def test_adjoint_gradient_matches_central_differences(orc):
     fd = (loss(m.values, blur + h) - loss(m.values, blur - h)) / (2 * h)
     assert abs(fd - gs) <= 1e-6 * abs(fd)
     assert np.max(np.abs(gv)) > 0 and gs != 0
+
+
+def test_multi_iteration_oracle_loss_reduces_to_the_reference(orc):
+    # one iteration of the C-oracle loss with the replayed schedule equals the autograd
+    # reference's loss (itself pinned to the oracle's integration above)
+    import torch
+    adj, m, A, it, blur, spec_t, r = _adjoint_case(orc)
+    steps = adj.accepted_steps(r.sched_h, r.sched_acc)
+    sch = adj.adaptive_schedules(orc, m, m.values, blur, 0.5, 2)
+    assert sch[0] == steps and len(sch[1]) > 0
+    with torch.no_grad():
+        L_t, _ = it.loss(torch.tensor(m.values), torch.tensor(blur, dtype=torch.float64), steps, 1e-3)
+    L_c = adj.cartogram_loss(orc, m, m.values, blur, 0.5, [steps], 1e-3)
+    assert abs(L_c - float(L_t)) < 1e-10 * abs(L_c)
+    # a second iteration moves the areas further towards their targets
+    L_2 = adj.cartogram_loss(orc, m, m.values, blur, 0.5, sch, 0.0)
+    L_1 = adj.cartogram_loss(orc, m, m.values, blur, 0.5, sch[:1], 0.0)
+    assert L_2 < L_1
