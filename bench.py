@@ -264,11 +264,19 @@ def run_reference(args):
 def run_batched(args, P, synth, flush, stream):
     """The batched workload: 64 independent frames (grid sizes from {128, ..., 1024}^2)
     as parallel branches of one CUDA-graph launch, against the same contexts run one
-    after another. Host wall clock around the synchronous batch call."""
+    after another. Host wall clock around the synchronous batch call. With several
+    ranks the frames are split between them (greedy balance of the expected updates, no
+    collective on the data path): each rank runs its share as one batch, the time is the
+    slowest rank's and the per-frame results are gathered to rank 0."""
     import collections
 
     import torch
-    frames = synth.make_batch()
+
+    from paper_1802_07625_gb300 import shard
+    world, rank, _ = _dist()
+    frames_all = synth.make_batch()
+    mine = shard.partition([shard.frame_cost(f.Lx, f.Ly) for f in frames_all], world)[rank]
+    frames = [frames_all[i] for i in mine]
     carts = [P.Cartogram(f.Lx, f.Ly, synth.BATCH["blur"], precision="mixed") for f in frames]
     try:
         for c, f in zip(carts, frames):
@@ -276,36 +284,51 @@ def run_batched(args, P, synth, flush, stream):
             c.integrate()  # picks the launch shapes, as in a first use
         torch.cuda.synchronize()
         # one after another (each context's own device-side loop)
+        _barrier(world)
         t = time.perf_counter()
         for c in carts:
             c.reset()
             c.integrate()
-        seq_s = time.perf_counter() - t
-        with P.Batch(carts) as b:
-            for c in carts:
-                c.reset()
-            b.integrate()  # captures the batch graph
-            times, stats = [], None
+        seq_s = _max_over_ranks(world, time.perf_counter() - t)
+        times, stats = [], []
+        batch = P.Batch(carts) if carts else None
+        try:
+            if batch:
+                for c in carts:
+                    c.reset()
+                batch.integrate()  # captures the batch graph
             for _ in range(args.batch_steps):
                 for c in carts:
                     c.reset()
                 with torch.cuda.stream(stream):
                     flush.zero_()
                 torch.cuda.synchronize()
+                _barrier(world)
                 t = time.perf_counter()
-                stats, status = b.integrate()
-                times.append(time.perf_counter() - t)
+                if batch:
+                    stats, status = batch.integrate()
+                times.append(_max_over_ranks(world, time.perf_counter() - t))
+        finally:
+            if batch:
+                batch.close()
         s_batch = sum(times) / len(times)
-        updates = sum(f.Lx * f.Ly * (s.steps_accepted + s.steps_rejected) for f, s in zip(frames, stats))
-        its = [s.iterations for s in stats]
+        local = [(f.Lx, f.Ly, s.steps_accepted + s.steps_rejected, s.iterations, s.converged)
+                 for f, s in zip(frames, stats)]
+        res = shard.gather_results(world, rank, mine, local)
+        if rank != 0:
+            return None
+        updates = sum(lx * ly * att for lx, ly, att, _, _ in res)
+        its = [r[3] for r in res]
         return {"workload": "64 frames, 300-region Voronoi maps, lognormal(1) values drifting by a "
                             "multiplicative random walk, blur %g, mixed" % synth.BATCH["blur"],
-                "size_counts": {str(k): v for k, v in sorted(collections.Counter(f.Lx for f in frames).items())},
+                "size_counts": {str(k): v for k, v in sorted(collections.Counter(f.Lx for f in frames_all).items())},
+                "ranks": world, "frames_per_rank": [len(p) for p in shard.partition(
+                    [shard.frame_cost(f.Lx, f.Ly) for f in frames_all], world)],
                 "s_per_batch": s_batch, "updates_per_s": updates / s_batch,
                 "sequential_s": seq_s, "speedup_vs_sequential": seq_s / s_batch,
-                "all_converged": all(s.converged for s in stats), "iterations_min_max": [min(its), max(its)],
-                "timing": "host wall clock around cartogram_batch_integrate (synchronous), mean of %d"
-                          % args.batch_steps}
+                "all_converged": all(r[4] for r in res), "iterations_min_max": [min(its), max(its)],
+                "timing": "host wall clock around cartogram_batch_integrate (synchronous), slowest rank, "
+                          "mean of %d" % args.batch_steps}
     except P.CartogramError as e:
         return {"error": str(e)}
     finally:

@@ -1269,6 +1269,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   std::vector<std::vector<double>> A(K, std::vector<double>(R));
   std::vector<double> sigma(K), decay(K);
   if (!replay) c->scheds.assign(K, std::vector<double>());
+  double2* D_last = nullptr;
   // forward: K outer iterations from the current vertices
   for (int k = 0; k < K; ++k) {
     decay[k] = std::pow(c->opt.blur_decay, (double)(c->hist_len + k));
@@ -1305,7 +1306,9 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
       CG_CUDA(c, cudaMalloc((void**)&p, sizeof(double2) * N));
       a->ckpt.push_back(p);
     }
-    double2* Dk = adj_replay(c, c->scheds[k], C, false);
+    // the last iteration's replay keeps its checkpoints for the reverse pass
+    double2* Dk = adj_replay(c, c->scheds[k], C, k == K - 1);
+    if (k == K - 1) D_last = Dk;
     cg::launch_map_points<double>(a->X[k], a->X[k + 1], nv, Dk, c->Lx, c->Ly, s);
     CG_CUDA(c, cudaGetLastError());
   }
@@ -1353,9 +1356,10 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
       // the iteration's spectrum, blur factors and integration
       CG_CUDA(c, cudaMemcpyAsync(c->spec64, a->spec[k], sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
       cg::launch_blur_tables(nullptr, sigma[k], c->bx, c->by, c->Lx, c->Ly, s);
-      // (the replay's buffers are reused by the reverse pass: keep D_k aside)
-      CG_CUDA(c, cudaMemcpyAsync(a->Dk, adj_replay(c, c->scheds[k], C, true), sizeof(double2) * N,
-                                 cudaMemcpyDeviceToDevice, s));
+      // (the replay's buffers are reused by the reverse pass: keep D_k aside; the last
+      // iteration's checkpoints and displacements are still those of the forward pass)
+      double2* Dk = k == K - 1 ? D_last : adj_replay(c, c->scheds[k], C, true);
+      CG_CUDA(c, cudaMemcpyAsync(a->Dk, Dk, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
       // the map X_{k+1} = X_k + D_k(X_k): the displacements' adjoint
       cg::launch_map_adjoint(a->X[k], lamX, (double*)a->lam, c->Lx, c->Ly, nv, s);
       adj_reverse(c, c->scheds[k], C);

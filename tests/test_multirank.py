@@ -43,3 +43,37 @@ def test_two_rank_replica_throughput():
     for r, w, value in out:
         assert w == 2
         assert value == pytest.approx((1e9 + 2e9) / 3.0)
+
+
+def _shard_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    from paper_1802_07625_gb300 import shard, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    frames = synth.make_batch(frames=10, sizes=(128, 256))
+    costs = [shard.frame_cost(f.Lx, f.Ly) for f in frames]
+    mine = shard.partition(costs, world)[rank]
+    # each rank "runs" its frames: here the result is the frame's size and a rank tag
+    res = shard.gather_results(world, rank, mine, [(frames[i].Lx, rank) for i in mine])
+    q.put((rank, mine, res))
+    dist.destroy_process_group()
+
+
+def test_two_rank_batch_sharding_gathers_every_frame_once():
+    from paper_1802_07625_gb300 import shard, synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(k, 2, port, q)) for k in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    frames = synth.make_batch(frames=10, sizes=(128, 256))
+    (r0, mine0, res0), (r1, mine1, res1) = out
+    assert sorted(mine0 + mine1) == list(range(10)) and not set(mine0) & set(mine1)
+    assert res1 is None
+    assert [r[0] for r in res0] == [f.Lx for f in frames]
+    assert all(res0[i][1] == 0 for i in mine0) and all(res0[i][1] == 1 for i in mine1)
