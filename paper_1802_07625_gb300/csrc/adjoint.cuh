@@ -233,13 +233,10 @@ __global__ void raster_adjoint_kernel(const double2* __restrict__ xy, const int*
     const double2 P = xy[v], Q = xy[next[v]];
     if (Q.y - P.y == 0.0) continue;
     double g = 0.0;
-    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double, double) {
+    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double, double, int ii, int jj) {
       const double pdy = by - ay;
-      if (pdy == 0.0) return;
-      const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
-      const int jj = (int)floor(my);
-      if (jj < 0 || jj >= Ly) return;
-      const int ii = (int)floor(mx);
+      if (pdy == 0.0 || jj < 0 || jj >= Ly) return;
+      const double mx = 0.5 * (ax + bx);
       const double c = -pdy;
       const double* row = lam + (size_t)jj * Lx;
       if (ii < 0) {
@@ -307,9 +304,7 @@ __global__ void coverage_vertex_adjoint_kernel(const double2* __restrict__ xy, c
     if (dx == 0.0 && dy == 0.0) continue;
     const double wr = w[vreg[v]];
     double aP = 0.0, aQ = 0.0;  // sum of lam_c times the hat integrals
-    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double s0, double s1) {
-      const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
-      const int jj = (int)floor(my), ii = (int)floor(mx);
+    edge_pieces(P, Q, Lx, Ly, [&](double, double, double, double, double s0, double s1, int ii, int jj) {
       if (jj < 0 || jj >= Ly || ii < 0 || ii >= Lx) return;
       const double lc = lam[(size_t)jj * Lx + ii];
       const double q = 0.5 * (s1 * s1 - s0 * s0);

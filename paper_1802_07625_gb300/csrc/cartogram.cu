@@ -96,7 +96,7 @@ struct cg_ctx {
   int* vreg = nullptr;
   double2* xy = nullptr;
   double2* xy0 = nullptr;  // vertices as given to set_regions
-  double* ring_area = nullptr;
+  double* area_sums = nullptr;  // (sum A, sum V) of the last area computation
   double* area = nullptr;
   double* err_d = nullptr;
   double* w = nullptr;
@@ -531,7 +531,7 @@ cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaS
   cudaGraphConditionalHandle ho = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, 0);
   if (e != cudaSuccess) return e;
-  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, c->values, c->R_n,
+  cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings, c->values, c->R_n,
                    c->area, c->err_d, c->w, c->info, cs);
   cg::launch_outer_decide(c->outer, c->info, ho, 0, cs);
   const int N = c->Lx * c->Ly;
@@ -545,7 +545,7 @@ cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaS
     if ((eb = capture_integration<T>(c, s, bs2, nullptr)) != cudaSuccess) return eb;
     cg::launch_outer_commit<T>(c->outer, c->info, (const V2<T>*)c->dres, N, s);
     cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s, &c->outer->status);
-    cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, c->values, c->R_n,
+    cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings, c->values, c->R_n,
                      c->area, c->err_d, c->w, c->info, s);
     cg::launch_outer_decide(c->outer, c->info, ho, 1, s);
     return cudaGetLastError();
@@ -701,7 +701,7 @@ int run_raster(cg_ctx* c) {
 }
 
 int run_areas(cg_ctx* c) {
-  cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings,
+  cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings,
                    c->values, c->R_n, c->area, c->err_d, c->w, c->info, c->stream);
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;
@@ -1274,7 +1274,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   for (int k = 0; k < K; ++k) {
     decay[k] = std::pow(c->opt.blur_decay, (double)(c->hist_len + k));
     sigma[k] = blur * decay[k];
-    cg::launch_areas(a->X[k], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R,
+    cg::launch_areas(a->X[k], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R,
                      c->area, c->err_d, c->w, c->info, s);
     CG_CUDA(c, cudaMemcpyAsync(A[k].data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
     CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * N, s));
@@ -1315,7 +1315,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   c->have_spectrum = true;
   c->blur_tab_sigma = -1.0;
   // the loss on the final vertices
-  cg::launch_areas(a->X[K], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R, c->area,
+  cg::launch_areas(a->X[K], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R, c->area,
                    c->err_d, c->w, c->info, s);
   std::vector<double> A1(R);
   std::vector<double2> X0(nv), X1(nv);
@@ -1369,7 +1369,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
       cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, a->flux, nullptr, a->dens,
                                   (const double2*)c->Wy, (const double2*)c->Ey, c->st, cg::kModeFlux, s);
       // the iteration's region weights again (for the coverage adjoint of its vertices)
-      cg::launch_areas(a->X[k], c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings, a->vals, R,
+      cg::launch_areas(a->X[k], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R,
                        c->area, c->err_d, c->w, c->info, s);
       if (k > 0)
         cg::launch_vertex_map_coverage(a->X[k], c->next, c->vreg, c->w, a->dens, a->Dk, lamX, lamX2, c->Lx, c->Ly,
@@ -1449,7 +1449,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
           break;
         default:
           cg::launch_map_points<T>(c->xy0, c->pts, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s);
-          cg::launch_areas(c->xy, c->ring_off, c->ring_area, c->n_rings, c->reg_off, c->reg_rings,
+          cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings,
                            c->values, c->R_n, c->area, c->err_d, c->w, c->info, s);
           break;
       }
@@ -1476,12 +1476,12 @@ void free_regions(cg_ctx* c) {
   c->prev = nullptr;
   c->scheds.clear();
   void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
-                c->xy, c->xy0, c->ring_area, c->area, c->err_d, c->w};
+                c->xy, c->xy0, c->area_sums, c->area, c->err_d, c->w};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->values = nullptr; c->ring_off = nullptr; c->reg_off = nullptr; c->reg_rings = nullptr;
   c->next = nullptr; c->vreg = nullptr; c->xy = nullptr; c->xy0 = nullptr;
-  c->ring_area = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
+  c->area_sums = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
   c->have_regions = false;
 }
 
@@ -1686,7 +1686,7 @@ int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values,
   CG_CUDA(c, cudaMalloc((void**)&c->vreg, sizeof(int) * nv));
   CG_CUDA(c, cudaMalloc((void**)&c->xy, sizeof(double2) * nv));
   CG_CUDA(c, cudaMalloc((void**)&c->xy0, sizeof(double2) * nv));
-  CG_CUDA(c, cudaMalloc((void**)&c->ring_area, sizeof(double) * n_rings));
+  CG_CUDA(c, cudaMalloc((void**)&c->area_sums, sizeof(double) * 2));
   CG_CUDA(c, cudaMalloc((void**)&c->area, sizeof(double) * n_regions));
   CG_CUDA(c, cudaMalloc((void**)&c->err_d, sizeof(double) * n_regions));
   CG_CUDA(c, cudaMalloc((void**)&c->w, sizeof(double) * n_regions));

@@ -17,39 +17,47 @@ namespace cg {
 // extent dy and mean abscissa x_m adds -w dy (i+1 - x_m) to D[j][i] and -w dy (x_m - i)
 // to D[j][i+1]; the prefix sum of D along each row is the coverage-weighted density.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void raster_piece(double ax, double ay, double bx, double by, double wt,
+// Deposit of one piece inside cell (i, j): c = -w dy to D[j][i] and D[j][i+1] in the
+// proportions (i+1 - x_m) and (x_m - i); a piece left of the box (i < 0) deposits all of
+// c in column 0.
+__device__ __forceinline__ void raster_piece(double ax, double bx, double pdy, int i, int j, double wt,
                                              double* __restrict__ acc, int Lx, int Ly) {
-  const double pdy = by - ay;
-  if (pdy == 0.0) return;
-  const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
-  const int j = (int)floor(my);
-  if (j < 0 || j >= Ly) return;
-  const int i = (int)floor(mx);
+  if (pdy == 0.0 || j < 0 || j >= Ly) return;
   const double c = -wt * pdy;
   double* row = acc + (size_t)j * Lx;
   if (i < 0) {
     atomicAdd(row, c);
   } else if (i < Lx) {
-    atomicAdd(row + i, c * ((double)(i + 1) - mx));
-    if (i + 1 < Lx) atomicAdd(row + i + 1, c * (mx - (double)i));
+    const double t = c * (0.5 * (ax + bx) - (double)i);
+    atomicAdd(row + i, c - t);
+    if (i + 1 < Lx) atomicAdd(row + i + 1, t);
   }
 }
 
-// The pieces of edge P -> Q cut at the grid lines (each inside one cell), in order:
-// piece(ax, ay, bx, by, s0, s1) for every piece, s0 and s1 its ends as edge parameters.
+// The pieces of edge P -> Q cut at the grid lines, in order: piece(ax, ay, bx, by, s0,
+// s1, i, j) for every piece, s0 and s1 its ends as edge parameters and (i, j) the cell
+// that holds it. The cell is tracked across the crossings (the first from the start
+// point and the direction, then +-1 per grid line crossed), and the crossings use the
+// reciprocals of the edge's extents: GB300's FP64 rate makes divisions and floors per
+// piece the bulk of the rasteriser's work.
 template <typename F>
 __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly, F&& piece) {
   const double dx = Q.x - P.x, dy = Q.y - P.y;
   // next grid line crossed along x and along y, as edge parameters in (0, 1]
-  double gx = 0.0, gy = 0.0, sx = 2.0, sy = 2.0;
-  const double stx = dx > 0.0 ? 1.0 : -1.0, sty = dy > 0.0 ? 1.0 : -1.0;
+  double gx = 0.0, gy = 0.0, sx = 2.0, sy = 2.0, rx = 0.0, ry = 0.0;
+  const int stx = dx > 0.0 ? 1 : -1, sty = dy > 0.0 ? 1 : -1;
+  int i = (int)floor(P.x), j = (int)floor(P.y);
   if (dx != 0.0) {
-    gx = dx > 0.0 ? floor(P.x) + 1.0 : ceil(P.x) - 1.0;
-    sx = (gx - P.x) / dx;
+    if (dx < 0.0) i = (int)ceil(P.x) - 1;
+    gx = dx > 0.0 ? (double)(i + 1) : (double)i;
+    rx = 1.0 / dx;
+    sx = (gx - P.x) * rx;
   }
   if (dy != 0.0) {
-    gy = dy > 0.0 ? floor(P.y) + 1.0 : ceil(P.y) - 1.0;
-    sy = (gy - P.y) / dy;
+    if (dy < 0.0) j = (int)ceil(P.y) - 1;
+    gy = dy > 0.0 ? (double)(j + 1) : (double)j;
+    ry = 1.0 / dy;
+    sy = (gy - P.y) * ry;
   }
   double ax = P.x, ay = P.y, s0 = 0.0;
   const int guard = Lx + Ly + 4;
@@ -63,15 +71,17 @@ __device__ __forceinline__ void edge_pieces(double2 P, double2 Q, int Lx, int Ly
       bx = P.x + s1 * dx;
       by = P.y + s1 * dy;
     }
-    piece(ax, ay, bx, by, s0, fmin(s1, 1.0));
+    piece(ax, ay, bx, by, s0, fmin(s1, 1.0), i, j);
     if (s1 >= 1.0) break;
     if (sx <= s1) {
-      gx += stx;
-      sx = (gx - P.x) / dx;
+      i += stx;
+      gx += (double)stx;
+      sx = (gx - P.x) * rx;
     }
     if (sy <= s1) {
-      gy += sty;
-      sy = (gy - P.y) / dy;
+      j += sty;
+      gy += (double)sty;
+      sy = (gy - P.y) * ry;
     }
     ax = bx;
     ay = by;
@@ -86,10 +96,9 @@ __global__ void raster_edges_kernel(const double2* __restrict__ xy, const int* _
     const double wt = w[vreg[v]];
     const double2 P = xy[v], Q = xy[next[v]];
     if (wt == 0.0 || Q.y - P.y == 0.0) continue;
-    edge_pieces(P, Q, Lx, Ly,
-                [&](double ax, double ay, double bx, double by, double, double) {
-                  raster_piece(ax, ay, bx, by, wt, acc, Lx, Ly);
-                });
+    edge_pieces(P, Q, Lx, Ly, [&](double ax, double ay, double bx, double by, double, double, int i, int j) {
+      raster_piece(ax, bx, by - ay, i, j, wt, acc, Lx, Ly);
+    });
   }
 }
 
@@ -131,26 +140,48 @@ __global__ void row_scan_kernel(double* __restrict__ acc, int Lx) {
 }
 
 // ---------------------------------------------------------------------------
-// Areas: shoelace formula per ring (relative to the ring's first vertex), one warp
-// per ring; then per region the signed sum over its rings, the relative errors
-// err_r = A_r / A^_r - 1 with A^_r = V_r sum(A) / sum(V), and the rasterisation
-// weights w_r = A^_r / A_r - 1. One block.
+// Areas: per region the signed sum of its rings' shoelace areas (each ring relative to
+// its first vertex), one warp per region; then sum(A) and sum(V) in one block (a fixed
+// order, so the result does not vary from run to run); then per region the relative
+// error err_r = A_r / A^_r - 1 with A^_r = V_r sum(A) / sum(V), the rasterisation weight
+// w_r = A^_r / A_r - 1 and the largest |err_r|. GB300's FP64 rate bounds these kernels:
+// the division-heavy last step is spread over many blocks.
 // ---------------------------------------------------------------------------
-__global__ void ring_area_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
-                                 double* __restrict__ ring_area, long long n_rings) {
-  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void region_area_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
+                                   const int* __restrict__ reg_off, const int* __restrict__ reg_rings,
+                                   int R, double* __restrict__ area) {
+  const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (r >= n_rings) return;
-  const long long a = off[r], b = off[r + 1];
-  const double2 o = xy[a];
-  double s = 0.0;
-  for (long long k = a + lane; k < b; k += 32) {
-    const double2 p = xy[k];
-    const double2 q = xy[k + 1 < b ? k + 1 : a];
-    s += (p.x - o.x) * (q.y - o.y) - (q.x - o.x) * (p.y - o.y);
+  if (r >= R) return;  // whole warps leave together
+  double A = 0.0;
+  for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) {
+    const int ring = reg_rings[k];
+    const long long a = off[ring], b = off[ring + 1];
+    const double2 o = xy[a];
+    double s = 0.0;
+    for (long long c = a; c < b; c += 32) {
+      // lane l holds the offset of vertex c + l from o; its successor's comes from lane
+      // l + 1, lane 31 loads it (the successor of the last vertex is o: offset 0)
+      const long long v = c + lane;
+      double2 d = make_double2(0.0, 0.0);
+      if (v < b) {
+        const double2 p = xy[v];
+        d = make_double2(p.x - o.x, p.y - o.y);
+      }
+      double2 e = make_double2(__shfl_down_sync(0xffffffffu, d.x, 1), __shfl_down_sync(0xffffffffu, d.y, 1));
+      if (lane == 31) {
+        e = make_double2(0.0, 0.0);
+        if (v + 1 < b) {
+          const double2 q = xy[v + 1];
+          e = make_double2(q.x - o.x, q.y - o.y);
+        }
+      }
+      s += d.x * e.y - e.x * d.y;
+    }
+    s = warp_sum(s);
+    A += 0.5 * s;
   }
-  s = warp_sum(s);
-  if (lane == 0) ring_area[r] = 0.5 * s;
+  if (lane == 0) area[r] = A;
 }
 
 __device__ __forceinline__ double block_sum_det(double v, double* red) {
@@ -165,32 +196,41 @@ __device__ __forceinline__ double block_sum_det(double v, double* red) {
   return t;
 }
 
-__global__ void region_kernel(const double* __restrict__ ring_area, const int* __restrict__ reg_off,
-                              const int* __restrict__ reg_rings, const double* __restrict__ values,
-                              int R, double* __restrict__ area, double* __restrict__ err,
-                              double* __restrict__ w, IterInfo* info) {
+// sums[0] = sum(A), sums[1] = sum(V); resets the largest error (one block).
+__global__ void area_sums_kernel(const double* __restrict__ area, const double* __restrict__ values, int R,
+                                 double* __restrict__ sums, IterInfo* info) {
   __shared__ double red[32];
   double sa = 0.0, sv = 0.0;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double A = 0.0;
-    for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) A += ring_area[reg_rings[k]];
-    area[r] = A;
-    sa += A;
+    sa += area[r];
     sv += values[r];
   }
   sa = block_sum_det(sa, red);
   sv = block_sum_det(sv, red);
+  if (threadIdx.x == 0) {
+    sums[0] = sa;
+    sums[1] = sv;
+    info->max_err = 0.0;
+  }
+}
+
+__global__ void region_error_kernel(const double* __restrict__ area, const double* __restrict__ values, int R,
+                                    const double* __restrict__ sums, double* __restrict__ err,
+                                    double* __restrict__ w, IterInfo* info) {
+  const double sa = sums[0], sv = sums[1];
   double mx = 0.0;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
     const double target = values[r] * sa / sv;
     const double A = area[r];
     const double e = A / target - 1.0;
     err[r] = e;
     w[r] = target / A - 1.0;
-    mx = fmax(mx, fabs(e));
+    mx = fmax(mx, fabs(e));  // a NaN error (degenerate area) does not count
   }
-  mx = block_max(mx, red);
-  if (threadIdx.x == 0) info->max_err = mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&info->max_err), mx);
 }
 
 // Copy the integration's outcome into the per-iteration record.

@@ -229,9 +229,10 @@ void launch_map_points(const double2* in, double2* out, long long n, const V2<T>
 
 void launch_raster(const double2* xy, const int* next, const int* vreg, const double* w,
                    double* acc, int Lx, int Ly, int n_vert, cudaStream_t s);
-void launch_areas(const double2* xy, const long long* ring_off, double* ring_area,
-                  long long n_rings, const int* reg_off, const int* reg_rings,
-                  const double* values, int R, double* area, double* err, double* w,
+// Region areas, sums[0..1] = (sum A, sum V) (scratch of two doubles), relative errors,
+// rasterisation weights and the largest |error| into info->max_err.
+void launch_areas(const double2* xy, const long long* ring_off, double* sums, const int* reg_off,
+                  const int* reg_rings, const double* values, int R, double* area, double* err, double* w,
                   IterInfo* info, cudaStream_t s);
 void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s);
 

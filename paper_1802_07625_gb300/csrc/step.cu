@@ -71,13 +71,13 @@ void launch_raster(const double2* xy, const int* next, const int* vreg, const do
   row_scan_kernel<<<Ly, t, 0, s>>>(acc, Lx);
 }
 
-void launch_areas(const double2* xy, const long long* ring_off, double* ring_area,
-                  long long n_rings, const int* reg_off, const int* reg_rings,
-                  const double* values, int R, double* area, double* err, double* w,
+void launch_areas(const double2* xy, const long long* ring_off, double* sums, const int* reg_off,
+                  const int* reg_rings, const double* values, int R, double* area, double* err, double* w,
                   IterInfo* info, cudaStream_t s) {
-  ring_area_kernel<<<blocks_for(n_rings * 32, 256, 1 << 20), 256, 0, s>>>(xy, ring_off, ring_area,
-                                                                          n_rings);
-  region_kernel<<<1, 1024, 0, s>>>(ring_area, reg_off, reg_rings, values, R, area, err, w, info);
+  region_area_kernel<<<blocks_for((long long)R * 32, 256, 1 << 20), 256, 0, s>>>(xy, ring_off, reg_off,
+                                                                                reg_rings, R, area);
+  area_sums_kernel<<<1, 1024, 0, s>>>(area, values, R, sums, info);
+  region_error_kernel<<<blocks_for(R, 32, sm_count()), 32, 0, s>>>(area, values, R, sums, err, w, info);
 }
 
 void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s) {
