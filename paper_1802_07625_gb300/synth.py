@@ -240,6 +240,24 @@ def rectangle_ring(x0, y0, x1, y1, spacing):
     return np.array(pts, dtype=np.float64)
 
 
+def holes_map(L: int = 64, spacing: float = 0.5) -> RegionMap:
+    """Four regions on an L x L grid with multi-ring structure: region 0 is a square with
+    a square hole (a clockwise ring), region 2 fills the hole, region 1 is two islands
+    (listed apart in the ring order), region 3 is a strip. Rings:
+    [0 outer, 1 island, 0 hole, 2, 3, 1 island]."""
+    f = L / 64.0
+
+    def sq(x0, y0, x1, y1):
+        return rectangle_ring(x0 * f, y0 * f, x1 * f, y1 * f, spacing)
+
+    rings = [sq(8, 8, 40, 40), sq(44, 8, 56, 20), sq(16, 16, 28, 28)[::-1].copy(), sq(16, 16, 28, 28),
+             sq(8, 44, 56, 56), sq(44, 26, 56, 40)]
+    region = np.array([0, 1, 0, 2, 3, 1], dtype=np.int32)
+    offsets = np.cumsum([0] + [r.shape[0] for r in rings]).astype(np.int64)
+    return RegionMap(L, L, np.array([1.0, 4.0, 6.0, 2.0]), offsets, region, np.concatenate(rings, axis=0),
+                     meta={"name": "holes", "L": L})
+
+
 def strip_map(Lx: int, Ly: int, cuts, values, spacing: float = 0.5) -> RegionMap:
     """Vertical strips [cuts[k], cuts[k+1]] x [0, Ly] that tile the whole box.
 

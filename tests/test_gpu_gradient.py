@@ -110,7 +110,7 @@ def test_torch_autograd_function_gives_the_librarys_gradient():
         b = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
         loss = P.iteration_loss(v, b, c, lam=LAM)
         loss.backward()
-    assert abs(float(loss) - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-12 * abs(ref_loss)
     assert np.max(np.abs(v.grad.numpy() - ref_gv)) <= 1e-12 * np.max(np.abs(ref_gv))
     assert abs(float(b.grad) - ref_gb) <= 1e-12 * abs(ref_gb)
 

@@ -151,6 +151,31 @@ def test_full_cartogram_matches_oracle(orc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_holes_and_islands_match_oracle(orc, precision):
+    # a region with a hole (clockwise ring), a region filling the hole, and a region of two
+    # islands listed apart in the ring order: densities, areas, and the whole cartogram
+    m = synth.holes_map(64)
+    with _ctx(m, 1.0, precision) as c:
+        rho = c.density()
+        err0 = c.area_errors()
+        st = c.integrate()
+        xy = c.vertices()
+        err = c.area_errors()
+        nhist = c.history_length()
+    ref = _oracle_density(orc, m)
+    assert np.max(np.abs(rho - ref)) < 1e-11 * np.max(np.abs(ref))
+    A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    assert np.allclose(A, [32 * 32 - 12 * 12, 12 * 12 + 12 * 14, 12 * 12, 48 * 12], rtol=1e-14)
+    assert np.max(np.abs(err0 - (A / (m.values * A.sum() / m.values.sum()) - 1.0))) < 1e-13
+    r = orc.cartogram(m, blur=1.0)
+    assert r.converged and st.converged
+    assert st.iterations == r.iterations == nhist
+    tol = FP64_POS_TOL if precision == "fp64" else MIXED_POS_TOL
+    assert np.max(np.abs(xy - r.xy)) < tol
+    assert np.max(np.abs(err - r.err)) < AREA_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("L", [64, 256])
 def test_step_loop_modes_agree(precision, L):
     # persistent cooperative kernel, conditional CUDA graph and host-driven loop run the
