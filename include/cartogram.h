@@ -96,6 +96,12 @@ typedef struct cg_options {
     int flow;           /* CG_FLOW_DIFFUSION (default) or CG_FLOW_LINEAR. With the linear flow
                            dt0 is in units of its time t in [0, 1], every integration ends at
                            t = 1, rho_tol is not used, and use_graph = 2 runs as 1 */
+    double time_limit;  /* seconds of device time one cartogram_integrate (or one batch call,
+                           per context) may take; 0 (default): no limit. The device clock is
+                           read when the call starts and by the step controller after every
+                           attempted step: past the limit, the integration in flight ends with
+                           CG_ETIMEOUT and maps nothing (the vertices and history keep the
+                           iterations completed before it). Must be finite and >= 0 */
 } cg_options;
 
 typedef struct cg_stats {

@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("flow", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("flow", ctypes.c_int), ("time_limit", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -89,6 +89,7 @@ __device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
   }
   if (status == kRunning) {
     if (st->accepted + st->rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
+    else if (deadline_passed(sp)) status = kTimeout;
     else if (st->vmax > 0.0 && h * st->vmax > sp.cfl) h = sp.cfl / st->vmax;
   }
   st->h = h;
@@ -128,6 +129,7 @@ __device__ __forceinline__ void control_linear(DevState* st, const StepParams& s
   }
   if (status == kRunning) {
     if (st->accepted + st->rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
+    else if (deadline_passed(sp)) status = kTimeout;
     else {
       if (st->vmax > 0.0 && h * st->vmax > sp.cfl) h = sp.cfl / st->vmax;
       if (h > 1.0 - st->t) h = 1.0 - st->t;

@@ -80,6 +80,7 @@ struct cg_ctx {
   void* flux = nullptr;      // linear flow: J = -grad Phi at the cell centres
   void* rho0 = nullptr;      // linear flow: initial density at the cell centres
   DevState* st = nullptr;
+  unsigned long long* deadline = nullptr;  // device-clock deadline of the call in flight (0: none)
   IterInfo* info = nullptr;
   IterInfo* info_h = nullptr;  // pinned
   bool have_spectrum = false;
@@ -183,6 +184,12 @@ int ilog2(int n) {
   return l;
 }
 
+// Start of a call: the deadline is the device clock now plus the time limit (0: none).
+void stamp_deadline(cg_ctx* c, bool limited = true) {
+  const double ns = limited ? c->opt.time_limit * 1e9 : 0.0;
+  cg::launch_deadline(c->deadline, ns > 0.0 ? (unsigned long long)ns + 1ull : 0ull, c->stream);
+}
+
 StepParams step_params(const cg_ctx* c) {
   StepParams sp;
   sp.dt0 = c->opt.dt0;
@@ -194,6 +201,7 @@ StepParams step_params(const cg_ctx* c) {
   sp.h_min = 0.0;
   sp.max_steps = c->opt.max_steps;
   sp.sched = c->sched_rec;
+  sp.deadline = c->deadline;
   return sp;
 }
 
@@ -277,6 +285,8 @@ int alloc_fields(cg_ctx* c) {
   }
   CG_CUDA(c, cudaMalloc((void**)&c->st, sizeof(DevState)));
   CG_CUDA(c, cudaMemset(c->st, 0, sizeof(DevState)));
+  CG_CUDA(c, cudaMalloc((void**)&c->deadline, sizeof(unsigned long long)));
+  CG_CUDA(c, cudaMemset(c->deadline, 0, sizeof(unsigned long long)));
   CG_CUDA(c, cudaMalloc((void**)&c->info, sizeof(IterInfo)));
   CG_CUDA(c, cudaMallocHost((void**)&c->info_h, sizeof(IterInfo)));
   CG_CUDA(c, cudaMemset(c->spec64, 0, sizeof(double) * N));
@@ -912,6 +922,7 @@ int do_integrate(cg_ctx* c, cg_stats* stats) {
   cg_stats s;
   memset(&s, 0, sizeof s);
   int status;
+  stamp_deadline(c);
   if (c->opt.use_graph == 1) status = do_integrate_device<T>(c, s);
   else status = do_integrate_host<T>(c, s, c->opt.max_iter, true, nullptr);
   s.converged = s.max_area_error < c->opt.area_tol;
@@ -1007,6 +1018,7 @@ int grid_out(cg_ctx* c, const void* disp, double* out) {
 
 template <typename T>
 int do_integrate_once(cg_ctx* c, double* grid, long long* acc, long long* rej, double* t_end) {
+  stamp_deadline(c, false);  // the time limit is for cartogram_integrate and batches
   int r = run_integration<T>(c);
   if (r) return r;
   if ((r = read_info(c))) return r;
@@ -1255,6 +1267,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   const int R = c->R_n;
   const size_t N = (size_t)c->Lx * c->Ly;
   const int nv = (int)c->n_vert;
+  stamp_deadline(c, false);  // the time limit is for cartogram_integrate and batches
   std::vector<double> V(R);
   CG_CUDA(c, cudaMemcpy(V.data(), values_in, sizeof(double) * R, cudaMemcpyDefault));
   for (int i = 0; i < R; ++i)
@@ -1582,6 +1595,7 @@ int cartogram_default_options(cg_options* o) {
   o->blur_decay = 0.5;
   o->autotune = 1;
   o->flow = CG_FLOW_DIFFUSION;
+  o->time_limit = 0.0;
   return CG_OK;
 }
 
@@ -1596,6 +1610,7 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED) return CG_EINVAL;
   if (o.use_graph < 0 || o.use_graph > 2) return CG_EINVAL;
   if (o.flow != CG_FLOW_DIFFUSION && o.flow != CG_FLOW_LINEAR) return CG_EINVAL;
+  if (!is_finite(o.time_limit) || o.time_limit < 0.0 || o.time_limit > 1e9) return CG_EINVAL;
   if (!(o.dt0 > 0) || !(o.atol > 0) || !(o.grow >= 1.0) || !(o.shrink > 0 && o.shrink < 1) ||
       !(o.cfl > 0) || !(o.rho_tol > 0) || !(o.area_tol > 0) || o.max_steps < 1 || o.max_iter < 0 ||
       !is_finite(o.dt0) || !is_finite(o.atol) || !is_finite(o.grow) || !is_finite(o.cfl) || !is_finite(o.rho_tol) ||
@@ -1909,7 +1924,7 @@ void cartogram_destroy(cg_ctx* c) {
   void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
                 c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
-                c->rho0, c->diag};
+                c->rho0, c->diag, c->deadline};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->specT && c->specT != c->spec64) cudaFree(c->specT);
@@ -1969,6 +1984,7 @@ int cartogram_batch_integrate(cg_batch* b, cg_stats* stats, int* status) {
       rc[i] = fail(c, CG_ESTATE, "no map: call cartogram_set_regions first");
       continue;
     }
+    stamp_deadline(c);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
       rc[i] = fail(c, CG_ECUDA, "stream synchronisation failed");
       continue;

@@ -120,7 +120,16 @@ struct StepParams {
   double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
   long long max_steps;
   double* sched;  // if not null: (t, h) of every accepted step, [max_steps][2]
+  // if not null: device-clock deadline of the call in ns (0: none), written at its start
+  const unsigned long long* deadline;
 };
+
+// The call's deadline has passed (read by the step controllers after every attempt).
+__device__ __forceinline__ bool deadline_passed(const StepParams& sp) {
+  if (!sp.deadline) return false;
+  const unsigned long long d = *(volatile const unsigned long long*)sp.deadline;
+  return d != 0ull && global_ns() > d;
+}
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   // non-negative doubles order like their bit patterns

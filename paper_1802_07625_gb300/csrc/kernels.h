@@ -175,6 +175,8 @@ template <typename T>
 void launch_outer_commit(OuterState* o, const IterInfo* info, const V2<T>* dres, int N, cudaStream_t s);
 void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphConditionalHandle handle, int after,
                          cudaStream_t s);
+// *deadline = device clock + limit_ns (0: no deadline), at the start of a call.
+void launch_deadline(unsigned long long* deadline, unsigned long long limit_ns, cudaStream_t s);
 // Diagnostics of the composed projection (history grids hist[0..K)): angular
 // distortion into out[4] (part: 2 * distortion_blocks doubles, max_bits: 2 words), and
 // the preimages of n points, in place.

@@ -66,4 +66,9 @@ static __global__ void outer_decide_kernel(OuterState* o, const IterInfo* info, 
   cudaGraphSetConditional(handle, o->status == kOuterRunning ? 1u : 0u);
 }
 
+// The call's deadline: the device clock now plus the limit (0: no limit).
+static __global__ void deadline_kernel(unsigned long long* deadline, unsigned long long limit_ns) {
+  *deadline = limit_ns ? global_ns() + limit_ns : 0ull;
+}
+
 }  // namespace cg

@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
     T e2 = heun_pairs_call<T>(vcur, vnew, dcur, dnew, a.Lx, a.Ly, a.log2Lx, hs, tid, nthreads);
     e2 = block_max(e2, red);
     if (threadIdx.x == 0) atomic_max_nonneg(&slot->err2, (double)e2);
+    // one clock reading for all blocks: block 0 flags the slot (bit 2) before the
+    // barrier, and every replicated controller reads the same flag after it
+    if (blockIdx.x == 0 && threadIdx.x == 0 && deadline_passed(a.sp)) atomicOr(&slot->bad, 2u);
     ok = grid_barrier(a.gb, gen);
     if (!ok) break;
     if (threadIdx.x == 0) {
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
       const double vmax_new = sqrt(__longlong_as_double((long long)ld_cg_u64(&slot->vmax2)));
       const double dev_new = __longlong_as_double((long long)ld_cg_u64(&slot->dev));
       const unsigned int bad = atomicOr(&slot->bad, 0u);
-      if (bad) {
+      if (bad & 1u) {
         status = kStepFail;
       } else if (e <= a.sp.atol) {
         par ^= 1;
@@ -204,6 +207,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
       }
       if (status == kRunning) {
         if (n_acc + n_rej >= a.sp.max_steps || !(h > a.sp.h_min)) status = kStepFail;
+        else if (bad & 2u) status = kTimeout;
         else if (vmax > 0.0 && h * vmax > a.sp.cfl) h = a.sp.cfl / vmax;
       }
       if (blockIdx.x == 0) {

@@ -129,6 +129,10 @@ void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphCondition
   outer_decide_kernel<<<1, 1, 0, s>>>(o, info, handle, after);
 }
 
+void launch_deadline(unsigned long long* deadline, unsigned long long limit_ns, cudaStream_t s) {
+  deadline_kernel<<<1, 1, 0, s>>>(deadline, limit_ns);
+}
+
 int distortion_blocks(int Lx, int Ly) { return blocks_for((long long)(Lx - 1) * (Ly - 1), 256, sm_count() * 8); }
 
 template <typename T>

@@ -44,7 +44,7 @@ def test_default_options_without_gpu():
     assert o.dt0 == 1e-2 and o.atol == 1e-2 and o.grow == 1.2 and o.shrink == 0.5
     assert o.cfl == 1.0 and o.rho_tol == 1e-4 and o.area_tol == 0.01
     assert o.max_steps == 4000 and o.max_iter == 500 and o.use_graph == 1 and o.blur_decay == 0.5 and o.autotune == 1
-    assert o.flow == P.CG_FLOW_DIFFUSION
+    assert o.flow == P.CG_FLOW_DIFFUSION and o.time_limit == 0.0
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
@@ -88,6 +88,12 @@ def test_init_rejects_bad_sizes_before_touching_the_gpu():
     with pytest.raises(P.CartogramError) as e:
         P.cartogram_init(64, 64, 1.0, o)
     assert e.value.code == P.CG_EINVAL
+    for bad in (-1.0, float("nan"), float("inf")):
+        o = P.cartogram_default_options()
+        o.time_limit = bad
+        with pytest.raises(P.CartogramError) as e:
+            P.cartogram_init(64, 64, 1.0, o)
+        assert e.value.code == P.CG_EINVAL
 
 
 def test_oracle_and_library_share_no_source():

@@ -288,3 +288,47 @@ def test_iteration_budget_reports_noconverge():
             c.integrate()
         assert e.value.code == P.CG_ENOCONVERGE
         assert c.history_length() == 2
+
+
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
+def test_time_limit_reports_timeout(use_graph):
+    # a 1 ns limit has passed by the first controller check: the integration in flight
+    # ends with CG_ETIMEOUT and maps nothing; a generous limit changes nothing
+    # (no autotuning: the first call then runs the device-side loop at once)
+    m = _small_map()
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph, time_limit=1e-9, autotune=0) as c:
+        with pytest.raises(P.CartogramError) as e:
+            c.integrate()
+        assert e.value.code == P.CG_ETIMEOUT
+        assert np.array_equal(c.vertices(), m.xy) and c.history_length() == 0
+        # entries other than cartogram_integrate do not use the limit
+        loss, gv, gb = c.iteration_gradient(m.values, 1.0, 1e-3)
+        assert np.isfinite(loss) and np.all(np.isfinite(gv))
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph) as c:
+        st0 = c.integrate()
+        xy0 = c.vertices()
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph, time_limit=100.0) as c:
+        st1 = c.integrate()
+        assert (st1.iterations, st1.steps_accepted, st1.steps_rejected) == \
+            (st0.iterations, st0.steps_accepted, st0.steps_rejected)
+        assert np.max(np.abs(c.vertices() - xy0)) < 1e-12
+
+
+def test_time_limit_in_a_batch_and_in_the_linear_flow():
+    m = _small_map()
+    limited = P.Cartogram(m.Lx, m.Ly, 1.0, precision="mixed", time_limit=1e-9, autotune=0)
+    free = P.Cartogram(m.Lx, m.Ly, 1.0, precision="mixed")
+    lin = P.Cartogram(m.Lx, m.Ly, 4.0, precision="mixed", flow="linear", time_limit=1e-9)
+    try:
+        for c in (limited, free, lin):
+            c.set_map(m)
+        with P.Batch([limited, free]) as b:
+            stats, status = b.integrate(check=False)
+        assert status == [P.CG_ETIMEOUT, P.CG_OK]
+        assert stats[1].converged and np.array_equal(limited.vertices(), m.xy)
+        with pytest.raises(P.CartogramError) as e:
+            lin.integrate()
+        assert e.value.code == P.CG_ETIMEOUT
+    finally:
+        for c in (limited, free, lin):
+            c.close()
