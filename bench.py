@@ -336,6 +336,42 @@ def run_batched(args, P, synth, flush, stream):
             c.close()
 
 
+def dense_transform_alternative(L, prof, reps=30):
+    """The transform design the passes replace, timed for comparison: the inverse transforms
+    of one attempted step as dense contractions against cosine/sine matrices (two L x L x L
+    products along x, three along y), each product timed with cuBLAS through torch.matmul
+    (TF32, and BF16 for the three-term split that FP32 accuracy needs). Not on the hot path."""
+    import torch
+    a = torch.randn(L, L, device="cuda")
+    b = torch.randn(L, L, device="cuda")
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32 in (("tf32", torch.float32, True), ("bf16", torch.bfloat16, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            x, y = a.to(dt), b.to(dt)
+            for _ in range(5):
+                torch.matmul(x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            out[name] = {"us_per_product": us, "tflops": 2.0 * L ** 3 / (us * 1e-6) / 1e12}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    passes_us = 1e3 * (prof["inverse_rows"] + prof["inverse_cols_velocity"])
+    return {"shape": "%dx%dx%d" % (L, L, L), "products_per_step": 5, **{k + "_product": v for k, v in out.items()},
+            "tf32_us_per_step": 5 * out["tf32"]["us_per_product"],
+            "split_bf16_us_per_step": 15 * out["bf16"]["us_per_product"],
+            "fft_passes_us_per_step": passes_us,
+            "note": "TF32 alone rounds to 5e-4 relative, far above the mixed path's 1e-3-cell target over a "
+                    "run; FP32 accuracy needs the three-term BF16 split (3 products each)"}
+
+
 def run_gradient(args, P, synth):
     """The differentiation workload: one outer iteration of the 512^2 clustered map (FP64
     path, blur 2) with the gradient of the area/displacement loss w.r.t. its 300 target
@@ -537,6 +573,7 @@ def run_ours(args):
 
     batched = run_batched(args, P, synth, flush, stream) if args.batch_steps > 0 else None
     gradient = run_gradient(args, P, synth) if args.grad_steps > 0 else None
+    dense = dense_transform_alternative(m.Lx, prof) if rank == 0 and not args.no_dense else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -566,6 +603,7 @@ def run_ours(args):
             "batched": batched,
             "gradient": gradient,
             "kernel_ms": prof,
+            "dense_transform_alternative": dense,
             "launch_shapes": tune,
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -598,6 +636,8 @@ def main():
     ap.add_argument("--ref-attempts", type=int, default=20,
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--no-dense", action="store_true",
+                    help="skip timing the dense-contraction alternative to the transform passes")
     ap.add_argument("--grad-steps", type=int, default=2,
                     help="timed gradients of the 512^2 differentiation workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=2,
