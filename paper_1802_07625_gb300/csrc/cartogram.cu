@@ -29,6 +29,11 @@ struct AdjWork {
   double *Crho = nullptr, *Cx = nullptr, *Cy = nullptr;       // their DCT-II [N]
   double *lam_spec = nullptr, *specp = nullptr, *R = nullptr, *dens = nullptr;  // [N]
   double2* AB = nullptr;         // inverse-pass intermediate [N]
+  // the three transposed transforms of a level run side by side (each fills a fraction of
+  // the GPU): the second and third on their own streams with their own intermediates
+  double* R2[2] = {nullptr, nullptr};  // [N] each
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   double2* Dk = nullptr;         // final displacements of the iteration being reversed [N]
   double2* flux = nullptr;       // inverse-pass side output [N]
   std::vector<double2*> v;       // fields of a segment's levels [C + 1][N]
@@ -1105,7 +1110,7 @@ void free_adj(cg_ctx* c) {
   if (!a) return;
   std::vector<void*> ps = {a->Dk, a->lam, a->L[0], a->L[1], a->a_rho, a->a_gx, a->a_gy, a->Crho, a->Cx, a->Cy,
                            a->lam_spec, a->specp, a->R, a->dens, a->AB, a->flux, a->sched, a->vals, a->dLdA,
-                           a->gw, a->dsig, a->xy1, a->gv, a->gv2};
+                           a->gw, a->dsig, a->xy1, a->gv, a->gv2, a->R2[0], a->R2[1]};
   for (auto p : a->X) ps.push_back(p);
   for (auto p : a->spec) ps.push_back(p);
   for (auto p : a->v) ps.push_back(p);
@@ -1114,6 +1119,11 @@ void free_adj(cg_ctx* c) {
   for (auto p : a->ckpt) ps.push_back(p);
   for (void* p : ps)
     if (p) cudaFree(p);
+  for (int k = 0; k < 2; ++k) {
+    if (a->side[k]) cudaStreamDestroy(a->side[k]);
+    if (a->join[k]) cudaEventDestroy(a->join[k]);
+  }
+  if (a->fork) cudaEventDestroy(a->fork);
   delete a;
   c->adj = nullptr;
 }
@@ -1130,6 +1140,12 @@ int adj_alloc(cg_ctx* c, int C) {
   double** ds[] = {&a->a_rho, &a->a_gx, &a->a_gy, &a->Crho, &a->Cx, &a->Cy, &a->lam_spec, &a->specp, &a->R, &a->dens};
   for (double** p : ds) CG_CUDA(c, cudaMalloc((void**)p, sizeof(double) * N));
   CG_CUDA(c, cudaMalloc((void**)&a->AB, sizeof(double2) * N));
+  for (int k = 0; k < 2; ++k) {
+    CG_CUDA(c, cudaMalloc((void**)&a->R2[k], sizeof(double) * N));
+    CG_CUDA(c, cudaStreamCreateWithFlags(&a->side[k], cudaStreamNonBlocking));
+    CG_CUDA(c, cudaEventCreateWithFlags(&a->join[k], cudaEventDisableTiming));
+  }
+  CG_CUDA(c, cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming));
   CG_CUDA(c, cudaMalloc((void**)&a->Dk, sizeof(double2) * N));
   CG_CUDA(c, cudaMalloc((void**)&a->flux, sizeof(double2) * N));
   a->v.assign(C + 1, nullptr);
@@ -1200,9 +1216,17 @@ void adj_level(cg_ctx* c, double* L, const double2* v, const double* rho, double
   cg::launch_node_adjoint(L, v, rho, a->a_rho, a->a_gx, a->a_gy, c->Lx, c->Ly, s);
   double* ins[3] = {a->a_rho, a->a_gx, a->a_gy};
   double* outs[3] = {a->Crho, a->Cx, a->Cy};
+  double* mid[3] = {a->R, a->R2[0], a->R2[1]};
+  cudaStream_t on[3] = {s, a->side[0], a->side[1]};
+  cudaEventRecord(a->fork, s);
+  for (int k = 1; k < 3; ++k) cudaStreamWaitEvent(on[k], a->fork, 0);
   for (int k = 0; k < 3; ++k)
-    cg::launch_fwd<double>(c->log2Lx, c->log2Ly, ins[k], a->R, outs[k], nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
-                           nullptr, nullptr, s);
+    cg::launch_fwd<double>(c->log2Lx, c->log2Ly, ins[k], mid[k], outs[k], nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                           nullptr, nullptr, on[k]);
+  for (int k = 1; k < 3; ++k) {
+    cudaEventRecord(a->join[k - 1], on[k]);
+    cudaStreamWaitEvent(s, a->join[k - 1], 0);
+  }
   cg::launch_spec_accumulate(a->Crho, a->Cx, a->Cy, a->lam_spec, tau, c->Lx, c->Ly, s);
   cudaMemsetAsync(L, 0, sizeof(double) * 2 * (size_t)c->Lx * c->Ly, s);
 }
