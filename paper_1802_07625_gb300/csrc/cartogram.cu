@@ -32,6 +32,7 @@ struct AdjWork {
   // the three transposed transforms of a level run side by side (each fills a fraction of
   // the GPU): the second and third on their own streams with their own intermediates
   double* R2[2] = {nullptr, nullptr};  // [N] each
+  double2* AB2[2] = {nullptr, nullptr};  // inverse-pass intermediates of the side streams [N] each
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   double2* Dk = nullptr;         // final displacements of the iteration being reversed [N]
@@ -1110,7 +1111,7 @@ void free_adj(cg_ctx* c) {
   if (!a) return;
   std::vector<void*> ps = {a->Dk, a->lam, a->L[0], a->L[1], a->a_rho, a->a_gx, a->a_gy, a->Crho, a->Cx, a->Cy,
                            a->lam_spec, a->specp, a->R, a->dens, a->AB, a->flux, a->sched, a->vals, a->dLdA,
-                           a->gw, a->dsig, a->xy1, a->gv, a->gv2, a->R2[0], a->R2[1]};
+                           a->gw, a->dsig, a->xy1, a->gv, a->gv2, a->R2[0], a->R2[1], a->AB2[0], a->AB2[1]};
   for (auto p : a->X) ps.push_back(p);
   for (auto p : a->spec) ps.push_back(p);
   for (auto p : a->v) ps.push_back(p);
@@ -1142,6 +1143,7 @@ int adj_alloc(cg_ctx* c, int C) {
   CG_CUDA(c, cudaMalloc((void**)&a->AB, sizeof(double2) * N));
   for (int k = 0; k < 2; ++k) {
     CG_CUDA(c, cudaMalloc((void**)&a->R2[k], sizeof(double) * N));
+    CG_CUDA(c, cudaMalloc((void**)&a->AB2[k], sizeof(double2) * N));
     CG_CUDA(c, cudaStreamCreateWithFlags(&a->side[k], cudaStreamNonBlocking));
     CG_CUDA(c, cudaEventCreateWithFlags(&a->join[k], cudaEventDisableTiming));
   }
@@ -1187,12 +1189,33 @@ int adj_alloc_iters(cg_ctx* c, int K) {
 }
 
 // Field v (and density) of the FP64 path at time tau, from the iteration's spectrum.
-void adj_field(cg_ctx* c, double tau, double2* v, double* rho) {
+void adj_field(cg_ctx* c, double tau, double2* v, double* rho, double2* AB = nullptr, cudaStream_t s = nullptr) {
   AdjWork* a = c->adj;
-  cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, c->spec64, a->AB, (const double2*)c->Wx,
-                              (const double2*)c->Ex, c->st, cg::kModeFixed, tau, 0, 0, 0u, c->stream);
-  cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, a->AB, v, nullptr, rho, (const double2*)c->Wy,
-                              (const double2*)c->Ey, c->st, cg::kModeFixed, c->stream);
+  if (!AB) AB = a->AB;
+  if (!s) s = c->stream;
+  cg::launch_inv_rows<double>(c->log2Lx, c->Ly, c->tune.rows, c->spec64, AB, (const double2*)c->Wx,
+                              (const double2*)c->Ex, c->st, cg::kModeFixed, tau, 0, 0, 0u, s);
+  cg::launch_inv_cols<double>(c->log2Ly, c->Lx, c->tune.cols, AB, v, nullptr, rho, (const double2*)c->Wy,
+                              (const double2*)c->Ey, c->st, cg::kModeFixed, s);
+}
+
+// The fields of levels n0 .. n0 + m (times from the schedule) into v[0 .. m], rho[0 .. m]:
+// they depend on the spectrum alone, so they run on three streams side by side (each FP64
+// transform pair fills a fraction of the GPU at these sizes).
+double adj_tau(const std::vector<double>& sch, int n);
+void adj_fields(cg_ctx* c, const std::vector<double>& sch, int n0, int m) {
+  AdjWork* a = c->adj;
+  cudaStream_t s = c->stream;
+  cudaEventRecord(a->fork, s);
+  for (int q = 0; q < 2; ++q) cudaStreamWaitEvent(a->side[q], a->fork, 0);
+  for (int k = 0; k <= m; ++k) {
+    const int q = k % 3;
+    adj_field(c, adj_tau(sch, n0 + k), a->v[k], a->rho[k], q ? a->AB2[q - 1] : a->AB, q ? a->side[q - 1] : s);
+  }
+  for (int q = 0; q < 2; ++q) {
+    cudaEventRecord(a->join[q], a->side[q]);
+    cudaStreamWaitEvent(s, a->join[q], 0);
+  }
 }
 
 // One predictor-corrector step of all points with the fixed step h (the step kernel).
@@ -1240,10 +1263,24 @@ double2* adj_replay(cg_ctx* c, const std::vector<double>& sch, int C, bool ck) {
   const int NS = (int)sch.size() / 2;
   if (ck) cudaMemsetAsync(a->ckpt[0], 0, sizeof(double2) * N, s);
   cudaMemsetAsync(a->D[0], 0, sizeof(double2) * N, s);
-  int cur = 0;  // v[cur] holds the field of level n
-  adj_field(c, 0.0, a->v[0], a->rho[0]);
   double2* din = a->D[0];
   double2* dout = a->D[1];
+  if (C >= 4) {
+    // chunks of C steps: the chunk's C + 1 fields side by side, then its steps in order
+    for (int n0 = 0; n0 < NS; n0 += C) {
+      const int n1 = std::min(n0 + C, NS);
+      adj_fields(c, sch, n0, n1 - n0);
+      for (int n = n0; n < n1; ++n) {
+        adj_step(c, a->v[n - n0], a->v[n - n0 + 1], din, dout, sch[2 * n + 1]);
+        std::swap(din, dout);
+        if (ck && (n + 1) % C == 0 && (n + 1) / C < (int)a->ckpt.size())
+          cudaMemcpyAsync(a->ckpt[(n + 1) / C], din, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
+      }
+    }
+    return din;
+  }
+  int cur = 0;  // v[cur] holds the field of level n
+  adj_field(c, 0.0, a->v[0], a->rho[0]);
   for (int n = 0; n < NS; ++n) {
     adj_field(c, adj_tau(sch, n + 1), a->v[1 - cur], a->rho[1 - cur]);
     adj_step(c, a->v[cur], a->v[1 - cur], din, dout, sch[2 * n + 1]);
@@ -1271,7 +1308,7 @@ void adj_reverse(cg_ctx* c, const std::vector<double>& sch, int C) {
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int n0 = sg * C, n1 = std::min(n0 + C, NS);
     cudaMemcpyAsync(a->D[0], a->ckpt[sg], sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
-    for (int k = 0; k <= n1 - n0; ++k) adj_field(c, adj_tau(sch, n0 + k), a->v[k], a->rho[k]);
+    adj_fields(c, sch, n0, n1 - n0);
     for (int k = 0; k < n1 - n0 - 1; ++k) adj_step(c, a->v[k], a->v[k + 1], a->D[k], a->D[k + 1], sch[2 * (n0 + k) + 1]);
     for (int n = n1 - 1; n >= n0; --n) {
       const int k = n - n0;
