@@ -145,7 +145,9 @@ int cartogram_set_stream(cg_ctx* ctx, void* cuda_stream);
  *                                  are outer boundaries, clockwise rings are holes, and
  *                                  a region's area is the signed sum over its rings.
  * Regions must not overlap and each must have positive area. Resets the iteration
- * history. Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
+ * history. A map with the same ring_offsets and ring_region as the current one (new values
+ * or moved vertices, e.g. the frames of an animation) reuses the context's device buffers
+ * and captured graphs. Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
 int cartogram_set_regions(cg_ctx* ctx, int n_regions, const double* target_values,
                           int64_t n_rings, const int64_t* ring_offsets,
                           const int32_t* ring_region, const double* xy);

@@ -104,6 +104,8 @@ struct cg_ctx {
   double2* xy = nullptr;
   double2* xy0 = nullptr;  // vertices as given to set_regions
   double* area_sums = nullptr;  // (sum A, sum V) of the last area computation
+  std::vector<long long> map_off;  // host copies of the map's ring offsets and ring regions:
+  std::vector<int> map_reg;        // a new map with the same rings reuses every buffer
   double* area = nullptr;
   double* err_d = nullptr;
   double* w = nullptr;
@@ -1558,6 +1560,8 @@ void free_regions(cg_ctx* c) {
   c->values = nullptr; c->ring_off = nullptr; c->reg_off = nullptr; c->reg_rings = nullptr;
   c->next = nullptr; c->vreg = nullptr; c->xy = nullptr; c->xy0 = nullptr;
   c->area_sums = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
+  c->map_off.clear();
+  c->map_reg.clear();
   c->have_regions = false;
 }
 
@@ -1707,6 +1711,20 @@ int cartogram_set_stream(cg_ctx* c, void* stream) {
   return CG_OK;
 }
 
+// The areas of a newly set map; every region needs a positive one (else the map is dropped).
+int check_areas(cg_ctx* c) {
+  int r;
+  if ((r = run_areas(c)) || (r = read_info(c))) return r;
+  std::vector<double> area(c->R_n);
+  CG_CUDA(c, cudaMemcpy(area.data(), c->area, sizeof(double) * c->R_n, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < c->R_n; ++k)
+    if (!(area[k] > 0.0)) {
+      free_regions(c);
+      return fail(c, CG_EINVAL, "region %d has non-positive area %g", k, area[k]);
+    }
+  return CG_OK;
+}
+
 int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values, int64_t n_rings,
                           const int64_t* ring_offsets, const int32_t* ring_region,
                           const double* xy) {
@@ -1731,12 +1749,34 @@ int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values,
   }
   const long long nv = off[n_rings];
   if (nv >= (1LL << 31)) return fail(c, CG_EINVAL, "too many vertices");
-  std::vector<double> pts(2 * (size_t)nv);
-  CG_CUDA(c, cudaMemcpy(pts.data(), xy, sizeof(double) * 2 * nv, cudaMemcpyDefault));
+  // the vertices are validated where they are when that is host memory, else from a copy
+  std::vector<double> pts;
+  const double* hxy = xy;
+  {
+    cudaPointerAttributes pa;
+    const bool dev = cudaPointerGetAttributes(&pa, xy) == cudaSuccess &&
+                     (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (dev) {
+      pts.resize(2 * (size_t)nv);
+      CG_CUDA(c, cudaMemcpy(pts.data(), xy, sizeof(double) * 2 * nv, cudaMemcpyDefault));
+      hxy = pts.data();
+    }
+  }
   for (long long k = 0; k < nv; ++k) {
-    const double x = pts[2 * k], y = pts[2 * k + 1];
+    const double x = hxy[2 * k], y = hxy[2 * k + 1];
     if (!is_finite(x) || !is_finite(y) || x < 0.0 || x > c->Lx || y < 0.0 || y > c->Ly)
       return fail(c, CG_EINVAL, "vertex %lld (%g, %g) is outside the box [0,%d]x[0,%d]", k, x, y, c->Lx, c->Ly);
+  }
+  if (c->have_regions && n_regions == c->R_n && off == c->map_off && reg == c->map_reg) {
+    // the same rings: keep every buffer (and the graphs and work spaces that hold them)
+    c->scheds.clear();
+    CG_CUDA(c, cudaMemcpy(c->values, vals.data(), sizeof(double) * n_regions, cudaMemcpyHostToDevice));
+    CG_CUDA(c, cudaMemcpy(c->xy, xy, sizeof(double2) * nv, cudaMemcpyDefault));
+    CG_CUDA(c, cudaMemcpy(c->xy0, c->xy, sizeof(double2) * nv, cudaMemcpyDeviceToDevice));
+    c->hist_len = 0;
+    c->have_spectrum = false;
+    return check_areas(c);
   }
   // per-vertex successor and region, region -> rings index
   std::vector<int> next(nv), vreg(nv), reg_off(n_regions + 1, 0), reg_rings(n_rings);
@@ -1780,21 +1820,14 @@ int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values,
     CG_CUDA(c, cudaMalloc((void**)&c->prev, sizeof(int) * nv));
     CG_CUDA(c, cudaMemcpy(c->prev, prev.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
   }
-  CG_CUDA(c, cudaMemcpy(c->xy, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
-  CG_CUDA(c, cudaMemcpy(c->xy0, pts.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(c->xy, xy, sizeof(double2) * nv, cudaMemcpyDefault));
+  CG_CUDA(c, cudaMemcpy(c->xy0, c->xy, sizeof(double2) * nv, cudaMemcpyDeviceToDevice));
   c->have_regions = true;
   c->hist_len = 0;
   c->have_spectrum = false;
-  // every region needs a positive area
-  if ((r = run_areas(c)) || (r = read_info(c))) return r;
-  std::vector<double> area(n_regions);
-  CG_CUDA(c, cudaMemcpy(area.data(), c->area, sizeof(double) * n_regions, cudaMemcpyDeviceToHost));
-  for (int k = 0; k < n_regions; ++k)
-    if (!(area[k] > 0.0)) {
-      free_regions(c);
-      return fail(c, CG_EINVAL, "region %d has non-positive area %g", k, area[k]);
-    }
-  return CG_OK;
+  c->map_off = std::move(off);
+  c->map_reg = std::move(reg);
+  return check_areas(c);
 }
 
 int cartogram_integrate(cg_ctx* c, cg_stats* stats) {

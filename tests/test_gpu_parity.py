@@ -332,3 +332,35 @@ def test_time_limit_in_a_batch_and_in_the_linear_flow():
     finally:
         for c in (limited, free, lin):
             c.close()
+
+
+@pytest.mark.parametrize("use_graph", [1, 2])
+def test_a_map_with_the_same_rings_reuses_the_context(use_graph):
+    # setting a map whose rings equal the current ones keeps the device buffers and the
+    # captured graphs; the results must equal a fresh context's
+    import dataclasses
+    m = _small_map()
+    rng = np.random.default_rng(3)
+    m2 = dataclasses.replace(m, values=m.values * rng.lognormal(0.0, 0.5, m.n_regions))
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph) as c:
+        st1 = c.integrate()
+        xy1 = c.vertices()
+        c.set_map(m2)
+        assert c.history_length() == 0 and np.array_equal(c.vertices(), m2.xy)
+        st2 = c.integrate()
+        xy2 = c.vertices()
+        c.set_map(m)
+        st3 = c.integrate()
+        assert (st3.iterations, st3.steps_accepted, st3.steps_rejected) == \
+            (st1.iterations, st1.steps_accepted, st1.steps_rejected)
+        assert np.max(np.abs(c.vertices() - xy1)) < 1e-10
+        # other rings: a new map from scratch
+        m3 = _small_map(L=64, n=12)
+        c.set_map(m3)
+        st4 = c.integrate()
+        assert st4.converged
+    with _ctx(m2, 1.0, "fp64", use_graph=use_graph) as c:
+        st = c.integrate()
+        assert (st.iterations, st.steps_accepted, st.steps_rejected) == \
+            (st2.iterations, st2.steps_accepted, st2.steps_rejected)
+        assert np.max(np.abs(c.vertices() - xy2)) < 1e-10
