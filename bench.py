@@ -652,9 +652,16 @@ def main():
                          "(profilers cannot capture kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="run only the warm-up and timed cartograms (for profiler captures)")
+    ap.add_argument("--grad-only", action="store_true",
+                    help="run only the differentiation workload's leg and print it (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.grad_only:
+        import paper_1802_07625_gb300 as P
+        from paper_1802_07625_gb300 import synth
+        print(json.dumps({"gradient": run_gradient(args, P, synth)}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -167,20 +167,35 @@ __global__ void node_adjoint_kernel(const double* __restrict__ L, const double2*
 // from the DCT-II outputs of the three adjoint fields (each holding the weights
 // (1 + (m>0))(1 + (n>0)), which are divided out). f is the damping of the inverse
 // pass: exp(-pi^2 tau m^2/Lx^2) exp(-pi^2 tau n^2/Ly^2).
+// The damping and the wavenumber factors are separable: a block evaluates those of the
+// columns once into shared memory (Lx <= 1024) and one of each per row, so a coefficient
+// costs no exponential and no division (GB300's FP64 rate makes both expensive); the
+// weights' divisions are by powers of two, so their products are the same numbers.
 __global__ void spec_accumulate_kernel(const double* __restrict__ Crho, const double* __restrict__ Cx,
                                        const double* __restrict__ Cy, double* lam_spec, double tau, int Lx,
                                        int Ly) {
-  const int N = Lx * Ly;
+  __shared__ double fxm[1024], gxm[1024];
   const double kx = kPi * kPi * tau / ((double)Lx * Lx), ky = kPi * kPi * tau / ((double)Ly * Ly);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-    const int m = p % Lx, n = p / Lx;
-    if (m == 0 && n == 0) continue;
-    const double wn = n == 0 ? 1.0 : 2.0, wm = m == 0 ? 1.0 : 2.0;
-    double s = Crho[p] / (wm * wn);
-    if (m > 0) s += (-kPi * m / Lx) * Cx[(size_t)n * Lx + (Lx - m)] / (2.0 * wn);
-    if (n > 0) s += (-kPi * n / Ly) * Cy[(size_t)(Ly - n) * Lx + m] / (wm * 2.0);
-    const double f = (exp(-kx * m * m) / Lx) * (exp(-ky * n * n) / Ly);
-    lam_spec[p] += f * s;
+  for (int m = threadIdx.x; m < Lx; m += blockDim.x) {
+    fxm[m] = exp(-kx * m * m) / Lx;
+    gxm[m] = -kPi * m / Lx;
+  }
+  __syncthreads();
+  for (int n = blockIdx.x; n < Ly; n += gridDim.x) {
+    const double fyn = exp(-ky * n * n) / Ly, gyn = -kPi * n / Ly;
+    const double wn = n == 0 ? 1.0 : 2.0;
+    const double* crow = Crho + (size_t)n * Lx;
+    const double* xrow = Cx + (size_t)n * Lx;
+    const double* yrow = Cy + (size_t)(Ly - n) * Lx;  // read only for n > 0
+    double* out = lam_spec + (size_t)n * Lx;
+    for (int m = threadIdx.x; m < Lx; m += blockDim.x) {
+      if (m == 0 && n == 0) continue;
+      const double wm = m == 0 ? 1.0 : 2.0;
+      double s = crow[m] * (1.0 / (wm * wn));
+      if (m > 0) s += gxm[m] * xrow[Lx - m] * (1.0 / (2.0 * wn));
+      if (n > 0) s += gyn * yrow[m] * (1.0 / (wm * 2.0));
+      out[m] += (fxm[m] * fyn) * s;
+    }
   }
 }
 

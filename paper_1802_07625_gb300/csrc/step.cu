@@ -169,8 +169,7 @@ void launch_node_adjoint(const double* L, const double2* v, const double* rho, d
 
 void launch_spec_accumulate(const double* Crho, const double* Cx, const double* Cy, double* lam_spec, double tau,
                             int Lx, int Ly, cudaStream_t s) {
-  spec_accumulate_kernel<<<blocks_for((long long)Lx * Ly, 256, 4096), 256, 0, s>>>(Crho, Cx, Cy, lam_spec, tau, Lx,
-                                                                                  Ly);
+  spec_accumulate_kernel<<<std::min(Ly, sm_count() * 4), 256, 0, s>>>(Crho, Cx, Cy, lam_spec, tau, Lx, Ly);
 }
 
 void launch_spec_tail(const double* lam_spec, const double* spec, const double* bx, const double* by, double sigma,
