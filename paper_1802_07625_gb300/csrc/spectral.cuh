@@ -27,6 +27,20 @@ namespace cg {
 __device__ __forceinline__ float texp(float x) { return expf(x); }
 __device__ __forceinline__ double texp(double x) { return exp(x); }
 
+// Two adjacent outputs with one store where the pair is one aligned vector (the callers'
+// pairs start at even indices of arrays that start at 16-byte boundaries).
+__device__ __forceinline__ void st_two(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_two(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+__device__ __forceinline__ void st_two(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st_two(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
 // Output index i of a cosine sum -> index of the complex DFT output that holds it.
 __device__ __forceinline__ int dct3_src(int i, int N) { return (i & 1) ? (N - 1 - (i >> 1)) : (i >> 1); }
 
@@ -112,12 +126,21 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   }
   __syncthreads();
   block_fft<T, LOG2N, true>(buf, S, W);
-  // S is a power of two: a runtime integer division here costs as much as the FFT
+  // S is a power of two: a runtime integer division here costs as much as the FFT. Two
+  // adjacent rows per task (one output slot, one vector store)
   const int ls = __ffs(S) - 1;
-  for (int task = threadIdx.x; task < S * N; task += blockDim.x) {
-    const int i = task >> ls, s = task & (S - 1);
-    const C u = buf[s * F::SSTRIDE + F::out_slot(dct3_src(i, N))];
-    ABt[(size_t)i * Ly + n0 + s] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
+  if (S >= 2) {
+    for (int task = threadIdx.x; task < (S * N) >> 1; task += blockDim.x) {
+      const int i = task >> (ls - 1), s = 2 * (task & ((S >> 1) - 1));
+      const int slot = F::out_slot(dct3_src(i, N));
+      const C ua = buf[s * F::SSTRIDE + slot], ub = buf[(s + 1) * F::SSTRIDE + slot];
+      st_two(ABt + (size_t)i * Ly + n0 + s, mk2<T>(ua.x, (i & 1) ? -ua.y : ua.y), mk2<T>(ub.x, (i & 1) ? -ub.y : ub.y));
+    }
+  } else {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const C u = buf[F::out_slot(dct3_src(i, N))];
+      ABt[(size_t)i * Ly + n0] = mk2<T>(u.x, (i & 1) ? -u.y : u.y);
+    }
   }
   __syncthreads();
   return true;
@@ -241,24 +264,33 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
 
   T dev = T(0), v2max = T(0);
   bool bad = false;
-  const int lw = __ffs(Wc) - 1;  // Wc is a power of two (no runtime integer division)
-  for (int task = threadIdx.x; task < N * Wc; task += blockDim.x) {
-    const int j = task >> lw, cc = task & (Wc - 1);
+  // a column pair per task (Wc is an even power of two; no runtime integer division): the
+  // two columns share the output slot and the d_x rho signal (real and imaginary parts)
+  const int lp = __ffs(Wc) - 2;
+  for (int task = threadIdx.x; task < (N * Wc) >> 1; task += blockDim.x) {
+    const int j = task >> lp, cp = task & ((Wc >> 1) - 1);
     const int slot = F::out_slot(dct3_src(j, N));
-    const C u1 = buf[cc * F::SSTRIDE + slot];
-    const C u2 = buf[(Wc + (cc >> 1)) * F::SSTRIDE + slot];
-    const T rp = u1.x;
-    const T gy = (j & 1) ? -u1.y : u1.y;
-    const T gx = (cc & 1) ? u2.y : u2.x;
-    const T rho = T(1) + rp;
-    if (!raw) bad |= !(rho > T(0));
-    const T inv = raw ? T(1) : T(1) / rho;
-    const T vx = -gx * inv, vy = -gy * inv;
-    const size_t o = (size_t)j * Lx + c0 + cc;
-    out[o] = mk2<T>(vx, vy);
-    if (rho_out) rho_out[o] = raw ? rp : rho;  // flux mode: the plain cosine sum
-    dev = max(dev, fabs(rp));
-    v2max = max(v2max, vx * vx + vy * vy);
+    const C u2 = buf[(Wc + cp) * F::SSTRIDE + slot];
+    V2<T> vv[2];
+    T rr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const C u1 = buf[(2 * cp + h) * F::SSTRIDE + slot];
+      const T rp = u1.x;
+      const T gy = (j & 1) ? -u1.y : u1.y;
+      const T gx = h ? u2.y : u2.x;
+      const T rho = T(1) + rp;
+      if (!raw) bad |= !(rho > T(0));
+      const T inv = raw ? T(1) : T(1) / rho;
+      const T vx = -gx * inv, vy = -gy * inv;
+      vv[h] = mk2<T>(vx, vy);
+      rr[h] = raw ? rp : rho;  // flux mode: the plain cosine sum
+      dev = max(dev, fabs(rp));
+      v2max = max(v2max, vx * vx + vy * vy);
+    }
+    const size_t o = (size_t)j * Lx + c0 + 2 * cp;
+    st_two(out + o, vv[0], vv[1]);
+    if (rho_out) st_two(rho_out + o, rr[0], rr[1]);
   }
   res.bad = __syncthreads_or(bad);
   res.dev = block_max(dev, red);
