@@ -227,6 +227,14 @@ int cartogram_get_vertices(cg_ctx* ctx, double* xy_out);
  * on the device (no host transfer). Errors: CG_ESTATE (no map). */
 int cartogram_reset(cg_ctx* ctx);
 
+/* New target values for the current map (the frames of an animation, replicates of the
+ * data; main text, problem statement: areas proportional to the values): restores the
+ * vertices given to the last cartogram_set_regions, clears the history and recomputes the
+ * area errors, keeping every device buffer and captured graph.
+ *   target_values [n_regions of the map]  > 0 and finite; host or device pointer
+ * Errors: CG_EINVAL (NULL or invalid values, nothing changed), CG_ESTATE (no map), CG_ECUDA. */
+int cartogram_set_values(cg_ctx* ctx, const double* target_values);
+
 /* Number of outer iterations in the history (projected grids stored). */
 int cartogram_history_length(const cg_ctx* ctx);
 

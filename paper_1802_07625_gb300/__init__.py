@@ -23,7 +23,7 @@ __all__ = [
     "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion",
     "cartogram_iteration_gradient", "cartogram_last_error",
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         "cartogram_history_length": (i, [_P]),
         "cartogram_fold_count": (i, [_P, i, ctypes.POINTER(ll), ctypes.POINTER(d)]),
         "cartogram_reset": (i, [_P]),
+        "cartogram_set_values": (i, [_P, _P]),
         "cartogram_autotune": (i, [_P, i, _P, _P]),
         "cartogram_profile": (i, [_P, i, _P]),
         "cartogram_get_grid": (i, [_P, i, _P]),
@@ -224,6 +225,11 @@ def cartogram_get_vertices(ctx, out):
 
 def cartogram_reset(ctx) -> None:
     _check(ctx, load().cartogram_reset(ctx))
+
+
+def cartogram_set_values(ctx, target_values) -> None:
+    pv, _ = _ptr(target_values, np.float64)
+    _check(ctx, load().cartogram_set_values(ctx, pv))
 
 
 PROFILE_CLASSES = ("inverse_rows", "inverse_cols_velocity", "heun_step", "rasterise", "forward",
@@ -457,6 +463,9 @@ class Cartogram:
 
     def vertices(self):
         return cartogram_get_vertices(self.ctx, np.empty((self._map.n_vertices, 2)))
+
+    def set_values(self, values):
+        cartogram_set_values(self.ctx, values)
 
     def reset(self):
         cartogram_reset(self.ctx)

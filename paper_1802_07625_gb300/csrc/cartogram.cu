@@ -1869,6 +1869,24 @@ int cartogram_reset(cg_ctx* c) {
   return CG_OK;
 }
 
+int cartogram_set_values(cg_ctx* c, const double* target_values) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!target_values) return fail(c, CG_EINVAL, "NULL values");
+  std::vector<double> vals(c->R_n);
+  CG_CUDA(c, cudaMemcpy(vals.data(), target_values, sizeof(double) * c->R_n, cudaMemcpyDefault));
+  for (int k = 0; k < c->R_n; ++k)
+    if (!is_finite(vals[k]) || !(vals[k] > 0.0)) return fail(c, CG_EINVAL, "target value %d is not positive and finite", k);
+  CG_CUDA(c, cudaMemcpyAsync(c->values, vals.data(), sizeof(double) * c->R_n, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(c, cudaMemcpyAsync(c->xy, c->xy0, sizeof(double2) * c->n_vert, cudaMemcpyDeviceToDevice, c->stream));
+  c->hist_len = 0;
+  c->have_spectrum = false;
+  c->scheds.clear();
+  if ((r = run_areas(c))) return r;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));  // vals is released on return
+  return CG_OK;
+}
+
 int cartogram_profile(cg_ctx* c, int reps, double* ms_out) {
   int r = check_ctx(c, true);
   if (r) return r;

@@ -364,3 +364,26 @@ def test_a_map_with_the_same_rings_reuses_the_context(use_graph):
         assert (st.iterations, st.steps_accepted, st.steps_rejected) == \
             (st2.iterations, st2.steps_accepted, st2.steps_rejected)
         assert np.max(np.abs(c.vertices() - xy2)) < 1e-10
+
+
+def test_set_values_restarts_from_the_original_map(orc):
+    import dataclasses
+    m = _small_map()
+    rng = np.random.default_rng(4)
+    v2 = m.values * rng.lognormal(0.0, 0.5, m.n_regions)
+    with _ctx(m, 1.0, "fp64") as c:
+        c.integrate()
+        c.set_values(v2)
+        assert c.history_length() == 0 and np.array_equal(c.vertices(), m.xy)
+        A = orc.region_areas(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+        assert np.max(np.abs(c.area_errors() - (A / (v2 * A.sum() / v2.sum()) - 1.0))) < 1e-13
+        with pytest.raises(P.CartogramError) as e:
+            c.set_values(-v2)
+        assert e.value.code == P.CG_EINVAL
+        st = c.integrate()
+        xy = c.vertices()
+    with _ctx(dataclasses.replace(m, values=v2), 1.0, "fp64") as c:
+        st2 = c.integrate()
+        assert (st.iterations, st.steps_accepted, st.steps_rejected) == \
+            (st2.iterations, st2.steps_accepted, st2.steps_rejected)
+        assert np.max(np.abs(xy - c.vertices())) < 1e-10
