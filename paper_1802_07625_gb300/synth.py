@@ -240,6 +240,21 @@ def rectangle_ring(x0, y0, x1, y1, spacing):
     return np.array(pts, dtype=np.float64)
 
 
+def blocks_map(Lx: int = 128, Ly: int = 64, nx: int = 4, ny: int = 2, seed: int = 5,
+               spacing: float = 0.5) -> RegionMap:
+    """An nx x ny arrangement of rectangular regions filling the inner half of an Lx x Ly box
+    (a non-square grid), with seeded lognormal(0, 0.7) values; neighbouring rectangles carry
+    bit-identical shared vertices."""
+    x0, y0, w, h = Lx / 4.0, Ly / 4.0, Lx / 2.0 / nx, Ly / 2.0 / ny
+    rings = [rectangle_ring(x0 + i * w, y0 + j * h, x0 + (i + 1) * w, y0 + (j + 1) * h, spacing)
+             for j in range(ny) for i in range(nx)]
+    offsets = np.cumsum([0] + [r.shape[0] for r in rings]).astype(np.int64)
+    g = Xoshiro256ss(180207625 + seed)
+    values = np.array([g.lognormal(0.0, 0.7) for _ in rings])
+    return RegionMap(Lx, Ly, values, offsets, np.arange(len(rings), dtype=np.int32),
+                     np.concatenate(rings, axis=0), meta={"name": "blocks", "Lx": Lx, "Ly": Ly})
+
+
 def holes_map(L: int = 64, spacing: float = 0.5) -> RegionMap:
     """Four regions on an L x L grid with multi-ring structure: region 0 is a square with
     a square hole (a clockwise ring), region 2 fills the hole, region 1 is two islands

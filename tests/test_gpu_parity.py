@@ -387,3 +387,20 @@ def test_set_values_restarts_from_the_original_map(orc):
         assert (st.iterations, st.steps_accepted, st.steps_rejected) == \
             (st2.iterations, st2.steps_accepted, st2.steps_rejected)
         assert np.max(np.abs(xy - c.vertices())) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_non_square_cartogram_matches_oracle(orc, precision):
+    # a 4 x 2 arrangement of rectangles on a 128 x 64 grid: every stage with Lx != Ly
+    m = synth.blocks_map(128, 64)
+    with _ctx(m, 1.0, precision) as c:
+        st = c.integrate()
+        xy = c.vertices()
+        err = c.area_errors()
+    r = orc.cartogram(m, blur=1.0)
+    assert r.converged and st.converged and st.iterations == r.iterations
+    tol = FP64_POS_TOL if precision == "fp64" else MIXED_POS_TOL
+    assert np.max(np.abs(xy - r.xy)) < tol
+    assert np.max(np.abs(err - r.err)) < AREA_TOL
+    if precision == "fp64":
+        assert st.steps_accepted == r.steps_accepted and st.steps_rejected == r.steps_rejected

@@ -56,3 +56,11 @@ def test_workload_sizes_match_their_recipes():
     m3 = synth.make_workload("powerlaw3000_1024")
     assert m3.n_regions == 3000 and 450_000 < m3.n_vertices < 700_000
     assert m3.values.min() >= 1.0
+
+
+def test_blocks_map_is_seeded_and_tiles_the_inner_half():
+    a, b = synth.blocks_map(128, 64), synth.blocks_map(128, 64)
+    assert np.array_equal(a.values, b.values) and np.array_equal(a.xy, b.xy)
+    assert a.n_regions == 8 and np.all(a.values > 0)
+    assert a.xy[:, 0].min() == 32.0 and a.xy[:, 0].max() == 96.0
+    assert a.xy[:, 1].min() == 16.0 and a.xy[:, 1].max() == 48.0
