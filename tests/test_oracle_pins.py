@@ -705,3 +705,67 @@ def test_multi_iteration_oracle_loss_reduces_to_the_reference(orc):
     L_2 = adj.cartogram_loss(orc, m, m.values, blur, 0.5, sch, 0.0)
     L_1 = adj.cartogram_loss(orc, m, m.values, blur, 0.5, sch[:1], 0.0)
     assert L_2 < L_1
+
+
+# ---- polygon-level measures (SI section 4) ------------------------------------------
+
+
+def _rot(xy, beta, centre=(5.0, 4.0)):
+    c = np.asarray(centre)
+    R = np.array([[math.cos(beta), -math.sin(beta)], [math.sin(beta), math.cos(beta)]])
+    return (xy - c) @ R.T + c
+
+
+def test_centroids_of_a_rectangle_and_a_square_with_a_hole():
+    from oracle import polygon as pg
+    outer = synth.rectangle_ring(0, 0, 4, 4, 1.0)
+    hole = synth.rectangle_ring(0, 0, 2, 2, 1.0)[::-1]
+    rect = synth.rectangle_ring(5, 1, 9, 3, 0.5)
+    xy = np.concatenate([outer, hole, rect])
+    off = np.cumsum([0, len(outer), len(hole), len(rect)])
+    c = pg.region_centroids(2, off, np.array([0, 0, 1]), xy)
+    # [0,4]^2 minus [0,2]^2: (16 (2,2) - 4 (1,1)) / 12 = (7/3, 7/3)
+    assert np.allclose(c, [[7 / 3, 7 / 3], [7.0, 2.0]], atol=1e-14)
+
+
+def test_relative_position_error_of_similarity_maps():
+    from oracle import polygon as pg
+    m = synth.make_workload("voronoi16_64", L=32, n=8)
+    c = pg.region_centroids(m.n_regions, m.ring_offsets, m.ring_region, m.xy)
+    assert pg.relative_position_error(c, c) == 0.0
+    # translations and uniform scalings keep every direction: theta = 0
+    assert pg.relative_position_error(c, 0.5 * c + 3.0) < 1e-15
+    # a rotation by beta turns every connecting line by beta: theta = beta / pi
+    for beta in (0.1, 1.0, 2.5):
+        d = pg.region_centroids(m.n_regions, m.ring_offsets, m.ring_region, _rot(m.xy, beta))
+        assert abs(pg.relative_position_error(c, d) - beta / math.pi) < 1e-12
+
+
+def test_aspect_ratio_of_rectangles_and_a_hexagon():
+    from oracle import polygon as pg
+    rect = synth.rectangle_ring(1, 1, 4, 2, 0.25)  # 3 x 1
+    for beta in (0.0, 0.3, 1.2):
+        hull = pg.convex_hull(_rot(rect, beta))
+        area, alpha = pg.min_area_rectangle(hull)
+        assert abs(area - 3.0) < 1e-12 and abs(alpha - 3.0) < 1e-12
+    hexagon = np.array([[math.cos(k * math.pi / 3), math.sin(k * math.pi / 3)] for k in range(6)])
+    # every orientation along a side gives the 2 x sqrt(3) rectangle
+    area, alpha = pg.min_area_rectangle(pg.convex_hull(_rot(hexagon, 0.4, (0, 0))))
+    assert abs(area - 2 * math.sqrt(3)) < 1e-12 and abs(alpha - 2 / math.sqrt(3)) < 1e-12
+
+
+def test_aspect_ratio_matches_a_brute_force_scan_over_orientations():
+    from oracle import polygon as pg
+    # a non-convex star: its hull's edges bridge the concavities
+    k = np.arange(14)
+    rad = np.where(k % 2 == 0, 3.0, 1.2) * (1.0 + 0.15 * np.sin(k))
+    star = np.stack([10 + rad * np.cos(2 * math.pi * k / 14) * 1.7, 10 + rad * np.sin(2 * math.pi * k / 14)], 1)
+    area, alpha = pg.min_area_rectangle(pg.convex_hull(star))
+    phi = np.linspace(0.0, math.pi / 2, 20001)[:-1]
+    u = np.stack([np.cos(phi), np.sin(phi)], 1)
+    a = star @ u.T
+    b = star @ np.stack([-np.sin(phi), np.cos(phi)], 1).T
+    w, t = a.max(0) - a.min(0), b.max(0) - b.min(0)
+    j = np.argmin(w * t)
+    assert area <= (w * t)[j] + 1e-12 and (w * t)[j] - area < 1e-3 * area
+    assert abs(max(w[j], t[j]) / min(w[j], t[j]) - alpha) < 1e-3 * alpha
