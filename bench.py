@@ -477,6 +477,10 @@ def run_ours(args):
     t = time.perf_counter()
     dist = c.distortion()
     dist["seconds"] = time.perf_counter() - t
+    # and the polygon-level measures of SI section 4 (mean aspect ratio, relative position error)
+    t = time.perf_counter()
+    dist["polygon"] = c.polygon_measures()
+    dist["polygon"]["seconds"] = time.perf_counter() - t
 
     # live per-kernel timing for the roofline (same stream, CUDA events)
     prof = c.profile(reps=20)

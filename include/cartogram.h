@@ -227,6 +227,20 @@ int cartogram_get_vertices(cg_ctx* ctx, double* xy_out);
  * on the device (no host transfer). Errors: CG_ESTATE (no map). */
 int cartogram_reset(cg_ctx* ctx);
 
+/* Polygon-level distortion measures (SI section 4) of the current vertices against those given
+ * to the last cartogram_set_regions (a region's points are the vertices of all its rings):
+ *   out[0]  mean over the regions of the aspect ratio (longer / shorter side) of the
+ *           bounding rectangle of minimum area over all orientations (exact: found along
+ *           the edges of the region's convex hull; NaN for a hull of more than 2048 vertices)
+ *   out[1]  relative position error theta in [0, 1]: the angle between c_i - c_j and
+ *           d_i - d_j averaged over all pairs of regions and divided by pi, c the centroids
+ *           on the input map and d on the current one
+ *   out[2]  the mean aspect ratio of the input map's regions
+ * The paper's third measure (the total Hamming distance, a minimum over translations of a
+ * symmetric difference of polygons) is not computed. out: 3 doubles, host or device.
+ * Errors: CG_EINVAL (NULL), CG_ESTATE (no map), CG_ECUDA. */
+int cartogram_polygon_measures(cg_ctx* ctx, double* out);
+
 /* New target values for the current map (the frames of an animation, replicates of the
  * data; main text, problem statement: areas proportional to the values): restores the
  * vertices given to the last cartogram_set_regions, clears the history and recomputes the

@@ -7,7 +7,10 @@ library's product path never does.
   all orientations phi in [0, 90 deg); alpha_i = longer side / shorter side of that
   rectangle; alpha = mean over the regions. The minimum lies at an orientation parallel
   to an edge of the region's convex hull (rotating calipers), so the hull's edges are the
-  candidates; exact ties in area go to the smaller ratio.
+  candidates. The paper's argmin is ambiguous where two orientations give the same area
+  (common: a cell cut by the axis-aligned sides of the inset square has two), and the
+  ratio jumps there; orientations whose areas agree to 1e-9 relative are read as ties,
+  which go to the smaller ratio (so that rounding cannot pick the side).
 - Relative position error theta: with c_i the centroids of the regions on the input map
   and d_i on the cartogram, phi_ij = the angle between c_i - c_j and d_i - d_j (the
   paper's arccos of the normalised dot product, evaluated as atan2(|cross|, dot)), and
@@ -73,9 +76,13 @@ def convex_hull(points):
     return np.array(lower[:-1] + upper[:-1])
 
 
+TIE = 1e-9  # relative: rectangle areas this close are the same minimum
+
+
 def min_area_rectangle(hull):
-    """(area, aspect ratio) of the minimum-area bounding rectangle of a convex polygon."""
-    best = (math.inf, math.inf)
+    """(area, aspect ratio) of the minimum-area bounding rectangle of a convex polygon
+    (ties in area, to TIE relative, to the smaller ratio)."""
+    cands = []
     h = len(hull)
     for e in range(h):
         u = hull[(e + 1) % h] - hull[e]
@@ -83,10 +90,9 @@ def min_area_rectangle(hull):
         a = hull @ u
         b = hull @ np.array([-u[1], u[0]])
         w, t = a.max() - a.min(), b.max() - b.min()
-        cand = (w * t, max(w, t) / min(w, t))
-        if cand < best:
-            best = cand
-    return best
+        cands.append((w * t, max(w, t) / min(w, t)))
+    amin = min(c[0] for c in cands)
+    return amin, min(r for a, r in cands if a <= amin * (1.0 + TIE))
 
 
 def aspect_ratios(n_regions, ring_offsets, ring_region, xy):

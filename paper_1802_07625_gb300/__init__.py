@@ -23,7 +23,7 @@ __all__ = [
     "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_polygon_measures", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion",
     "cartogram_iteration_gradient", "cartogram_last_error",
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "cartogram_fold_count": (i, [_P, i, ctypes.POINTER(ll), ctypes.POINTER(d)]),
         "cartogram_reset": (i, [_P]),
         "cartogram_set_values": (i, [_P, _P]),
+        "cartogram_polygon_measures": (i, [_P, _P]),
         "cartogram_autotune": (i, [_P, i, _P, _P]),
         "cartogram_profile": (i, [_P, i, _P]),
         "cartogram_get_grid": (i, [_P, i, _P]),
@@ -225,6 +226,13 @@ def cartogram_get_vertices(ctx, out):
 
 def cartogram_reset(ctx) -> None:
     _check(ctx, load().cartogram_reset(ctx))
+
+
+def cartogram_polygon_measures(ctx) -> dict:
+    out = np.zeros(3)
+    po, _ = _ptr(out, np.float64, writable=True)
+    _check(ctx, load().cartogram_polygon_measures(ctx, po))
+    return {"alpha": float(out[0]), "theta": float(out[1]), "alpha_input": float(out[2])}
 
 
 def cartogram_set_values(ctx, target_values) -> None:
@@ -463,6 +471,9 @@ class Cartogram:
 
     def vertices(self):
         return cartogram_get_vertices(self.ctx, np.empty((self._map.n_vertices, 2)))
+
+    def polygon_measures(self):
+        return cartogram_polygon_measures(self.ctx)
 
     def set_values(self, values):
         cartogram_set_values(self.ctx, values)

@@ -1869,6 +1869,29 @@ int cartogram_reset(cg_ctx* c) {
   return CG_OK;
 }
 
+int cartogram_polygon_measures(cg_ctx* c, double* out) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (!out) return fail(c, CG_EINVAL, "NULL output");
+  const int R = c->R_n, nb = cg::polygon_blocks(R);
+  double* scratch = nullptr;  // cent [2R][2], alpha [R], part [nb], result [3]
+  CG_CUDA(c, cudaMalloc((void**)&scratch, sizeof(double) * (5 * (size_t)R + nb + 3)));
+  double2* cent = (double2*)scratch;
+  double* alpha = scratch + 4 * (size_t)R;
+  double* part = alpha + R;
+  double* res = part + nb;
+  cg::launch_polygon_measures(c->xy, c->xy0, c->ring_off, c->reg_off, c->reg_rings, R, cent, alpha, part, res,
+                              c->stream);
+  double h[3];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail(c, CG_ECUDA, "polygon measures: %s", cudaGetErrorString(e));
+  CG_CUDA(c, cudaMemcpy(out, h, sizeof h, cudaMemcpyDefault));
+  return CG_OK;
+}
+
 int cartogram_set_values(cg_ctx* c, const double* target_values) {
   int r = check_ctx(c, true);
   if (r) return r;

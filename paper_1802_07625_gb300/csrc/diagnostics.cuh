@@ -219,4 +219,232 @@ __global__ void inverse_points_kernel(const void* const* __restrict__ hist, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Polygon-level measures (SI section 4): the mean aspect ratio of the regions' minimum-
+// area bounding rectangles, and the relative position error of their centroids between
+// two vertex sets (the input map and the current one). A region's points are the vertices
+// of all its rings.
+// ---------------------------------------------------------------------------
+
+// Centroids of the regions from the shoelace moments of their rings (signed: holes
+// subtract), one warp per region.
+__global__ void region_centroid_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
+                                       const int* __restrict__ reg_off, const int* __restrict__ reg_rings, int R,
+                                       double2* __restrict__ cent) {
+  const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= R) return;  // whole warps leave together
+  double A = 0.0, Mx = 0.0, My = 0.0;
+  for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) {
+    const int ring = reg_rings[k];
+    const long long a = off[ring], b = off[ring + 1];
+    for (long long v = a + lane; v < b; v += 32) {
+      const double2 p = xy[v], q = xy[v + 1 < b ? v + 1 : a];
+      const double cr = p.x * q.y - q.x * p.y;
+      A += cr;
+      Mx += (p.x + q.x) * cr;
+      My += (p.y + q.y) * cr;
+    }
+  }
+  A = warp_sum(A);
+  Mx = warp_sum(Mx);
+  My = warp_sum(My);
+  // (M / 6) / (A / 2)
+  if (lane == 0) cent[r] = make_double2(Mx / (3.0 * A), My / (3.0 * A));
+}
+
+// Sum over the pairs i < j of the angle between c_i - c_j and d_i - d_j (atan2 of the
+// cross product's magnitude and the dot product: the arccos of their cosine without its
+// loss of accuracy near 0 and pi; 0 where a vector vanishes); block b covers the rows
+// i = b, b + gridDim.x, ... and writes its sum to part[b] (fixed order within the block).
+__global__ void position_error_kernel(const double2* __restrict__ c, const double2* __restrict__ d, int R,
+                                      double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = blockIdx.x; i < R - 1; i += gridDim.x) {
+    const double2 ci = c[i], di = d[i];
+    for (int j = i + 1 + threadIdx.x; j < R; j += blockDim.x) {
+      const double ux = ci.x - c[j].x, uy = ci.y - c[j].y;
+      const double wx = di.x - d[j].x, wy = di.y - d[j].y;
+      // products rounded on their own (no fused multiply-add): the cross product of two
+      // equal vectors is then exactly 0
+      acc += atan2(fabs(__dmul_rn(ux, wy) - __dmul_rn(uy, wx)), __dmul_rn(ux, wx) + __dmul_rn(uy, wy));
+    }
+  }
+  acc = warp_sum(acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Gift wrapping needs "the point q such that no point lies right of p -> q"; between two
+// candidates a and b the one more clockwise about p wins, and of collinear ones the
+// farther (so that points on a hull edge are skipped). Collinear means within 1e-12 of
+// |a - p| |b - p|: the subdivided straight edges of a map put hundreds of points on a line
+// to within rounding, where the exact sign of the cross product is noise and would make
+// the comparison inconsistent (the march could then wander instead of closing).
+__device__ __forceinline__ bool wrap_better(double2 p, double2 a, double2 b) {
+  const double ax = a.x - p.x, ay = a.y - p.y, bx = b.x - p.x, by = b.y - p.y;
+  const double da = ax * ax + ay * ay, db = bx * bx + by * by;
+  const double cr = ax * by - ay * bx, tol = 1e-12 * sqrt(da * db);
+  if (cr < -tol) return true;  // b lies right of p -> a
+  if (cr > tol) return false;
+  return db > da;
+}
+
+constexpr int kHullMax = 2048;
+constexpr double kRectTie = 1e-9;  // rectangle areas this close (relative) are the same minimum
+
+// Area and aspect ratio of the bounding rectangle of the convex polygon hull[0..h) with a
+// side along edge e.
+__device__ __forceinline__ void hull_rectangle(const double2* hull, int h, int e, double& area, double& ratio) {
+  const double2 a = hull[e], b = hull[e + 1 < h ? e + 1 : 0];
+  const double len = sqrt((b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y));
+  const double ux = (b.x - a.x) / len, uy = (b.y - a.y) / len;
+  double lo1 = INFINITY, hi1 = -INFINITY, lo2 = INFINITY, hi2 = -INFINITY;
+  for (int k = 0; k < h; ++k) {
+    const double2 q = hull[k];
+    const double s1 = q.x * ux + q.y * uy, s2 = q.y * ux - q.x * uy;
+    lo1 = fmin(lo1, s1);
+    hi1 = fmax(hi1, s1);
+    lo2 = fmin(lo2, s2);
+    hi2 = fmax(hi2, s2);
+  }
+  const double w = hi1 - lo1, t = hi2 - lo2;
+  area = w * t;
+  ratio = fmax(w, t) / fmin(w, t);
+}
+
+// Aspect ratio alpha_r of every region: its convex hull by gift wrapping (each step one
+// block-wide scan of the region's points), then the bounding rectangle along every hull
+// edge (the minimum-area rectangle of a convex polygon has a side on one of its edges);
+// the smallest area wins, exact ties to the smaller ratio. One block per region (grid-
+// stride); a hull of more than kHullMax vertices gives NaN.
+__global__ void aspect_ratio_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
+                                    const int* __restrict__ reg_off, const int* __restrict__ reg_rings, int R,
+                                    double* __restrict__ alpha) {
+  __shared__ double2 hull[kHullMax];
+  __shared__ double2 s_pt[32];
+  __shared__ double s_a[32], s_r[32];
+  __shared__ int s_h, s_done;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int k0 = reg_off[r], k1 = reg_off[r + 1];
+    // the lowest point (smallest x, then y) is on the hull
+    double2 best = make_double2(INFINITY, INFINITY);
+    for (int k = k0; k < k1; ++k) {
+      const long long a = off[reg_rings[k]], b = off[reg_rings[k] + 1];
+      for (long long v = a + threadIdx.x; v < b; v += blockDim.x) {
+        const double2 q = xy[v];
+        if (q.x < best.x || (q.x == best.x && q.y < best.y)) best = q;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double2 q = make_double2(__shfl_xor_sync(0xffffffffu, best.x, o), __shfl_xor_sync(0xffffffffu, best.y, o));
+      if (q.x < best.x || (q.x == best.x && q.y < best.y)) best = q;
+    }
+    if (lane == 0) s_pt[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 b0 = s_pt[0];
+      for (int w = 1; w < nw; ++w) {
+        const double2 q = s_pt[w];
+        if (q.x < b0.x || (q.x == b0.x && q.y < b0.y)) b0 = q;
+      }
+      hull[0] = b0;
+      s_h = 1;
+      s_done = 0;
+    }
+    __syncthreads();
+    const double2 start = hull[0];
+    // gift wrapping: at most kHullMax steps
+    for (int it = 0; it < kHullMax; ++it) {
+      const double2 p = hull[s_h - 1];
+      double2 cand = p;
+      bool have = false;
+      for (int k = k0; k < k1; ++k) {
+        const long long a = off[reg_rings[k]], b = off[reg_rings[k] + 1];
+        for (long long v = a + threadIdx.x; v < b; v += blockDim.x) {
+          const double2 q = xy[v];
+          if (q.x == p.x && q.y == p.y) continue;
+          if (!have || wrap_better(p, cand, q)) {
+            cand = q;
+            have = true;
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double2 q = make_double2(__shfl_xor_sync(0xffffffffu, cand.x, o), __shfl_xor_sync(0xffffffffu, cand.y, o));
+        const bool qh = __shfl_xor_sync(0xffffffffu, have ? 1 : 0, o) != 0;
+        if (qh && (!have || wrap_better(p, cand, q))) {
+          cand = q;
+          have = true;
+        }
+      }
+      if (lane == 0) s_pt[warp] = have ? cand : make_double2(NAN, NAN);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double2 q0 = make_double2(NAN, NAN);
+        for (int w = 0; w < nw; ++w) {
+          const double2 q = s_pt[w];
+          if (q.x != q.x) continue;  // no candidate in that warp
+          if (q0.x != q0.x || wrap_better(p, q0, q)) q0 = q;
+        }
+        if (q0.x != q0.x || (q0.x == start.x && q0.y == start.y)) s_done = 1;
+        else if (s_h < kHullMax) hull[s_h++] = q0;
+        else s_done = 2;  // hull too long
+      }
+      __syncthreads();
+      if (s_done) break;
+    }
+    const int h = s_h;
+    const bool too_long = s_done == 2;
+    // the rectangle along every hull edge: the smallest area, then the smallest ratio among
+    // the edges whose area is within kRectTie of it (two orientations often tie, and the
+    // ratio jumps between them: rounding must not pick the side)
+    double ba = INFINITY;
+    for (int pass = 0; pass < 2; ++pass) {
+      double bv = INFINITY;
+      for (int e = threadIdx.x; e < h && h >= 3; e += blockDim.x) {
+        double area, ratio;
+        hull_rectangle(hull, h, e, area, ratio);
+        if (pass == 0) bv = fmin(bv, area);
+        else if (area <= ba * (1.0 + kRectTie)) bv = fmin(bv, ratio);
+      }
+      for (int o = 16; o > 0; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+      if (lane == 0) s_a[warp] = bv;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double v = s_a[0];
+        for (int w = 1; w < nw; ++w) v = fmin(v, s_a[w]);
+        s_r[0] = v;
+      }
+      __syncthreads();
+      if (pass == 0) ba = s_r[0];
+      __syncthreads();  // s_r[0] is written again by the next pass
+    }
+    if (threadIdx.x == 0) alpha[r] = (too_long || h < 3) ? NAN : s_r[0];
+    __syncthreads();  // the hull is reused by the next region
+  }
+}
+
+// out[0] = mean of alpha[0..R); with part: out[1] = sum of part[0..nb) * 2 / (R (R - 1) pi)
+// (fixed order, one thread).
+__global__ void polygon_finish_kernel(const double* __restrict__ alpha, int R, const double* __restrict__ part,
+                                      int nb, double* __restrict__ out) {
+  double s = 0.0;
+  for (int r = 0; r < R; ++r) s += alpha[r];
+  out[0] = s / R;
+  if (part) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += part[b];
+    out[1] = R > 1 ? 2.0 * t / ((double)R * (R - 1) * kPi) : 0.0;
+  }
+}
+
 }  // namespace cg

@@ -177,6 +177,13 @@ void launch_outer_decide(OuterState* o, const IterInfo* info, cudaGraphCondition
                          cudaStream_t s);
 // *deadline = device clock + limit_ns (0: no deadline), at the start of a call.
 void launch_deadline(unsigned long long* deadline, unsigned long long limit_ns, cudaStream_t s);
+// Polygon-level measures (SI section 4) of the map with vertices xy against the input map
+// xy0: out[0] mean aspect ratio of xy's regions, out[1] relative position error, out[2] mean
+// aspect ratio of xy0's regions. Scratch: cent [2R], alpha [R], part [polygon_blocks(R)].
+int polygon_blocks(int R);
+void launch_polygon_measures(const double2* xy, const double2* xy0, const long long* off, const int* reg_off,
+                             const int* reg_rings, int R, double2* cent, double* alpha, double* part, double* out,
+                             cudaStream_t s);
 // Diagnostics of the composed projection (history grids hist[0..K)): angular
 // distortion into out[4] (part: 2 * distortion_blocks doubles, max_bits: 2 words), and
 // the preimages of n points, in place.

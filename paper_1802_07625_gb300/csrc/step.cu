@@ -1,4 +1,6 @@
 // Instantiation of the advection, step-control and geometry kernels.
+#include <algorithm>
+
 #include "advect.cuh"
 #include "geometry.cuh"
 #include "linear.cuh"
@@ -149,6 +151,22 @@ void launch_inverse_points(const void* const* hist, int K, int Lx, int Ly, long 
                            cudaStream_t s) {
   if (n <= 0) return;
   inverse_points_kernel<T><<<blocks_for(n, 128, 1 << 16), 128, 0, s>>>(hist, K, Lx, Ly, n, pts);
+}
+
+int polygon_blocks(int R) { return std::max(1, std::min(R - 1, sm_count() * 4)); }
+
+void launch_polygon_measures(const double2* xy, const double2* xy0, const long long* off, const int* reg_off,
+                             const int* reg_rings, int R, double2* cent, double* alpha, double* part, double* out,
+                             cudaStream_t s) {
+  const int cb = blocks_for((long long)R * 32, 256, 1 << 20), ab = std::min(R, sm_count() * 4);
+  const int nb = polygon_blocks(R);
+  region_centroid_kernel<<<cb, 256, 0, s>>>(xy0, off, reg_off, reg_rings, R, cent);
+  region_centroid_kernel<<<cb, 256, 0, s>>>(xy, off, reg_off, reg_rings, R, cent + R);
+  position_error_kernel<<<nb, 256, 0, s>>>(cent, cent + R, R, part);
+  aspect_ratio_kernel<<<ab, 256, 0, s>>>(xy, off, reg_off, reg_rings, R, alpha);
+  polygon_finish_kernel<<<1, 1, 0, s>>>(alpha, R, part, nb, out);
+  aspect_ratio_kernel<<<ab, 256, 0, s>>>(xy0, off, reg_off, reg_rings, R, alpha);
+  polygon_finish_kernel<<<1, 1, 0, s>>>(alpha, R, nullptr, 0, out + 2);
 }
 
 // ---- adjoint of one outer iteration (FP64) ----------------------------------------

@@ -86,3 +86,34 @@ def test_diagnostics_at_1024(orc):
     # map folded has more than one preimage; all others come back
     err = np.max(np.abs(back - p), axis=1)
     assert np.mean(err < 1e-9) > 0.999
+
+
+@pytest.mark.parametrize("name,precision", [("voronoi16_64", "fp64"), ("holes", "fp64"),
+                                            ("clustered300_512", "mixed"), ("powerlaw3000_1024", "mixed")])
+def test_polygon_measures_match_oracle(name, precision):
+    # SI section 4: mean aspect ratio of the minimum-area bounding rectangles, and the
+    # relative position error of the centroids, against the oracle on the GPU's vertices.
+    # The hulls may differ in points collinear to within rounding (the GPU's orientation
+    # test treats 1e-12 relative as collinear), which moves the extents by ~1e-12: alpha
+    # to 1e-10
+    from oracle import polygon as pg
+    m = synth.holes_map(64) if name == "holes" else synth.make_workload(name)
+    blur = synth.WORKLOADS[name]["blur"] if name in synth.WORKLOADS else 1.0
+    with P.Cartogram(m.Lx, m.Ly, blur, precision=precision) as c:
+        c.set_map(m)
+        pm0 = c.polygon_measures()
+        c.integrate()
+        pm = c.polygon_measures()
+        xy = c.vertices()
+    args = (m.n_regions, m.ring_offsets, m.ring_region)
+    a_in = pg.mean_aspect_ratio(*args, m.xy)
+    a_out = pg.mean_aspect_ratio(*args, xy)
+    theta = pg.relative_position_error(pg.region_centroids(*args, m.xy), pg.region_centroids(*args, xy))
+    assert pm0["theta"] == 0.0 and pm0["alpha"] == pm0["alpha_input"]
+    assert abs(pm0["alpha"] - a_in) <= 1e-10 * a_in
+    assert abs(pm["alpha_input"] - a_in) <= 1e-10 * a_in
+    assert abs(pm["alpha"] - a_out) <= 1e-10 * a_out
+    # theta sums p (p - 1) / 2 angles (4.5 million at 1024^2) in a different order on each
+    # side: 1e-10
+    assert abs(pm["theta"] - theta) <= 1e-10 * max(theta, 1e-3)
+    assert 0.0 < pm["theta"] < 0.5 and pm["alpha"] >= 1.0

@@ -769,3 +769,24 @@ def test_aspect_ratio_matches_a_brute_force_scan_over_orientations():
     j = np.argmin(w * t)
     assert area <= (w * t)[j] + 1e-12 and (w * t)[j] - area < 1e-3 * area
     assert abs(max(w[j], t[j]) / min(w[j], t[j]) - alpha) < 1e-3 * alpha
+
+
+def test_aspect_ratio_ties_go_to_the_smaller_ratio():
+    from oracle import polygon as pg
+    # region 3 of the 64^2 Voronoi map is cut by two sides of the inset square: two hull
+    # edges give the same minimum area with different aspect ratios
+    m = synth.make_workload("voronoi16_64")
+    pts = m.xy[m.ring_offsets[3]:m.ring_offsets[4]]
+    hull = pg.convex_hull(pts)
+    cands = []
+    for e in range(len(hull)):
+        u = hull[(e + 1) % len(hull)] - hull[e]
+        u = u / np.hypot(*u)
+        w = np.ptp(hull @ u)
+        t = np.ptp(hull @ np.array([-u[1], u[0]]))
+        cands.append((w * t, max(w, t) / min(w, t)))
+    amin = min(a for a, _ in cands)
+    tied = sorted(r for a, r in cands if a <= amin * (1 + 1e-9))
+    assert len(tied) >= 2 and tied[-1] - tied[0] > 0.1
+    area, alpha = pg.min_area_rectangle(hull)
+    assert area == amin and alpha == tied[0]
