@@ -106,3 +106,14 @@ def test_oracle_and_library_share_no_source():
     for f in ("__init__.py", "build.py", "synth.py"):
         txt = open(os.path.join(ROOT, "paper_1802_07625_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_unknown_options_are_rejected_before_touching_the_gpu():
+    import paper_1802_07625_gb300 as P
+    with pytest.raises(TypeError):
+        P.Cartogram(64, 64, 1.0, no_such_option=1)
+    with pytest.raises(ValueError):
+        P.Cartogram(64, 64, 1.0, flow="sideways")
+    o = P.cartogram_default_options()
+    for name in ("time_limit", "max_iter", "blur_decay", "use_graph", "autotune", "flow"):
+        assert hasattr(o, name)
