@@ -18,6 +18,12 @@ library's product path never does.
   centroids coincide on either map contributes 0.
 A region's vertices are those of all its rings; its centroid is that of the signed sum
 of its rings (holes subtract).
+
+Parity status (tests/test_oracle_pins.py): region_centroids by a square with a hole in
+closed form; relative_position_error by similarity maps (0 for translations and scalings,
+beta / pi for a rotation by beta); convex_hull and min_area_rectangle by rectangles at
+several angles and a regular hexagon in closed form, a brute-force scan over 20,000
+orientations, and the tie rule on a tied cell (pinned).
 """
 import math
 
