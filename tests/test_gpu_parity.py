@@ -404,3 +404,27 @@ def test_non_square_cartogram_matches_oracle(orc, precision):
     assert np.max(np.abs(err - r.err)) < AREA_TOL
     if precision == "fp64":
         assert st.steps_accepted == r.steps_accepted and st.steps_rejected == r.steps_rejected
+
+
+def test_caller_stream_profile_and_autotune():
+    # the context's work on a caller's stream gives the same result as on its own; the
+    # kernel timings and the launch-shape tuner answer with sane values
+    import torch
+    m = _small_map(L=128, n=40)
+    with _ctx(m, 1.0, "mixed") as c:
+        st0 = c.integrate()
+        xy0 = c.vertices()
+    s = torch.cuda.Stream()
+    with _ctx(m, 1.0, "mixed") as c:
+        c.set_stream(s)
+        st = c.integrate()
+        assert (st.iterations, st.steps_accepted, st.steps_rejected) == \
+            (st0.iterations, st0.steps_accepted, st0.steps_rejected)
+        assert np.max(np.abs(c.vertices() - xy0)) < 1e-4  # atomic-order rounding of the FP32 path
+        prof = c.profile(reps=3)
+        assert set(prof) == set(P.PROFILE_CLASSES) and all(0.0 < v < 100.0 for v in prof.values())
+        tuned = c.autotune(reps=2)
+        assert tuned["rows_per_block"] >= 1 and tuned["cols_per_block"] >= 2 and tuned["heun_blocks_per_sm"] >= 1
+        assert all(0.0 < v < 100.0 for v in tuned["ms"])
+        st2 = c.integrate()  # converged already: no iteration
+        assert st2.iterations == 0
