@@ -48,7 +48,8 @@ enum {
     CG_ENOCONVERGE = -4,   /* max_iter outer iterations did not reach area_tol */
     CG_EFOLD = -5,         /* a projected grid folded over (non-positive quad area) */
     CG_ESTEPFAIL = -6,     /* an integration used max_steps attempts, or its step collapsed */
-    CG_ETIMEOUT = -7,      /* a bounded device-side wait (grid barrier, bulk copy) gave up */
+    CG_ETIMEOUT = -7,      /* the call's time_limit passed, or a bounded device-side wait
+                              (grid barrier, bulk copy) gave up */
     CG_ESTATE = -8         /* call out of order (e.g. integrate before set_regions) */
 };
 
