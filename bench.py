@@ -14,6 +14,15 @@ the paper) on the host cores, on a bounded sample of the same workload.
 Under torchrun (N > 1) every rank runs an independent replica of the workload (a
 single cartogram has no data-parallel split worth a collective); value sums the
 updates of all ranks over the slowest rank's time.
+
+Besides the headline, the JSON line carries: the FP64 GPU path on the same workload, the
+linear-equalisation flow, the batched workload (64 frames, split between the ranks), the
+differentiation workload (512^2, FP64 gradient), the Tissot and polygon-level distortion
+of the converged map, live per-kernel timings with the roofline of the dominant step
+kernel, the dense-contraction alternative to the transform passes timed with cuBLAS, the
+end-to-end rate through the C ABI from pinned host buffers, the oracle on the host cores,
+and the SM clocks sampled during the timed region. --no-extras and --grad-only run only
+the headline or only the gradient leg (for profiler captures).
 """
 from __future__ import annotations
 
