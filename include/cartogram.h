@@ -103,6 +103,10 @@ typedef struct cg_options {
                            attempted step: past the limit, the integration in flight ends with
                            CG_ETIMEOUT and maps nothing (the vertices and history keep the
                            iterations completed before it). Must be finite and >= 0 */
+    long long barrier_spins; /* use_graph = 2: polls of one grid-barrier wait before the
+                           persistent kernel gives up and the integration ends with
+                           CG_ETIMEOUT, mapping nothing (2^25, about a second); from 1 to
+                           2^40 */
 } cg_options;
 
 typedef struct cg_stats {
@@ -318,27 +322,33 @@ int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
 int cartogram_autotune(cg_ctx* ctx, int reps, int* shapes_out, double* ms_out);
 
 /* Velocity field from a caller's spectrum with no device allocation. The paper has no
- * counterpart; this serves callers that cannot allocate GPU memory when they need the
- * field (while capturing a CUDA graph, where cudaMalloc is not allowed; under a fixed
- * memory budget; inside a real-time loop that must not touch the allocator).
+ * counterpart. It serves callers that cannot allocate GPU memory when they need the
+ * field: a host application that gives this library a fixed device-memory budget and
+ * owns every allocation itself, or a real-time loop that must not call the allocator
+ * (cudaMalloc and cudaFree may synchronise the device and take unbounded time).
  *   Lx, Ly   powers of two from 8 to 512 (at most 512 x 512 cells); larger sizes
  *            return CG_EINVAL
- *   spec     device, FP32, [Ly][Lx] indexed [n*Lx + m], 16-byte aligned: the cosine
- *            spectrum of rho/rho_bar - 1 (so spec[0] = 0), e.g. cartogram_spectrum's
- *            output with its (0,0) entry set to zero, rounded to FP32
+ *   spec     device memory of the current device, FP32, [Ly][Lx] indexed [n*Lx + m],
+ *            16-byte aligned: the cosine spectrum of rho/rho_bar - 1 (so spec[0] = 0),
+ *            e.g. cartogram_spectrum's output with its (0,0) entry set to zero, rounded
+ *            to FP32
  *   t        diffusion time (D = 1) at which the field is evaluated, >= 0
- *   v_out    device, FP32, [Lx*Ly][2] (vx, vy) at the cell centres, 8-byte aligned
+ *   v_out    device memory of the current device, FP32, [Lx*Ly][2] (vx, vy) at the cell
+ *            centres, 16-byte aligned (the field is written with 16-byte stores)
  *   stream   cudaStream_t the work is queued on (NULL: the legacy default stream);
  *            the call returns without waiting for it
  * The scratch (about 2.1 MB: the intermediate of the two transform passes, the
  * transform tables and a reduction state) is one array in device memory created when
  * the library is loaded onto a GPU and kept until the process exits. The first call on
  * a device, with that device current, looks up the array's device address and sets
- * the kernels' shared-memory limits; make that first call before any stream capture.
- * Every call on a device shares the array and leaves its contents behind: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. Returns CG_OK, CG_EINVAL (sizes, NULL, alignment, host
- * pointers) or CG_ECUDA. */
+ * the kernels' shared-memory limits. Every call on a device shares the array and
+ * leaves its contents behind (the reduction state is cleared by each call): calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. The call is asynchronous, so a failure inside the kernels
+ * is not reported: a spectrum whose density is not positive everywhere gives a
+ * meaningless field, as does a bounded wait inside the kernels that gave up. Returns
+ * CG_OK, CG_EINVAL (sizes, NULL, alignment, host pointers or pointers of another
+ * device) or CG_ECUDA; it calls no cudaMalloc, cudaFree or other allocating routine. */
 int cartogram_velocity_noalloc(int Lx, int Ly, const float* spec, double t, float* v_out,
                                void* stream);
 

@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("rho_tol", ctypes.c_double), ("area_tol", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("use_graph", ctypes.c_int), ("blur_decay", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("flow", ctypes.c_int), ("time_limit", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("flow", ctypes.c_int), ("time_limit", ctypes.c_double),
+                ("barrier_spins", ctypes.c_longlong)]
 
 
 class Stats(ctypes.Structure):
@@ -312,16 +313,23 @@ def cartogram_integrate_once(ctx, grid_out=None):
 
 def cartogram_velocity_noalloc(Lx, Ly, spec, t, v_out, stream=None) -> None:
     """Field from a device FP32 spectrum into a device FP32 [Ly, Lx, 2] buffer, with no
-    device allocation (torch CUDA tensors; queued on `stream`, default torch's current)."""
+    device allocation (torch CUDA tensors on one device; queued on `stream`, default
+    torch's current stream of that device)."""
     import torch
     if not (spec.is_cuda and v_out.is_cuda and spec.dtype == torch.float32 and v_out.dtype == torch.float32
             and spec.is_contiguous() and v_out.is_contiguous()):
         raise ValueError("spec and v_out must be contiguous float32 CUDA tensors")
-    if stream is None:
-        stream = torch.cuda.current_stream(spec.device)
-    if hasattr(stream, "cuda_stream"):
-        stream = stream.cuda_stream
-    rc = load().cartogram_velocity_noalloc(int(Lx), int(Ly), spec.data_ptr(), float(t), v_out.data_ptr(), stream)
+    if spec.device != v_out.device:
+        raise ValueError("spec and v_out must be on the same device")
+    if spec.numel() < int(Lx) * int(Ly) or v_out.numel() < 2 * int(Lx) * int(Ly):
+        raise ValueError("spec needs Lx*Ly and v_out 2*Lx*Ly elements")
+    with torch.cuda.device(spec.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(spec.device)
+        if hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        rc = load().cartogram_velocity_noalloc(int(Lx), int(Ly), spec.data_ptr(), float(t), v_out.data_ptr(),
+                                               stream)
     if rc != CG_OK:
         raise CartogramError(rc, "cartogram_velocity_noalloc(%d, %d) failed" % (Lx, Ly))
 

@@ -1,13 +1,14 @@
 // Velocity field from a caller's spectrum without any device allocation.
 //
-// Some callers cannot allocate GPU memory at the time they need the field: code running
-// while a CUDA graph is being captured (cudaMalloc is not capturable), hosts that hand
-// the library a fixed memory budget, or real-time loops that must not touch the
-// allocator. This entry point keeps its scratch (the transposed intermediate of the
-// two transform passes, the transform tables and the reduction state) in one
-// file-scope device array of fixed size; the caller passes the input spectrum and the
-// output field. The array is created when the library is loaded onto a GPU and held by
-// every GPU that loads the library until the process exits.
+// Some callers cannot allocate GPU memory at the time they need the field: a host
+// application that hands this library a fixed device-memory budget and owns every
+// allocation itself, or a real-time loop that must not call the allocator because
+// cudaMalloc and cudaFree may synchronise the device and take unbounded time. This
+// entry point keeps its scratch (the transposed intermediate of the two transform
+// passes, the transform tables and the reduction state) in one file-scope device array
+// of fixed size; the caller passes the input spectrum and the output field. The array
+// is created when the library is loaded onto a GPU and held by every GPU that loads the
+// library until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -76,13 +77,14 @@ int log2i(int n) {
   return l;
 }
 
-bool is_device_memory(const void* p) {
+// Device (or managed) memory of device `dev`.
+bool is_device_memory(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -91,10 +93,11 @@ extern "C" int cartogram_velocity_noalloc(int Lx, int Ly, const float* spec, dou
                                           void* stream) {
   if (!pow2_between(Lx, 8, 512) || !pow2_between(Ly, 8, 512) || Lx * Ly > kMaxCells) return CG_EINVAL;
   if (!spec || !v_out || !(t >= 0.0) || t > 1e300) return CG_EINVAL;
-  if (((uintptr_t)spec & 15) || ((uintptr_t)v_out & 7)) return CG_EINVAL;
-  if (!is_device_memory(spec) || !is_device_memory(v_out)) return CG_EINVAL;
+  // the transform passes read the spectrum and write the field with 16-byte vector accesses
+  if (((uintptr_t)spec & 15) || ((uintptr_t)v_out & 15)) return CG_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CG_ECUDA;
+  if (!is_device_memory(spec, dev) || !is_device_memory(v_out, dev)) return CG_EINVAL;
   void* base = nullptr;
   const int r = setup_device(dev, &base);
   if (r != CG_OK) return r;
@@ -109,6 +112,10 @@ extern "C" int cartogram_velocity_noalloc(int Lx, int Ly, const float* spec, dou
   const int log2Lx = log2i(Lx), log2Ly = log2i(Ly);
   // the reduction state must start at zero; everything else is overwritten
   if (cudaMemsetAsync(st, 0, sizeof(cg::DevState), s) != cudaSuccess) return CG_ECUDA;
+  // The tables kernels stay plain launches (no programmatic dependent launch) placed
+  // before the row pass: that pass starts its bulk copies of the tables before it waits
+  // on its predecessor, which is safe only because a full kernel boundary separates it
+  // from the kernels that write them.
   noalloc_tables_kernel<<<(Lx + 255) / 256, 256, 0, s>>>(Wx, Ex, Lx, cg::fft_n1(log2Lx));
   noalloc_tables_kernel<<<(Ly + 255) / 256, 256, 0, s>>>(Wy, Ey, Ly, cg::fft_n1(log2Ly));
   cg::launch_inv_rows<float>(log2Lx, Ly, cg::default_rows(log2Lx, Ly), spec, ABt, Wx, Ex, st, cg::kModeFixed,
