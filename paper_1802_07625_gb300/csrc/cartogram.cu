@@ -648,6 +648,7 @@ int run_integration(cg_ctx* c) {
     a.log2Ly = c->log2Ly;
     a.S = c->persist_rows;
     a.Wc = c->persist_cols;
+    a.spins = c->opt.barrier_spins;
     CG_CUDA(c, cudaEventRecord(c->ev0, s));
     CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
     CG_CUDA(c, cudaMemsetAsync(c->gb, 0, sizeof(cg::GridBarrier), s));
@@ -1661,6 +1662,7 @@ int cartogram_default_options(cg_options* o) {
   o->autotune = 1;
   o->flow = CG_FLOW_DIFFUSION;
   o->time_limit = 0.0;
+  o->barrier_spins = 1ll << 25;
   return CG_OK;
 }
 
@@ -1676,6 +1678,7 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   if (o.use_graph < 0 || o.use_graph > 2) return CG_EINVAL;
   if (o.flow != CG_FLOW_DIFFUSION && o.flow != CG_FLOW_LINEAR) return CG_EINVAL;
   if (!is_finite(o.time_limit) || o.time_limit < 0.0 || o.time_limit > 1e9) return CG_EINVAL;
+  if (o.barrier_spins < 1 || o.barrier_spins > (1ll << 40)) return CG_EINVAL;
   if (!(o.dt0 > 0) || !(o.atol > 0) || !(o.grow >= 1.0) || !(o.shrink > 0 && o.shrink < 1) ||
       !(o.cfl > 0) || !(o.rho_tol > 0) || !(o.area_tol > 0) || o.max_steps < 1 || o.max_iter < 0 ||
       !is_finite(o.dt0) || !is_finite(o.atol) || !is_finite(o.grow) || !is_finite(o.cfl) || !is_finite(o.rho_tol) ||

@@ -181,6 +181,7 @@ struct IntegrateArgs {
   StepAcc* acc;  // two slots, zero at launch
   StepParams sp;
   int Lx, Ly, log2Lx, log2Ly, S, Wc;
+  long long spins;  // polls of one grid-barrier wait before giving up
 };
 
 }  // namespace cg

@@ -17,8 +17,6 @@
 
 namespace cg {
 
-constexpr long long kBarrierSpins = 1ll << 25;
-
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -26,8 +24,8 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
 }
 
 // Grid-wide barrier of a cooperative launch. `gen` is the barrier generation as seen
-// by thread 0 of this block. Returns false if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int& gen) {
+// by thread 0 of this block. Returns false if the wait ran out after `spins` polls.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int& gen, long long spins) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -42,9 +40,9 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int& gen)
       __threadfence();
       atomicExch(&gb->gen, g + 1u);
     } else {
-      long long spins = 0;
+      long long left = spins;
       while (ld_acquire_gpu(&gb->gen) == g) {
-        if (++spins > kBarrierSpins) {
+        if (--left <= 0) {
           ok = 0;
           break;
         }
@@ -124,7 +122,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
     for (int it = blockIdx.x; it < nrows; it += gridDim.x)
       if (!p1_dispatch<T>(a.log2Lx, a.spec, a.ABt, a.Wx, a.Ex, a.Ly, a.S, it * a.S, tau, smem, &bar, ph))
         return false;
-    if (!grid_barrier(a.gb, gen)) return false;
+    if (!grid_barrier(a.gb, gen, a.spins)) return false;
     T dev = T(0), v2 = T(0);
     bool bad = false;
     for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
@@ -140,7 +138,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
       atomic_max_nonneg(&slot->vmax2, (double)v2);
       if (bad) atomicOr(&slot->bad, 1u);
     }
-    return grid_barrier(a.gb, gen);
+    return grid_barrier(a.gb, gen, a.spins);
   };
 
   // ---- field at t = 0 and the first step ----
@@ -184,7 +182,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(IntegrateA
     // one clock reading for all blocks: block 0 flags the slot (bit 2) before the
     // barrier, and every replicated controller reads the same flag after it
     if (blockIdx.x == 0 && threadIdx.x == 0 && deadline_passed(a.sp)) atomicOr(&slot->bad, 2u);
-    ok = grid_barrier(a.gb, gen);
+    ok = grid_barrier(a.gb, gen, a.spins);
     if (!ok) break;
     if (threadIdx.x == 0) {
       // the controller, replicated: accept / reject, next step, stopping rule

@@ -45,6 +45,7 @@ def test_default_options_without_gpu():
     assert o.cfl == 1.0 and o.rho_tol == 1e-4 and o.area_tol == 0.01
     assert o.max_steps == 4000 and o.max_iter == 500 and o.use_graph == 1 and o.blur_decay == 0.5 and o.autotune == 1
     assert o.flow == P.CG_FLOW_DIFFUSION and o.time_limit == 0.0
+    assert o.barrier_spins == 1 << 25
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
@@ -91,6 +92,12 @@ def test_init_rejects_bad_sizes_before_touching_the_gpu():
     for bad in (-1.0, float("nan"), float("inf")):
         o = P.cartogram_default_options()
         o.time_limit = bad
+        with pytest.raises(P.CartogramError) as e:
+            P.cartogram_init(64, 64, 1.0, o)
+        assert e.value.code == P.CG_EINVAL
+    for bad in (0, -5, (1 << 40) + 1):
+        o = P.cartogram_default_options()
+        o.barrier_spins = bad
         with pytest.raises(P.CartogramError) as e:
             P.cartogram_init(64, 64, 1.0, o)
         assert e.value.code == P.CG_EINVAL

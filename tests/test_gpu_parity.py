@@ -314,6 +314,28 @@ def test_time_limit_reports_timeout(use_graph):
         assert np.max(np.abs(c.vertices() - xy0)) < 1e-12
 
 
+def test_grid_barrier_give_up_reports_timeout():
+    """The persistent kernel's grid-barrier waits are bounded: with a one-poll limit the
+    first barrier that is not already open makes its waiting blocks give up; every other
+    block gives up at its next barrier, so the launch ends, the integration reports
+    CG_ETIMEOUT and maps nothing. A generous limit reproduces the default run."""
+    m = _small_map()
+    with _ctx(m, 1.0, "fp64", use_graph=2, autotune=0) as ref:
+        st0 = ref.integrate()
+        xy0 = ref.vertices()
+    with _ctx(m, 1.0, "fp64", use_graph=2, barrier_spins=1, autotune=0) as c:
+        with pytest.raises(P.CartogramError) as e:
+            c.integrate()
+        assert e.value.code == P.CG_ETIMEOUT
+        assert np.array_equal(c.vertices(), m.xy) and c.history_length() == 0
+    # a context whose limit is generous reproduces the unlimited run
+    with _ctx(m, 1.0, "fp64", use_graph=2, barrier_spins=1 << 30, autotune=0) as c:
+        st1 = c.integrate()
+        assert (st1.iterations, st1.steps_accepted, st1.steps_rejected) == \
+            (st0.iterations, st0.steps_accepted, st0.steps_rejected)
+        assert np.max(np.abs(c.vertices() - xy0)) < 1e-12
+
+
 def test_time_limit_in_a_batch_and_in_the_linear_flow():
     m = _small_map()
     limited = P.Cartogram(m.Lx, m.Ly, 1.0, precision="mixed", time_limit=1e-9, autotune=0)
