@@ -275,8 +275,9 @@ def run_batched(args, P, synth, flush, stream):
     as parallel branches of one CUDA-graph launch, against the same contexts run one
     after another. Host wall clock around the synchronous batch call. With several
     ranks the frames are split between them (greedy balance of the expected updates, no
-    collective on the data path): each rank runs its share as one batch, the time is the
-    slowest rank's and the per-frame results are gathered to rank 0."""
+    collective on the data path; the split uses each frame's attempted steps measured by a
+    calibration run): each rank runs its share as one batch, the time is the slowest
+    rank's and the per-frame results are gathered to rank 0."""
     import collections
 
     import torch
@@ -284,13 +285,30 @@ def run_batched(args, P, synth, flush, stream):
     from paper_1802_07625_gb300 import shard
     world, rank, _ = _dist()
     frames_all = synth.make_batch()
-    mine = shard.partition([shard.frame_cost(f.Lx, f.Ly) for f in frames_all], world)[rank]
+    sizes = [(f.Lx, f.Ly) for f in frames_all]
+
+    def open_share(idx):
+        cs = [P.Cartogram(frames_all[i].Lx, frames_all[i].Ly, synth.BATCH["blur"], precision="mixed") for i in idx]
+        steps = []
+        for c, i in zip(cs, idx):
+            c.set_map(frames_all[i])
+            st = c.integrate()  # picks the launch shapes, as in a first use
+            steps.append(st.steps_accepted + st.steps_rejected)
+        return cs, steps
+
+    # first split by the size model; the calibration run measures every frame's attempted
+    # steps, and the frames are split again by those (host-side exchange, untimed)
+    mine = shard.partition([shard.frame_cost(*sz) for sz in sizes], world)[rank]
+    carts, cal = open_share(mine)
+    costs = shard.measured_costs(sizes, shard.gather_results(world, rank, mine, cal, all_ranks=True))
+    parts = shard.partition(costs, world)
+    if parts[rank] != mine:
+        for c in carts:
+            c.close()
+        mine = parts[rank]
+        carts, _ = open_share(mine)
     frames = [frames_all[i] for i in mine]
-    carts = [P.Cartogram(f.Lx, f.Ly, synth.BATCH["blur"], precision="mixed") for f in frames]
     try:
-        for c, f in zip(carts, frames):
-            c.set_map(f)
-            c.integrate()  # picks the launch shapes, as in a first use
         torch.cuda.synchronize()
         # one after another (each context's own device-side loop)
         _barrier(world)
@@ -331,8 +349,8 @@ def run_batched(args, P, synth, flush, stream):
         return {"workload": "64 frames, 300-region Voronoi maps, lognormal(1) values drifting by a "
                             "multiplicative random walk, blur %g, mixed" % synth.BATCH["blur"],
                 "size_counts": {str(k): v for k, v in sorted(collections.Counter(f.Lx for f in frames_all).items())},
-                "ranks": world, "frames_per_rank": [len(p) for p in shard.partition(
-                    [shard.frame_cost(f.Lx, f.Ly) for f in frames_all], world)],
+                "ranks": world, "frames_per_rank": [len(p) for p in parts],
+                "split": "greedy balance of each frame's attempted steps measured by a calibration run",
                 "s_per_batch": s_batch, "updates_per_s": updates / s_batch,
                 "sequential_s": seq_s, "speedup_vs_sequential": seq_s / s_batch,
                 "all_converged": all(r[4] for r in res), "iterations_min_max": [min(its), max(its)],

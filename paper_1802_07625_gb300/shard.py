@@ -8,10 +8,13 @@ results to rank 0 on the host at the end.
 The split is a greedy longest-first balance (each frame, costliest first, goes to the
 rank with the least work so far; ties to the lower rank), which gives a makespan within
 4/3 of the optimum. A frame's cost is its grid-point updates to convergence,
-Lx * Ly * (attempted steps); the attempted steps are not known before the run, so the
-default model takes them proportional to the grid's larger side (the step size is
-capped at one cell of displacement per step and the displacements, in cells, grow with
-the grid).
+Lx * Ly * (attempted steps). Before any run the attempted steps are unknown, and the size
+model takes them proportional to the grid's larger side (the step size is capped at one
+cell of displacement per step and the displacements, in cells, grow with the grid). That
+model can be off by an order of magnitude: frames of one size need from a few to over a
+hundred outer iterations. Once a run has measured each frame's attempted steps, the split
+uses those (measured_costs); frames drift slowly, so a frame without a measurement takes
+the steps of the nearest earlier measured frame of its size.
 """
 
 
@@ -19,6 +22,27 @@ def frame_cost(Lx, Ly, steps=None):
     """Expected grid-point updates of one frame: Lx * Ly * steps, with steps taken as
     max(Lx, Ly) when not given."""
     return float(Lx) * float(Ly) * float(max(Lx, Ly) if steps is None else steps)
+
+
+def measured_costs(sizes, steps):
+    """Costs Lx * Ly * steps from measured attempted steps. `sizes` lists (Lx, Ly) per
+    frame and `steps` the measured attempted steps per frame (None where not measured):
+    such a frame takes the steps of the nearest earlier measured frame of the same size,
+    else the nearest later one, else the size model."""
+    if len(sizes) != len(steps):
+        raise ValueError("one step count per frame")
+    out = []
+    for i, (lx, ly) in enumerate(sizes):
+        st = steps[i]
+        if st is None:
+            same = [k for k in range(len(sizes)) if tuple(sizes[k]) == (lx, ly) and steps[k] is not None]
+            earlier = [k for k in same if k < i]
+            later = [k for k in same if k > i]
+            st = steps[earlier[-1]] if earlier else (steps[later[0]] if later else None)
+        if st is not None and not (st >= 0):
+            raise ValueError("step counts must be non-negative")
+        out.append(frame_cost(lx, ly, st))
+    return out
 
 
 def partition(costs, world):
@@ -39,10 +63,11 @@ def partition(costs, world):
     return [sorted(p) for p in parts]
 
 
-def gather_results(world, rank, frames, results):
-    """Collect each rank's per-frame results on rank 0, in frame order: returns the list
-    indexed by frame on rank 0 and None elsewhere. `frames` are this rank's frame indices
-    and `results` its results for them (any picklable objects), in the same order."""
+def gather_results(world, rank, frames, results, all_ranks=False):
+    """Collect each rank's per-frame results on rank 0 (on every rank with all_ranks), in
+    frame order: returns the list indexed by frame there and None elsewhere. `frames` are
+    this rank's frame indices and `results` its results for them (any picklable objects),
+    in the same order."""
     if len(frames) != len(results):
         raise ValueError("one result per frame")
     if world == 1:
@@ -53,7 +78,7 @@ def gather_results(world, rank, frames, results):
     import torch.distributed as dist
     got = [None] * world
     dist.all_gather_object(got, (list(frames), list(results)))
-    if rank != 0:
+    if rank != 0 and not all_ranks:
         return None
     n = sum(len(f) for f, _ in got)
     out = [None] * n

@@ -55,7 +55,11 @@ def _shard_worker(rank, world, port, q):
     mine = shard.partition(costs, world)[rank]
     # each rank "runs" its frames: here the result is the frame's size and a rank tag
     res = shard.gather_results(world, rank, mine, [(frames[i].Lx, rank) for i in mine])
-    q.put((rank, mine, res))
+    # the re-split by measured step counts: every rank gathers every frame's count and
+    # computes the same new split (here the "measured" steps are 10 * (frame index + 1))
+    steps = shard.gather_results(world, rank, mine, [10 * (i + 1) for i in mine], all_ranks=True)
+    parts = shard.partition(shard.measured_costs([(f.Lx, f.Ly) for f in frames], steps), world)
+    q.put((rank, mine, res, steps, parts))
     dist.destroy_process_group()
 
 
@@ -72,7 +76,9 @@ def test_two_rank_batch_sharding_gathers_every_frame_once():
         p.join(timeout=60)
         assert p.exitcode == 0
     frames = synth.make_batch(frames=10, sizes=(128, 256))
-    (r0, mine0, res0), (r1, mine1, res1) = out
+    (r0, mine0, res0, steps0, parts0), (r1, mine1, res1, steps1, parts1) = out
+    assert steps0 == steps1 == [10 * (i + 1) for i in range(10)]
+    assert parts0 == parts1 and sorted(parts0[0] + parts0[1]) == list(range(10))
     assert sorted(mine0 + mine1) == list(range(10)) and not set(mine0) & set(mine1)
     assert res1 is None
     assert [r[0] for r in res0] == [f.Lx for f in frames]

@@ -48,3 +48,33 @@ def test_partition_and_gather_reject_bad_input():
     with pytest.raises(ValueError):
         shard.gather_results(1, 0, [0, 1], [None])
     assert shard.gather_results(1, 0, [1, 0], ["b", "a"]) == ["a", "b"]
+
+
+def test_measured_costs_fill_gaps_from_frames_of_the_same_size():
+    sizes = [(128, 128), (256, 256), (128, 128), (256, 256), (512, 512)]
+    steps = [100, None, None, 40, None]
+    c = shard.measured_costs(sizes, steps)
+    assert c[0] == 128 * 128 * 100
+    assert c[1] == 256 * 256 * 40      # the nearest later frame of its size
+    assert c[2] == 128 * 128 * 100     # the nearest earlier frame of its size
+    assert c[3] == 256 * 256 * 40
+    assert c[4] == shard.frame_cost(512, 512)  # no measurement of that size: the size model
+    with pytest.raises(ValueError):
+        shard.measured_costs(sizes, steps[:2])
+
+
+def test_measured_costs_balance_better_than_the_size_model():
+    # frames of one size whose step counts differ by 20x: the size model sees equal costs,
+    # the measured costs let the split balance the real work
+    rng = np.random.default_rng(3)
+    sizes = [(256, 256)] * 16
+    steps = list(rng.integers(50, 1000, 16))
+    real = [256 * 256 * s for s in steps]
+    by_size = shard.partition([shard.frame_cost(*sz) for sz in sizes], 4)
+    by_steps = shard.partition(shard.measured_costs(sizes, steps), 4)
+
+    def makespan(parts):
+        return max(sum(real[i] for i in p) for p in parts)
+
+    assert makespan(by_steps) <= makespan(by_size)
+    assert makespan(by_steps) <= sum(real) / 4 + max(real)
