@@ -18,7 +18,8 @@ Stored per workload (`<name>.npz`):
   cell_index, grid  projected position (X, Y) of a fixed sample of grid cells after every
                     outer iteration, [iterations, 2, n_cells]
 
-Usage:  python oracle/make_golden.py [workload ...]   (default: all three)
+Usage:  python oracle/make_golden.py [--out DIR] [workload ...]   (default: all of RUNS,
+        written to tests/golden/)
 The 1024^2 workload costs about 3000 attempted steps of O(L^3) direct sums: tens of
 minutes on a few host cores.
 """
@@ -43,6 +44,10 @@ RUNS = {
     "voronoi16_64": dict(max_iter=200, n_vertices=4096, n_cells=256),
     "clustered300_512": dict(max_iter=260, n_vertices=16384, n_cells=512),
     "powerlaw3000_1024": dict(max_iter=60, n_vertices=16384, n_cells=512),
+    # the first frame of each of the two smaller grid sizes of the batched workload
+    # (64 frames whose values drift by a multiplicative random walk)
+    "batch_frame_128": dict(max_iter=200, n_vertices=8192, n_cells=256, batch_size=128),
+    "batch_frame_256": dict(max_iter=200, n_vertices=8192, n_cells=256, batch_size=256),
 }
 
 
@@ -69,14 +74,30 @@ def sample_indices(n: int, k: int) -> np.ndarray:
     return (np.arange(k, dtype=np.int64) * n) // k
 
 
-def run(name: str) -> dict:
+def batch_frame(synth, size: int):
+    """(frame number, map) of the first frame of the batched workload with this grid size."""
+    for f, m in enumerate(synth.make_batch()):
+        if m.Lx == size:
+            return f, m
+    raise ValueError("no frame of size %d" % size)
+
+
+def workload(synth, name: str):
+    cfg = RUNS[name]
+    if "batch_size" in cfg:
+        f, m = batch_frame(synth, cfg["batch_size"])
+        return m, float(synth.BATCH["blur"]), f
+    m = synth.make_workload(name)
+    return m, float(m.meta["blur"]), -1
+
+
+def run(name: str, out_dir: str = GOLDEN) -> dict:
     sys.path.insert(0, ROOT)
     import oracle
 
     synth = load_synth()
     cfg = RUNS[name]
-    m = synth.make_workload(name)
-    blur = float(m.meta["blur"])
+    m, blur, frame = workload(synth, name)
     t0 = time.time()
     res = oracle.cartogram(m, blur, keep_grids=True, max_iter=cfg["max_iter"])
     seconds = time.time() - t0
@@ -88,18 +109,23 @@ def run(name: str) -> dict:
     grid = res.grids[:, :, iy, ix] if res.iterations else np.zeros((0, 2, ci.size))
     out = dict(map_sha256=map_sha256(m), iterations=res.iterations, converged=int(res.converged),
                status=res.status, steps_accepted=res.steps_accepted, steps_rejected=res.steps_rejected,
-               max_area_error=res.max_area_error, blur=blur, max_iter=cfg["max_iter"],
+               max_area_error=res.max_area_error, blur=blur, max_iter=cfg["max_iter"], frame=frame,
                oracle_seconds=seconds, oracle_threads=oracle.num_threads())
-    os.makedirs(GOLDEN, exist_ok=True)
-    np.savez_compressed(os.path.join(GOLDEN, name + ".npz"), err=res.err, vertex_index=vi, xy=res.xy[vi],
+    os.makedirs(out_dir, exist_ok=True)
+    np.savez_compressed(os.path.join(out_dir, name + ".npz"), err=res.err, vertex_index=vi, xy=res.xy[vi],
                         cell_index=ci, grid=grid, meta=np.array(json.dumps(out)))
     return out
 
 
 def main(argv):
+    out_dir = GOLDEN
+    if "--out" in argv:
+        k = argv.index("--out")
+        out_dir = argv[k + 1]
+        argv = argv[:k] + argv[k + 2:]
     names = argv or list(RUNS)
     for name in names:
-        info = run(name)
+        info = run(name, out_dir)
         print(name, json.dumps(info), flush=True)
 
 
