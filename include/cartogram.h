@@ -222,6 +222,28 @@ int cartogram_distortion(cg_ctx* ctx, double* out);
 int cartogram_iteration_gradient(cg_ctx* ctx, const double* values, double blur_width, double lambda, int iterations,
                                  int replay, int checkpoint, double* loss, double* grad_values, double* grad_blur);
 
+/* Vector-Jacobian product of `iterations` outer iterations, for a loss of the caller's
+ * choosing on the mapped vertices and areas (the reverse mode of
+ * cartogram_iteration_gradient with the loss left to the caller). From the current
+ * vertices X (left unchanged; no history entry is added) with target values
+ * V = values[n_regions] and blur width blur_width, the iterations give the mapped vertices
+ * X' and their region areas A' (SI Eq. det: the areas the cartogram equalises).
+ *   xy_out     [n_vertices][2] FP64: X' (may be NULL)
+ *   area_out   [n_regions] FP64: A' (may be NULL)
+ *   grad_xy    [n_vertices][2] FP64: dL/dX' of the caller's loss (NULL: zero)
+ *   grad_area  [n_regions] FP64: dL/dA' (NULL: zero)
+ *   grad_values[n_regions], grad_blur: receive (dX'/dV)^T dL/dX' + (dA'/dV)^T dL/dA' and the
+ *              same for the blur width (each may be NULL; with both NULL only the forward
+ *              runs). A term of the loss that depends on V directly is not included.
+ * replay and checkpoint are as for cartogram_iteration_gradient (a forward call with
+ * replay = 0 records the step schedules, a later call with replay = 1 differentiates that
+ * same function). Every array may be host or device memory. Needs the FP64 path and the
+ * diffusion flow. Errors: CG_EINVAL (arguments, non-finite adjoints), CG_ESTATE,
+ * CG_ESTEPFAIL, CG_ENOMEM, CG_ECUDA. */
+int cartogram_iteration_vjp(cg_ctx* ctx, const double* values, double blur_width, int iterations, int replay,
+                            int checkpoint, double* xy_out, double* area_out, const double* grad_xy,
+                            const double* grad_area, double* grad_values, double* grad_blur);
+
 /* Signed relative area errors A_i / A^_i - 1 of the current vertices, [n_regions]. */
 int cartogram_area_errors(cg_ctx* ctx, double* err);
 
@@ -320,6 +342,15 @@ int cartogram_profile(cg_ctx* ctx, int reps, double* ms_out);
  * after its first integration, when the autotune option is set. Errors: CG_EINVAL,
  * CG_ECUDA. */
 int cartogram_autotune(cg_ctx* ctx, int reps, int* shapes_out, double* ms_out);
+
+/* Diagnostic (no counterpart in the paper): the read bandwidth of the current GPU, the
+ * roofline the step kernels are compared against. A buffer of `bytes` (from 1 MiB to
+ * 64 GiB, a multiple of 16) is allocated, filled, read once, and then read `passes`
+ * times by 8 blocks of 256 threads per SM with 16-byte loads that bypass L1, timed with
+ * CUDA events (best of three). A buffer well below the L2 size measures L2 read
+ * bandwidth, one far above it HBM read bandwidth. *gbs_out = bytes * passes / time in
+ * GB/s (1e9 bytes). Synchronous. Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
+int cartogram_read_bandwidth(int64_t bytes, int passes, double* gbs_out);
 
 /* Velocity field from a caller's spectrum with no device allocation. The paper has no
  * counterpart. It serves callers that cannot allocate GPU memory when they need the

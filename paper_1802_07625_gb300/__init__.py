@@ -23,13 +23,13 @@ __all__ = [
     "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_polygon_measures", "cartogram_autotune", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_polygon_measures", "cartogram_autotune", "cartogram_read_bandwidth", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion",
-    "cartogram_iteration_gradient", "cartogram_last_error",
+    "cartogram_iteration_gradient", "cartogram_iteration_vjp", "cartogram_last_error",
     "cartogram_destroy", "cartogram_batch_create",
     "cartogram_batch_integrate", "cartogram_batch_last_error", "cartogram_batch_destroy", "Cartogram", "Batch",
-    "iteration_loss",
+    "iteration_loss", "mapped_iterations",
 ]
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
         "cartogram_set_values": (i, [_P, _P]),
         "cartogram_polygon_measures": (i, [_P, _P]),
         "cartogram_autotune": (i, [_P, i, _P, _P]),
+        "cartogram_read_bandwidth": (i, [ll, i, ctypes.POINTER(d)]),
         "cartogram_profile": (i, [_P, i, _P]),
         "cartogram_get_grid": (i, [_P, i, _P]),
         "cartogram_density": (i, [_P, _P]),
@@ -112,6 +113,7 @@ def load(build_if_missing: bool = True):
         "cartogram_inverse_project": (i, [_P, ll, _P, _P]),
         "cartogram_distortion": (i, [_P, _P]),
         "cartogram_iteration_gradient": (i, [_P, _P, d, d, i, i, i, _P, _P, _P]),
+        "cartogram_iteration_vjp": (i, [_P, _P, d, i, i, i, _P, _P, _P, _P, _P, _P]),
         "cartogram_last_error": (ctypes.c_char_p, [_P]),
         "cartogram_destroy": (None, [_P]),
         "cartogram_batch_create": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P)]),
@@ -259,6 +261,15 @@ def cartogram_autotune(ctx, reps: int = 10) -> dict:
             "heun_blocks_per_sm": int(shapes[2]), "ms": ms.tolist()}
 
 
+def cartogram_read_bandwidth(nbytes: int, passes: int = 20) -> float:
+    """Read bandwidth (GB/s) of the current GPU over a resident buffer of nbytes."""
+    g = ctypes.c_double()
+    rc = load().cartogram_read_bandwidth(int(nbytes), int(passes), ctypes.byref(g))
+    if rc != CG_OK:
+        raise CartogramError(rc, "cartogram_read_bandwidth(%d, %d) failed" % (nbytes, passes))
+    return g.value
+
+
 def cartogram_history_length(ctx) -> int:
     return load().cartogram_history_length(ctx)
 
@@ -360,6 +371,31 @@ def cartogram_iteration_gradient(ctx, values, blur, lam=1e-3, replay=False, chec
                                                    gv.ctypes.data if grad else None,
                                                    ctypes.byref(gb) if grad else None))
     return (loss.value, gv, gb.value) if grad else loss.value
+
+
+def cartogram_iteration_vjp(ctx, values, blur, n_vertices, iterations=1, replay=False, checkpoint=8,
+                            grad_xy=None, grad_area=None, grad=True):
+    """Mapped vertices X' [n_vertices, 2] and areas A' of `iterations` outer iterations and
+    (grad=True) the vector-Jacobian product of the adjoints grad_xy = dL/dX', grad_area =
+    dL/dA' (None: zero) with respect to the values and the blur width."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    xy = np.empty((int(n_vertices), 2))
+    area = np.empty(v.shape[0])
+    gx = None if grad_xy is None else np.ascontiguousarray(grad_xy, dtype=np.float64)
+    ga = None if grad_area is None else np.ascontiguousarray(grad_area, dtype=np.float64)
+    if gx is not None and gx.shape != xy.shape:
+        raise ValueError("grad_xy must have shape %s" % (xy.shape,))
+    if ga is not None and ga.shape != area.shape:
+        raise ValueError("grad_area must have shape %s" % (area.shape,))
+    gv = np.zeros_like(v) if grad else None
+    gb = ctypes.c_double()
+    _check(ctx, load().cartogram_iteration_vjp(ctx, v.ctypes.data, float(blur), int(iterations), int(bool(replay)),
+                                              int(checkpoint), xy.ctypes.data, area.ctypes.data,
+                                              gx.ctypes.data if gx is not None else None,
+                                              ga.ctypes.data if ga is not None else None,
+                                              gv.ctypes.data if grad else None,
+                                              ctypes.byref(gb) if grad else None))
+    return (xy, area, gv, gb.value) if grad else (xy, area)
 
 
 def cartogram_last_error(ctx) -> str:
@@ -474,6 +510,11 @@ class Cartogram:
     def iteration_gradient(self, values, blur, lam=1e-3, replay=False, checkpoint=8, grad=True, iterations=1):
         return cartogram_iteration_gradient(self.ctx, values, blur, lam, replay, checkpoint, grad, iterations)
 
+    def iteration_vjp(self, values, blur, iterations=1, replay=False, checkpoint=8, grad_xy=None, grad_area=None,
+                      grad=True):
+        return cartogram_iteration_vjp(self.ctx, values, blur, self._map.n_vertices, iterations, replay, checkpoint,
+                                       grad_xy, grad_area, grad)
+
     def area_errors(self):
         return cartogram_area_errors(self.ctx, np.empty(self._map.n_regions))
 
@@ -583,3 +624,37 @@ def iteration_loss(values, blur, cartogram, lam=1e-3, checkpoint=8, iterations=1
 
     b = blur if isinstance(blur, torch.Tensor) else torch.tensor(float(blur), dtype=torch.float64)
     return _IterationLoss.apply(values, b)
+
+
+def mapped_iterations(values, blur, cartogram, iterations=1, checkpoint=8):
+    """The mapped vertices X' [n_vertices, 2] and region areas A' [n_regions] after
+    `iterations` outer iterations from the cartogram's current vertices, as a
+    differentiable torch function of the target values (1-D float64 tensor) and the blur
+    width (0-D tensor or float). Any loss written in torch on (X', A') -- and on the values
+    directly -- can be differentiated: the backward hands dL/dX' and dL/dA' to the library's
+    vector-Jacobian product (cartogram_iteration_vjp), which replays the step schedules the
+    forward recorded. The context must not run anything else between the two."""
+    import torch
+
+    class _MappedIterations(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v, b):
+            vals = v.detach().cpu().double().numpy()
+            xy, area = cartogram.iteration_vjp(vals, float(b), iterations=iterations, replay=False,
+                                               checkpoint=checkpoint, grad=False)
+            ctx.args = (vals, float(b), v.device, v.dtype)
+            return (torch.as_tensor(xy, dtype=torch.float64, device=v.device),
+                    torch.as_tensor(area, dtype=torch.float64, device=v.device))
+
+        @staticmethod
+        def backward(ctx, g_xy, g_area):
+            vals, b, dev, dt = ctx.args
+            gx = None if g_xy is None else g_xy.detach().cpu().double().numpy()
+            ga = None if g_area is None else g_area.detach().cpu().double().numpy()
+            _, _, gv, gb = cartogram.iteration_vjp(vals, b, iterations=iterations, replay=True,
+                                                   checkpoint=checkpoint, grad_xy=gx, grad_area=ga)
+            return (torch.as_tensor(gv, device=dev).to(dt),
+                    torch.tensor(gb, dtype=torch.float64, device=dev))
+
+    b = blur if isinstance(blur, torch.Tensor) else torch.tensor(float(blur), dtype=torch.float64)
+    return _MappedIterations.apply(values, b)

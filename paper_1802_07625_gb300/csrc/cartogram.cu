@@ -1325,8 +1325,19 @@ void adj_reverse(cg_ctx* c, const std::vector<double>& sch, int C) {
   if (NS > 0) adj_level(c, a->L[hi], a->v[0], a->rho[0], 0.0);
 }
 
+// A caller's own loss of the mapped vertices X' and areas A': its adjoints dL/dX' and
+// dL/dA' (either may be NULL: zero) replace the built-in loss, and X', A' are returned.
+struct Upstream {
+  bool custom = false;
+  const double* g_xy = nullptr;    // [n_vert][2]
+  const double* g_area = nullptr;  // [R]
+  double* xy_out = nullptr;        // [n_vert][2]
+  double* area_out = nullptr;      // [R]
+};
+
 int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, double lam, int K, int replay, int C,
-                          double* loss_out, double* grad_values, double* grad_blur) {
+                          double* loss_out, double* grad_values, double* grad_blur,
+                          const Upstream& up = Upstream()) {
   cudaStream_t s = c->stream;
   const int R = c->R_n;
   const size_t N = (size_t)c->Lx * c->Ly;
@@ -1402,34 +1413,54 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   CG_CUDA(c, cudaMemcpyAsync(X1.data(), a->X[K], sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
   CG_CUDA(c, cudaMemcpyAsync(X0.data(), a->X[0], sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
   CG_CUDA(c, cudaStreamSynchronize(s));
+  if (up.custom) {
+    if (up.xy_out) CG_CUDA(c, cudaMemcpy(up.xy_out, X1.data(), sizeof(double2) * nv, cudaMemcpyDefault));
+    if (up.area_out) CG_CUDA(c, cudaMemcpy(up.area_out, A1.data(), sizeof(double) * R, cudaMemcpyDefault));
+  }
   double sA1 = 0.0;
   for (int i = 0; i < R; ++i) sA1 += A1[i];
   std::vector<double> res(R);
   double L = 0.0, sres = 0.0;
-  for (int i = 0; i < R; ++i) {
+  for (int i = 0; i < R && !up.custom; ++i) {
     if (!(A1[i] > 0.0)) return fail(c, CG_EFOLD, "region %d has non-positive mapped area %g", i, A1[i]);
     res[i] = std::log(A1[i]) - std::log(V[i] * sA1 / sV);
     L += res[i] * res[i];
     sres += res[i];
   }
   double pen = 0.0;
-  for (int v = 0; v < nv; ++v) {
+  for (int v = 0; v < nv && !up.custom; ++v) {
     const double dx = X1[v].x - X0[v].x, dy = X1[v].y - X0[v].y;
     pen += dx * dx + dy * dy;
   }
   L += lam * pen;
-  if (loss_out) *loss_out = L;
+  if (loss_out && !up.custom) *loss_out = L;
   if (grad_values || grad_blur) {
-    std::vector<double> dLdA(R), gV(R);
-    for (int j = 0; j < R; ++j) {
-      dLdA[j] = 2.0 * res[j] / A1[j] - 2.0 * sres / sA1;
-      gV[j] = -2.0 * res[j] / V[j] + 2.0 * sres / sV;
-    }
-    CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dLdA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
-    // adjoint of the final vertices
+    std::vector<double> dLdA(R, 0.0), gV(R, 0.0);
     double2* lamX = a->gv;
     double2* lamX2 = a->gv2;
-    cg::launch_loss_vertex_adjoint(a->X[K], a->X[0], c->next, c->prev, c->vreg, a->dLdA, lam, lamX, nv, s);
+    if (up.custom) {
+      // the caller's adjoints: dL/dX' directly, dL/dA' through the shoelace derivative;
+      // the loss has no direct dependence on the values here (the caller differentiates
+      // any such term itself)
+      if (up.g_area) CG_CUDA(c, cudaMemcpy(dLdA.data(), up.g_area, sizeof(double) * R, cudaMemcpyDefault));
+      for (int j = 0; j < R; ++j)
+        if (!is_finite(dLdA[j])) return fail(c, CG_EINVAL, "area adjoint %d is not finite", j);
+      if (up.g_xy) {
+        CG_CUDA(c, cudaMemcpyAsync(lamX, up.g_xy, sizeof(double2) * nv, cudaMemcpyDefault, s));
+      } else {
+        CG_CUDA(c, cudaMemsetAsync(lamX, 0, sizeof(double2) * nv, s));
+      }
+      CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dLdA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
+      cg::launch_shoelace_adjoint(a->X[K], c->next, c->prev, c->vreg, a->dLdA, lamX, nv, s);
+    } else {
+      for (int j = 0; j < R; ++j) {
+        dLdA[j] = 2.0 * res[j] / A1[j] - 2.0 * sres / sA1;
+        gV[j] = -2.0 * res[j] / V[j] + 2.0 * sres / sV;
+      }
+      CG_CUDA(c, cudaMemcpyAsync(a->dLdA, dLdA.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
+      // adjoint of the final vertices
+      cg::launch_loss_vertex_adjoint(a->X[K], a->X[0], c->next, c->prev, c->vreg, a->dLdA, lam, lamX, nv, s);
+    }
     double dsig_total = 0.0;
     for (int k = K - 1; k >= 0; --k) {
       // the iteration's spectrum, blur factors and integration
@@ -1921,6 +1952,39 @@ int cartogram_profile(cg_ctx* c, int reps, double* ms_out) {
   return c->mixed ? do_profile<float>(c, reps, ms_out) : do_profile<double>(c, reps, ms_out);
 }
 
+int cartogram_read_bandwidth(int64_t bytes, int passes, double* gbs_out) {
+  if (bytes < (1 << 20) || bytes > (int64_t)64 << 30 || (bytes & 15) || passes < 1 || passes > 1000 || !gbs_out)
+    return CG_EINVAL;
+  void* buf = nullptr;
+  float* sink = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = CG_OK;
+  if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess || cudaMalloc((void**)&sink, 64) != cudaSuccess) rc = CG_ENOMEM;
+  if (!rc && (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+    rc = CG_ECUDA;
+  if (!rc && cudaMemsetAsync(buf, 0, (size_t)bytes, s) != cudaSuccess) rc = CG_ECUDA;
+  float best = 1e30f;
+  for (int round = 0; round < 4 && !rc; ++round) {
+    cg::launch_read_bw(buf, (size_t)bytes, 1, sink, s);  // brings a buffer that fits in L2 there
+    cudaEventRecord(a, s);
+    cg::launch_read_bw(buf, (size_t)bytes, passes, sink, s);
+    cudaEventRecord(b, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) rc = CG_ECUDA;
+    else if (round > 0) best = std::min(best, ms);  // round 0 warms up
+  }
+  if (!rc) *gbs_out = (double)bytes * passes / (best * 1e-3) / 1e9;
+  if (b) cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (s) cudaStreamDestroy(s);
+  if (sink) cudaFree(sink);
+  if (buf) cudaFree(buf);
+  cudaGetLastError();
+  return rc;
+}
+
 int cartogram_autotune(cg_ctx* c, int reps, int* shapes_out, double* ms_out) {
   int r = check_ctx(c, false);
   if (r) return r;
@@ -2048,6 +2112,26 @@ int cartogram_iteration_gradient(cg_ctx* c, const double* values, double blur_wi
   if (!loss && !grad_values && !grad_blur) return fail(c, CG_EINVAL, "no output");
   return do_iteration_gradient(c, values, blur_width, lambda, iterations, replay, checkpoint, loss, grad_values,
                                grad_blur);
+}
+
+int cartogram_iteration_vjp(cg_ctx* c, const double* values, double blur_width, int iterations, int replay,
+                            int checkpoint, double* xy_out, double* area_out, const double* grad_xy,
+                            const double* grad_area, double* grad_values, double* grad_blur) {
+  int r = check_ctx(c, true);
+  if (r) return r;
+  if (c->mixed || c->opt.flow != CG_FLOW_DIFFUSION)
+    return fail(c, CG_EINVAL, "the gradient needs the FP64 path and the diffusion flow");
+  if (!values || !is_finite(blur_width) || blur_width < 0.0 || checkpoint < 1 || iterations < 1)
+    return fail(c, CG_EINVAL, "bad gradient arguments");
+  if (!xy_out && !area_out && !grad_values && !grad_blur) return fail(c, CG_EINVAL, "no output");
+  Upstream up;
+  up.custom = true;
+  up.g_xy = grad_xy;
+  up.g_area = grad_area;
+  up.xy_out = xy_out;
+  up.area_out = area_out;
+  return do_iteration_gradient(c, values, blur_width, 0.0, iterations, replay, checkpoint, nullptr, grad_values,
+                               grad_blur, up);
 }
 
 const char* cartogram_last_error(const cg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

@@ -143,6 +143,8 @@ void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T
                  V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
                  int use_cond, int blocks_per_sm, cudaStream_t s);
 int sm_count();
+// Read `bytes` (a multiple of 16) of p, `passes` times, bypassing L1.
+void launch_read_bw(const void* p, size_t bytes, int passes, float* sink, cudaStream_t s);
 
 // persistent integration kernel (persist.cu)
 constexpr int kIntegrateThreads = 256;

@@ -28,6 +28,29 @@ static inline int blocks_for(long long n, int threads, int cap) {
   return (int)b;
 }
 
+// Read bandwidth probe: every thread streams 16-byte loads that bypass L1 (ld.global.cg),
+// four independent loads in flight per iteration, `passes` times over the buffer; the
+// sum is kept live by a store that never happens.
+__global__ void __launch_bounds__(256) read_bw_kernel(const float4* __restrict__ p, long long n4, int passes,
+                                                      float* sink) {
+  float acc = 0.f;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int r = 0; r < passes; ++r) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+      const float4 a = __ldcg(p + i), b = __ldcg(p + i + stride);
+      const float4 c = __ldcg(p + i + 2 * stride), d = __ldcg(p + i + 3 * stride);
+      acc += (a.x + b.y) + (c.z + d.w);
+    }
+    for (; i < n4; i += stride) acc += __ldcg(p + i).x;
+  }
+  if (acc == -1.2345e-30f) sink[0] = acc;
+}
+
+void launch_read_bw(const void* p, size_t bytes, int passes, float* sink, cudaStream_t s) {
+  read_bw_kernel<<<sm_count() * 8, 256, 0, s>>>((const float4*)p, (long long)(bytes / 16), passes, sink);
+}
+
 template <typename T>
 void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
                  V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,

@@ -178,3 +178,80 @@ def test_gradient_through_several_iterations_against_gpu_differences():
             c.iteration_gradient(m.values, 1.0, LAM, replay=True, iterations=2)  # recorded with 3
         assert e.value.code == P.CG_ESTATE
         assert np.array_equal(c.vertices(), m.xy) and c.history_length() == 0
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_vjp_of_the_builtin_loss_gives_the_librarys_gradient(K):
+    """The configured loss written in torch on the mapped vertices X' and areas A' (plus its
+    direct dependence on the values through the target areas) gives, through the
+    vector-Jacobian product, the gradient of cartogram_iteration_gradient."""
+    import torch
+    m = synth.make_workload("voronoi16_64")
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64") as c:
+        c.set_map(m)
+        ref_loss, ref_gv, ref_gb = c.iteration_gradient(m.values, 1.0, LAM, iterations=K)
+        X0 = torch.tensor(m.xy, dtype=torch.float64)
+        v = torch.tensor(m.values, dtype=torch.float64, requires_grad=True)
+        b = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        xy, area = P.mapped_iterations(v, b, c, iterations=K)
+        target = v * area.sum() / v.sum()
+        loss = ((torch.log(area) - torch.log(target)) ** 2).sum() + LAM * ((xy - X0) ** 2).sum()
+        loss.backward()
+        assert np.array_equal(c.vertices(), m.xy) and c.history_length() == 0
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert np.max(np.abs(v.grad.numpy() - ref_gv)) <= 1e-11 * np.max(np.abs(ref_gv))
+    assert abs(float(b.grad) - ref_gb) <= 1e-11 * abs(ref_gb)
+
+
+def test_vjp_forward_is_the_mapped_map():
+    # one iteration's X' and A' are the vertices and areas cartogram_integrate produces
+    m = synth.make_workload("voronoi16_64")
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64") as c:
+        c.set_map(m)
+        xy, area = c.iteration_vjp(m.values, 1.0, grad=False)
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64", max_iter=1) as c:
+        c.set_map(m)
+        with pytest.raises(P.CartogramError):
+            c.integrate()  # one iteration does not converge this map
+        assert c.history_length() == 1
+        assert np.max(np.abs(c.vertices() - xy)) < 1e-10
+        err = c.area_errors()
+    target = m.values * area.sum() / m.values.sum()
+    assert np.max(np.abs((area / target - 1.0) - err)) < 1e-10
+
+
+def test_vjp_of_another_loss_matches_central_differences():
+    """A loss the library does not know: L = sum_i A'_i^2 / A0_i + sum_v w_v . X'_v with
+    fixed weights w, against differences of the same loss with the schedule replayed."""
+    m = synth.make_workload("voronoi16_64")
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=(m.n_vertices, 2))
+    with P.Cartogram(m.Lx, m.Ly, 1.0, precision="fp64") as c:
+        c.set_map(m)
+        xy, area = c.iteration_vjp(m.values, 1.0, iterations=2, grad=False)
+        a0 = area.copy()
+
+        def loss(v, b):
+            x, a = c.iteration_vjp(v, b, iterations=2, replay=True, grad=False)
+            return float(np.sum(a * a / a0) + np.sum(w * x))
+
+        _, _, gv, gb = c.iteration_vjp(m.values, 1.0, iterations=2, replay=True, checkpoint=3,
+                                       grad_xy=w, grad_area=2.0 * area / a0)
+        L0 = loss(m.values, 1.0)
+        for i in (0, 5, 11, 15):
+            h = 1e-6 * m.values[i]
+            vp, vm = m.values.copy(), m.values.copy()
+            vp[i] += h
+            vm[i] -= h
+            Lp, Lm = loss(vp, 1.0), loss(vm, 1.0)
+            diffs = [(Lp - Lm) / (2 * h), (Lp - L0) / h, (L0 - Lm) / h]
+            assert min(abs(d - gv[i]) for d in diffs) <= 1e-5 * max(abs(gv[i]), 1e-3 * np.max(np.abs(gv))), \
+                (i, diffs, gv[i])
+        h = 1e-6
+        Lp, Lm = loss(m.values, 1.0 + h), loss(m.values, 1.0 - h)
+        diffs = [(Lp - Lm) / (2 * h), (Lp - L0) / h, (L0 - Lm) / h]
+        assert min(abs(d - gb) for d in diffs) <= 1e-5 * abs(gb), (diffs, gb)
+        # only dL/dA' given (dL/dX' = 0): the area part of the product alone
+        _, _, gva, _ = c.iteration_vjp(m.values, 1.0, iterations=2, replay=True, grad_area=2.0 * area / a0)
+        _, _, gvx, _ = c.iteration_vjp(m.values, 1.0, iterations=2, replay=True, grad_xy=w)
+        assert np.max(np.abs(gva + gvx - gv)) <= 1e-12 * np.max(np.abs(gv))
