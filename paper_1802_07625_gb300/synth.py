@@ -365,7 +365,9 @@ def make_batch(frames: int | None = None, sizes=None) -> list:
     base = np.array([rng.lognormal(0.0, w["sigma"]) for _ in range(w["n"])])
     geometry = {}
     out = []
-    logv = np.log(base)
+    # the C library's log and exp, element by element (numpy's vectorised versions round
+    # differently on different hosts; these give the same bits on x86 and Arm)
+    logv = np.array([math.log(x) for x in base])
     for f in range(w["frames"]):
         L = w["sizes"][int(rng.uniform() * len(w["sizes"]))]
         if f > 0:
@@ -374,7 +376,7 @@ def make_batch(frames: int | None = None, sizes=None) -> list:
             lo, hi = L / 8.0, L - L / 8.0
             geometry[L] = voronoi_map(L, L, lo + unit * (hi - lo), lo, w["spacing"], base)
         g = geometry[L]
-        out.append(RegionMap(L, L, np.exp(logv), g.ring_offsets, g.ring_region, g.xy,
+        out.append(RegionMap(L, L, np.array([math.exp(x) for x in logv]), g.ring_offsets, g.ring_region, g.xy,
                              {"name": "batch_frame%d" % f, "blur": w["blur"], "precision": "mixed"}))
     return out
 

@@ -70,6 +70,59 @@ def test_batch_matches_single_runs():
             c.close()
 
 
+def test_batch_frames_match_oracle(orc):
+    """Every cartogram of a batch against the FP64 oracle (the batch's independent problems
+    are the paper's independent integrations, run side by side): the 64^2 map in FP64
+    (1e-9 grid units, identical step counts), the 128^2 map mixed (1e-3), and the first
+    128^2 and 256^2 frames of the batched workload in both precisions against the
+    oracle's stored converged results."""
+    from test_gpu_golden import MIXED_TOL, AREA_TOL, FP64_TOL, golden_map, load_golden
+    maps = _maps()[:2]
+    refs = [orc.cartogram(m, b, keep_grids=False) for _, m, b, _ in maps]
+    frames = []
+    for name in ("batch_frame_128", "batch_frame_256"):
+        g = load_golden(name)
+        frames.append((name, golden_map(name, g["meta"]), g))
+    carts = []
+    try:
+        for _, m, b, kw in maps:
+            carts.append(P.Cartogram(m.Lx, m.Ly, b, **kw))
+            carts[-1].set_map(m)
+        for _, m, g in frames:
+            for precision in ("fp64", "mixed"):
+                carts.append(P.Cartogram(m.Lx, m.Ly, g["meta"]["blur"], precision=precision))
+                carts[-1].set_map(m)
+        with P.Batch(carts) as batch:
+            stats, status = batch.integrate()
+        assert status == [P.CG_OK] * len(carts)
+        for (name, m, b, kw), ref, c, st in zip(maps, refs, carts, stats):
+            assert ref.converged and st.converged and st.iterations == ref.iterations, name
+            if kw["precision"] == "fp64":
+                assert (st.steps_accepted, st.steps_rejected) == (ref.steps_accepted, ref.steps_rejected)
+            tol = FP64_TOL if kw["precision"] == "fp64" else MIXED_TOL
+            assert np.max(np.abs(c.vertices() - ref.xy)) < tol, name
+            assert np.max(np.abs(c.area_errors() - ref.err)) < (FP64_TOL if tol == FP64_TOL else AREA_TOL)
+        k = len(maps)
+        for name, m, g in frames:
+            for precision in ("fp64", "mixed"):
+                c, st = carts[k], stats[k]
+                k += 1
+                meta = g["meta"]
+                assert st.converged and st.iterations == meta["iterations"], (name, precision)
+                xy = c.vertices()[g["vertex_index"]]
+                if precision == "fp64":
+                    assert (st.steps_accepted, st.steps_rejected) == \
+                        (meta["steps_accepted"], meta["steps_rejected"]), name
+                    assert np.max(np.abs(xy - g["xy"])) < FP64_TOL, name
+                    assert np.max(np.abs(c.area_errors() - g["err"])) < FP64_TOL, name
+                else:
+                    assert np.max(np.abs(xy - g["xy"])) < MIXED_TOL, name
+                    assert np.max(np.abs(c.area_errors() - g["err"])) < AREA_TOL, name
+    finally:
+        for c in carts:
+            c.close()
+
+
 def test_batch_reports_each_contexts_failure():
     m = synth.make_workload("voronoi16_64")
     good = P.Cartogram(m.Lx, m.Ly, 1.0, precision="mixed")
