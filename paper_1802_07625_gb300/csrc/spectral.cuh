@@ -106,23 +106,28 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   if (!__syncthreads_and(ok)) return false;
 
   const T kd = (T)(kPi / N);
-  const int P = N / 2 + 1;
-  for (int task = threadIdx.x; task < S * P; task += blockDim.x) {
-    const int s = task / P, m = task - s * P;
+  // N/2 tasks per row (no runtime integer division): task m > 0 packs the pair (m, N - m);
+  // task 0 packs m = 0 and the self-paired m = N/2
+  for (int task = threadIdx.x; task < S * (N / 2); task += blockDim.x) {
+    const int s = task >> (LOG2N - 1), m = task & (N / 2 - 1);
     const T* row = stage + s * N;
     C* x = buf + s * F::SSTRIDE;
     const T f = fyS[s];
-    const T am = row[m] * fx[m] * f;
     if (m == 0) {
-      x[F::pidx(0)] = mk2<T>(am, T(0));
+      x[F::pidx(0)] = mk2<T>(row[0] * fx[0] * f, T(0));
+      constexpr int h = N / 2;
+      const T ah = row[h] * fx[h] * f;
+      const T bh = -kd * (T)h * ah;
+      x[F::pidx(h)] = cmul(E[h], mk2<T>((ah + bh) * T(0.5), (bh - ah) * T(0.5)));
       continue;
     }
+    const T am = row[m] * fx[m] * f;
     const T bm = -kd * (T)m * am;
     const int q = N - m;
     const T aq = row[q] * fx[q] * f;
     const T bq = -kd * (T)q * aq;
     x[F::pidx(m)] = cmul(E[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
-    if (q != m) x[F::pidx(q)] = cmul(E[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+    x[F::pidx(q)] = cmul(E[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
   }
   __syncthreads();
   block_fft<T, LOG2N, true>(buf, S, W);
@@ -224,22 +229,25 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
   if (!__syncthreads_and(ok)) return false;
 
   const int Wp = Wc / 2;
-  const int P = N / 2 + 1;
   const T kd = (T)(kPi / N);
-  for (int task = threadIdx.x; task < P * Wp; task += blockDim.x) {
-    const int p = task / P, m = task - p * P;
+  // N/2 tasks per column pair (no runtime integer division): task m > 0 packs the pair
+  // (m, N - m); task 0 packs m = 0 and then (second round) the self-paired m = N/2
+  for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
+    const int p = task >> (LOG2N - 1);
+    int m = task & (N / 2 - 1);
     const C* s0 = stage + (2 * p) * N;
     const C* s1 = s0 + N;
-    const C Am0 = s0[m], Am1 = s1[m];
     C* x0 = buf + (2 * p) * F::SSTRIDE;
     C* x1 = x0 + F::SSTRIDE;
     C* x2 = buf + (Wc + p) * F::SSTRIDE;
     if (m == 0) {
-      x0[F::pidx(0)] = mk2<T>(Am0.x, T(0));
-      x1[F::pidx(0)] = mk2<T>(Am1.x, T(0));
-      x2[F::pidx(0)] = mk2<T>(Am0.y, Am1.y);
-      continue;
+      const C A00 = s0[0], A01 = s1[0];
+      x0[F::pidx(0)] = mk2<T>(A00.x, T(0));
+      x1[F::pidx(0)] = mk2<T>(A01.x, T(0));
+      x2[F::pidx(0)] = mk2<T>(A00.y, A01.y);
+      m = N / 2;
     }
+    const C Am0 = s0[m], Am1 = s1[m];
     const int q = N - m;
     const C Aq0 = s0[q], Aq1 = s1[q];
     const C em = E[m], eq = E[q];
