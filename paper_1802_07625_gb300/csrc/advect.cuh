@@ -61,53 +61,13 @@ template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Accept / reject the attempt whose reductions are in st, update t, h, buffers and
-// status (one thread). The cap h * max|v| <= cfl uses the field at the accepted time.
-__device__ __forceinline__ void control_step(DevState* st, const StepParams& sp,
-                                             cudaGraphConditionalHandle handle, int use_cond) {
-  const double e = sqrt(__longlong_as_double((long long)st->err2_bits));
-  const double vmax_new = sqrt(__longlong_as_double((long long)st->vmax2_bits));
-  const double dev_new = __longlong_as_double((long long)st->dev_bits);
-  int status = kRunning;
-  double h = st->h;
-  if (st->bad) {
-    status = kStepFail;
-  } else if (e <= sp.atol) {
-    if (sp.sched) {
-      sp.sched[2 * st->accepted] = st->t;
-      sp.sched[2 * st->accepted + 1] = h;
-    }
-    st->parity ^= 1;
-    st->t += h;
-    st->accepted += 1;
-    st->vmax = vmax_new;
-    if (dev_new <= sp.rho_tol) status = kDone;
-    else h *= sp.grow;
-  } else {
-    st->rejected += 1;
-    h *= sp.shrink;
-  }
-  if (status == kRunning) {
-    if (st->accepted + st->rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
-    else if (deadline_passed(sp)) status = kTimeout;
-    else if (st->vmax > 0.0 && h * st->vmax > sp.cfl) h = sp.cfl / st->vmax;
-  }
-  st->h = h;
-  st->status = status;
-  st->err2_bits = 0;
-  st->vmax2_bits = 0;
-  st->dev_bits = 0;
-  st->ticket = 0;
-  st->bad = 0;
-  if (status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
-}
-
 // End of the attempted step t -> t1 of the linear-equalisation flow (the step that
 // reaches t = 1 ends exactly there).
 __device__ __forceinline__ double linear_t1(double t, double h) { return (t + h >= 1.0) ? 1.0 : t + h; }
 
-// Controller of the linear-equalisation flow: accept / reject as above, the next step
-// capped by cfl / max|v| and by 1 - t; done once an accepted step reaches t = 1.
+// Controller of the linear-equalisation flow: accept / reject as for the diffusion flow
+// (loop_decide), the next step capped by cfl / max|v| and by 1 - t; done once an
+// accepted step reaches t = 1.
 __device__ __forceinline__ void control_linear(DevState* st, const StepParams& sp,
                                                cudaGraphConditionalHandle handle, int use_cond) {
   const double e = sqrt(__longlong_as_double((long long)st->err2_bits));
@@ -181,10 +141,13 @@ __device__ __forceinline__ T heun_pairs(const V2<T>* __restrict__ vcur, const V2
   return e2;
 }
 
-// One Heun step of every grid point. Step modes: buffers by parity, h from the state,
-// and the last block to finish runs the controller (kModeStep: diffusion flow;
-// kModeLinear: linear-equalisation flow, the attempt ending at min(t + h, 1)). Fixed
-// mode (single step on explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0,
+// One Heun step of every grid point. Diffusion-flow step modes (kModeStep,
+// kModeStepOdd): buffers by parity and h from the attempt's state, which its first pass
+// decided and stored; the step error goes to the attempt's slot, on which the next
+// attempt's first pass decides.
+// kModeLinear (linear-equalisation flow, the attempt ending at min(t + h, 1)): buffers
+// and h from the state, and the last block to finish runs the controller. Fixed mode
+// (single step on explicit buffers): vcur = vbuf0, vnew = vbuf1, din = dbuf0,
 // dout = dbuf1, step h.
 template <typename T>
 __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
@@ -194,33 +157,45 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
                                                     cudaGraphConditionalHandle handle, int use_cond) {
   __shared__ unsigned long long s_err2;
   __shared__ unsigned int s_warps;
+  __shared__ int s_run, s_par;
+  __shared__ double s_h;
+  const bool pipe = is_step_mode(mode);
   if (threadIdx.x == 0) {
     s_err2 = 0ull;
     s_warps = 0u;
   }
-  __syncthreads();
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the fields of the previous kernel
-  const bool step = mode == kModeStep || mode == kModeLinear;
+  if (pipe && threadIdx.x == 0) {
+    // the attempt's state, as its first pass decided and stored it
+    const LoopSlot* q = &st->ls[step_slot(mode)];
+    s_run = __ldcg(&q->status) == kRunning;
+    s_par = __ldcg(&q->parity);
+    s_h = __ldcg(&q->h);
+  }
+  __syncthreads();
+  const bool step = mode == kModeLinear;
   if (step && st->status != kRunning) return;
+  if (pipe && !s_run) return;
   const V2<T>* vcur = vbuf0;
   const V2<T>* vnew = vbuf1;
   const V2<T>* din = dbuf0;
   V2<T>* dout = dbuf1;
   double hd = h_fixed;
-  if (step) {
-    const int par = st->parity;
+  if (step || pipe) {
+    const int par = pipe ? s_par : st->parity;
     vcur = par ? vbuf1 : vbuf0;
     vnew = par ? vbuf0 : vbuf1;
     din = par ? dbuf1 : dbuf0;
     dout = par ? dbuf0 : dbuf1;
-    hd = mode == kModeLinear ? linear_t1(st->t, st->h) - st->t : st->h;
+    hd = pipe ? s_h : linear_t1(st->t, st->h) - st->t;
   }
   T e2 = heun_pairs<T>(vcur, vnew, din, dout, Lx, Ly, log2Lx, hd,
                        blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // Block reduction without a block-wide barrier: each warp folds its maximum into
   // shared memory; the last warp of the block to arrive publishes the block maximum
-  // and takes the block's ticket; the last block runs the controller.
+  // (in the linear flow it also takes the block's ticket, and the last block runs the
+  // controller).
   e2 = warp_max(e2);
   if ((threadIdx.x & 31) == 0) {
     atomicMax(&s_err2, (unsigned long long)__double_as_longlong((double)e2));
@@ -229,14 +204,21 @@ __global__ void __launch_bounds__(256) heun_kernel(DevState* st, StepParams sp,
     if (arrived == (blockDim.x >> 5) - 1) {
       __threadfence_block();
       const double bm = __longlong_as_double((long long)atomicOr(&s_err2, 0ull));
+      if (pipe) {
+        LoopSlot* q = &st->ls[step_slot(mode)];
+        atomic_max_nonneg(&q->err2_bits, bm);
+        // one clock reading per attempt, taken into the slot so that every kernel of
+        // the next attempt decides the same
+        if (blockIdx.x == 0 && deadline_passed(sp)) atomicOr(&q->bad, 2);
+        return;
+      }
       atomic_max_nonneg(&st->err2_bits, bm);
       if (step) {
         __threadfence();
         const unsigned int t = atomicAdd(&st->ticket, 1u);
         if (t == gridDim.x - 1) {
           __threadfence();
-          if (mode == kModeLinear) control_linear(st, sp, handle, use_cond);
-          else control_step(st, sp, handle, use_cond);
+          control_linear(st, sp, handle, use_cond);
         }
       }
     }
@@ -259,6 +241,7 @@ static __global__ void init_state_kernel(DevState* st, StepParams sp) {
   st->bad = 0;
   st->body_iters = 0;
   st->t_start_ns = global_ns();
+  st->sp = sp;
 }
 
 // After the field at t = 0: stop at once if the density is already equal, else cap
@@ -280,6 +263,15 @@ static __global__ void init_finish_kernel(DevState* st, StepParams sp, cudaGraph
   st->dev_bits = 0;
   st->ticket = 0;
   st->bad = 0;
+  // the diffusion flow's step loop starts from slot 1 (the first attempt has parity 0)
+  LoopSlot z = {};
+  z.t = st->t;
+  z.vmax = vmax;
+  z.h = h;
+  z.parity = st->parity;
+  z.status = status;
+  st->ls[1] = z;
+  st->ls[0] = LoopSlot{};
   // set either way: inside an outer loop the same step loop runs once per iteration
   if (use_cond) cudaGraphSetConditional(handle, status == kRunning ? 1u : 0u);
 }

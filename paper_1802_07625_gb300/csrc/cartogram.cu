@@ -343,13 +343,15 @@ void enqueue_init(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStr
   cg::launch_init_finish(c->st, sp, h, use_cond, s);
 }
 
+// Attempt k of a run of attempts that starts at an even attempt (its parity selects the
+// state slot of the step loop).
 template <typename T>
-void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s, int k) {
   const StepParams sp = step_params(c);
-  enqueue_field<T>(c, cg::kModeStep, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s, h,
-                   use_cond);
+  const int mode = (k & 1) ? cg::kModeStepOdd : cg::kModeStep;
+  enqueue_field<T>(c, mode, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s, h, use_cond);
   cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeStep, 0.0, h,
+                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, mode, 0.0, h,
                      use_cond, c->tune.heun_bps, s);
 }
 
@@ -477,6 +479,7 @@ int do_autotune(cg_ctx* c, int reps) {
 // attempts per body of the step loop's WHILE node (measured at 1024^2: 8 takes 1 % less
 // time than 4, 16 no less than 8; the attempts after the last one return at once)
 constexpr int kGraphUnroll = 8;
+static_assert(kGraphUnroll % 2 == 0, "a body starts at an even attempt: the step loop state alternates slots");
 
 // ---- graph capture ----------------------------------------------------------
 
@@ -531,7 +534,7 @@ cudaError_t capture_integration(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cud
   e = capture_while(cs, bs, h, [&](cudaStream_t s) {
     for (int k = 0; k < kGraphUnroll; ++k) {
       if (lin) enqueue_body_linear<T>(c, h, 1, s);
-      else enqueue_body<T>(c, h, 1, s);
+      else enqueue_body<T>(c, h, 1, s, k);
     }
     return cudaGetLastError();
   });
@@ -680,11 +683,11 @@ int run_integration_host(cg_ctx* c) {
   const bool lin = c->opt.flow == CG_FLOW_LINEAR;
   if (lin) enqueue_init_linear<T>(c, 0, 0, s);
   else enqueue_init<T>(c, 0, 0, s);
-  const int chunk = 8;
+  const int chunk = 8;  // even: each chunk starts at an even attempt
   for (long long done = 0; done < (long long)c->opt.max_steps + chunk; done += chunk) {
     for (int k = 0; k < chunk; ++k) {
       if (lin) enqueue_body_linear<T>(c, 0, 0, s);
-      else enqueue_body<T>(c, 0, 0, s);
+      else enqueue_body<T>(c, 0, 0, s, k);
     }
     cg::launch_collect(c->st, c->info, s);
     CG_CUDA(c, cudaMemcpyAsync(c->info_h, c->info, sizeof(IterInfo), cudaMemcpyDeviceToHost, s));

@@ -27,6 +27,33 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Step-control constants passed by value to the kernels that need them.
+struct StepParams {
+  double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
+  long long max_steps;
+  double* sched;  // if not null: (t, h) of every accepted step, [max_steps][2]
+  // if not null: device-clock deadline of the call in ns (0: none), written at its start
+  const unsigned long long* deadline;
+};
+
+// Step state of the diffusion flow's step loop (graph and host-driven modes), kept in
+// two slots by attempt parity: slot b holds the state at the start of an attempt of
+// parity b and that attempt's reductions. Every block of the first pass of attempt n
+// computes the controller's decision on attempt n - 1 from slot (n - 1) & 1 (so the
+// decision needs no serial tail at the end of the step kernel); its block 0 stores the
+// result into slot n & 1, which pass 2 and the step kernel of attempt n read. One slot
+// per 128-byte line.
+struct __align__(128) LoopSlot {
+  double t, h, vmax;
+  long long accepted, rejected;
+  int parity, status;
+  int pending;  // an attempt ran from this state: its reductions are below
+  int bad;      // bit 0: the new field's density was not positive; bit 1: deadline passed
+  unsigned long long err2_bits;   // max ||r_corr - r_pred||^2
+  unsigned long long vmax2_bits;  // max |v|^2 of the new field
+  unsigned long long dev_bits;    // max |rho/rho_bar - 1| of the new field
+};
+
 // Device-resident state of one integration (written by the step controller).
 struct DevState {
   double t;          // accepted diffusion time
@@ -45,10 +72,16 @@ struct DevState {
   unsigned int body_iters;        // step-loop iterations started (termination guard)
   unsigned int pad;
   unsigned long long t_start_ns;  // device clock at the start of the integration
+  StepParams sp;                  // the integration's constants (written at its start)
+  LoopSlot ls[2];                 // the step loop's state by attempt parity
 };
 // What a field or step kernel works on: the field at t (start of an integration),
 // the attempt at t + h inside the step loop, or explicit buffers and times.
-enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2, kModeFlux = 3, kModeLinear = 4 };
+enum FieldMode { kModeInit = 0, kModeStep = 1, kModeFixed = 2, kModeFlux = 3, kModeLinear = 4, kModeStepOdd = 5 };
+// kModeStep / kModeStepOdd: an attempt of the diffusion flow's step loop of even / odd
+// parity (its state in DevState::ls).
+__host__ __device__ inline bool is_step_mode(int mode) { return mode == kModeStep || mode == kModeStepOdd; }
+__host__ __device__ inline int step_slot(int mode) { return mode == kModeStepOdd ? 1 : 0; }
 // kModeFlux: explicit buffers like kModeFixed, and pass 2 writes -grad instead of the
 // velocity (the flux J = -grad Phi of the linear-equalisation flow).
 // kModeLinear: a step-loop attempt of the linear-equalisation flow (buffers by parity,
@@ -115,20 +148,98 @@ struct StepAcc {
   unsigned int pad;
 };
 
-// Step-control constants passed by value to the kernels that need them.
-struct StepParams {
-  double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
-  long long max_steps;
-  double* sched;  // if not null: (t, h) of every accepted step, [max_steps][2]
-  // if not null: device-clock deadline of the call in ns (0: none), written at its start
-  const unsigned long long* deadline;
-};
 
 // The call's deadline has passed (read by the step controllers after every attempt).
 __device__ __forceinline__ bool deadline_passed(const StepParams& sp) {
   if (!sp.deadline) return false;
   const unsigned long long d = *(volatile const unsigned long long*)sp.deadline;
   return d != 0ull && global_ns() > d;
+}
+
+// A loop slot as written by other blocks or earlier kernels: every field from L2.
+__device__ __forceinline__ LoopSlot load_slot(const LoopSlot* q) {
+  LoopSlot r;
+  r.t = __ldcg(&q->t);
+  r.h = __ldcg(&q->h);
+  r.vmax = __ldcg(&q->vmax);
+  r.accepted = __ldcg(&q->accepted);
+  r.rejected = __ldcg(&q->rejected);
+  r.parity = __ldcg(&q->parity);
+  r.status = __ldcg(&q->status);
+  r.pending = __ldcg(&q->pending);
+  r.bad = __ldcg(&q->bad);
+  r.err2_bits = __ldcg(&q->err2_bits);
+  r.vmax2_bits = __ldcg(&q->vmax2_bits);
+  r.dev_bits = __ldcg(&q->dev_bits);
+  return r;
+}
+
+// The integration's constants as stored in its state, from L2.
+__device__ __forceinline__ StepParams load_sp(const DevState* st) {
+  StepParams r;
+  r.dt0 = __ldcg(&st->sp.dt0);
+  r.atol = __ldcg(&st->sp.atol);
+  r.grow = __ldcg(&st->sp.grow);
+  r.shrink = __ldcg(&st->sp.shrink);
+  r.cfl = __ldcg(&st->sp.cfl);
+  r.rho_tol = __ldcg(&st->sp.rho_tol);
+  r.h_min = __ldcg(&st->sp.h_min);
+  r.max_steps = __ldcg(&st->sp.max_steps);
+  r.sched = (double*)__ldcg((const long long*)&st->sp.sched);
+  r.deadline = (const unsigned long long*)__ldcg((const long long*)&st->sp.deadline);
+  return r;
+}
+
+// The step controller (the paper's predictor-corrector "automatically adapts the size
+// of the next time step") on the attempt run from state p, whose reductions p holds:
+// accept if max ||r_corr - r_pred|| <= atol (t += h; the integration ends once
+// max |rho/rho_bar - 1| <= rho_tol, else h *= grow), otherwise h *= shrink; the step
+// budget or a collapsed step end it with a failure, a passed deadline with a time-out;
+// the next step is capped by h * max|v| <= cfl with the field at the accepted time.
+// Returns the state at the start of the next attempt (reductions cleared). Pure: every
+// kernel of that attempt computes it from the same slot and gets the same answer.
+// `record`: store each accepted (t, h) into sp.sched (one caller only).
+__device__ __forceinline__ LoopSlot loop_decide(const LoopSlot& p, const StepParams& sp, bool record) {
+  LoopSlot n = p;
+  n.bad = 0;
+  n.err2_bits = 0;
+  n.vmax2_bits = 0;
+  n.dev_bits = 0;
+  n.pending = 0;
+  if (p.status != kRunning) return n;
+  n.pending = 1;
+  if (!p.pending) return n;  // the integration's first attempt
+  const double e = sqrt(__longlong_as_double((long long)p.err2_bits));
+  const double vmax_new = sqrt(__longlong_as_double((long long)p.vmax2_bits));
+  const double dev_new = __longlong_as_double((long long)p.dev_bits);
+  int status = kRunning;
+  double h = p.h;
+  if (p.bad & 1) {
+    status = kStepFail;
+  } else if (e <= sp.atol) {
+    if (record && sp.sched) {
+      sp.sched[2 * p.accepted] = p.t;
+      sp.sched[2 * p.accepted + 1] = h;
+    }
+    n.parity = p.parity ^ 1;
+    n.t = p.t + h;
+    n.accepted = p.accepted + 1;
+    n.vmax = vmax_new;
+    if (dev_new <= sp.rho_tol) status = kDone;
+    else h *= sp.grow;
+  } else {
+    n.rejected = p.rejected + 1;
+    h *= sp.shrink;
+  }
+  if (status == kRunning) {
+    if (n.accepted + n.rejected >= sp.max_steps || !(h > sp.h_min)) status = kStepFail;
+    else if (p.bad & 2) status = kTimeout;
+    else if (n.vmax > 0.0 && h * n.vmax > sp.cfl) h = sp.cfl / n.vmax;
+  }
+  n.h = h;
+  n.status = status;
+  if (status != kRunning) n.pending = 0;
+  return n;
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {

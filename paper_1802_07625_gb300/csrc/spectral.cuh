@@ -339,25 +339,70 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   p1_issue<T, LOG2N>(spec, Wg, Eg, S, blockIdx.x * S, smem_raw, &bar);
+  __shared__ double s_tau;
+  __shared__ int s_run;
   pdl_wait();
   double tau = tau_fixed;
-  if (mode == kModeStep && blockIdx.x == 0 && threadIdx.x == 0) {
-    // first kernel of a loop iteration: end the loop if the integration is over or
-    // has run more iterations than the controller allows
-    const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
-    if (st->status == kRunning && it > max_body) st->status = kStepFail;
-    if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
-  }
-  if (mode == kModeInit || mode == kModeStep) {
+  if (is_step_mode(mode)) {
+    // first kernel of an attempt: the controller's decision on the previous attempt
+    // (every block computes it; block 0 stores it as this attempt's state, ends the
+    // loop when the integration is over or has run more attempts than it allows, and
+    // then also commits the final state)
+    if (threadIdx.x == 0) {
+      const int b = step_slot(mode);
+      LoopSlot n = loop_decide(load_slot(&st->ls[b ^ 1]), load_sp(st), blockIdx.x == 0);
+      if (blockIdx.x == 0) {
+        const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
+        if (n.status == kRunning && it > max_body) {
+          n.status = kStepFail;
+          n.pending = 0;
+        }
+        // every field but `bad`, which another block may already have flagged (it is
+        // zero in a slot whose attempt was followed by another)
+        LoopSlot* q = &st->ls[b];
+        q->t = n.t;
+        q->h = n.h;
+        q->vmax = n.vmax;
+        q->accepted = n.accepted;
+        q->rejected = n.rejected;
+        q->parity = n.parity;
+        q->status = n.status;
+        q->pending = n.pending;
+        q->err2_bits = 0;
+        q->vmax2_bits = 0;
+        q->dev_bits = 0;
+        if (n.status != kRunning) {
+          st->t = n.t;
+          st->h = n.h;
+          st->vmax = n.vmax;
+          st->accepted = n.accepted;
+          st->rejected = n.rejected;
+          st->parity = n.parity;
+          st->status = n.status;
+          if (use_cond) cudaGraphSetConditional(handle, 0);
+        }
+      }
+      s_run = n.status == kRunning;
+      s_tau = n.t + n.h;
+    }
+    __syncthreads();
+    if (!s_run) {
+      mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
+      return;
+    }
+    tau = s_tau;
+  } else if (mode == kModeInit) {
     if (st->status != kRunning) {
       mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
       return;
     }
-    tau = (mode == kModeInit) ? st->t : st->t + st->h;
+    tau = st->t;
   }
   uint32_t ph = 0;
-  if (!p1_finish<T, LOG2N>(ABt, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) && threadIdx.x == 0)
-    st->bad = 2;
+  if (!p1_finish<T, LOG2N>(ABt, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) && threadIdx.x == 0) {
+    if (is_step_mode(mode)) atomicOr(&st->ls[step_slot(mode)].bad, 1);
+    else st->bad = 2;
+  }
   pdl_trigger();
 }
 
@@ -375,25 +420,46 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
   __syncthreads();
   const int c0 = blockIdx.x * Wc;
   p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem_raw, &bar);
+  __shared__ int s_run, s_par;
+  const bool step = is_step_mode(mode);
   pdl_wait();
   p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem_raw, &bar);
-  if ((mode == kModeInit || mode == kModeStep) && st->status != kRunning) {
+  if (step) {
+    // the attempt's state, as pass 1 decided and stored it (read while the copies land)
+    if (threadIdx.x == 0) {
+      const LoopSlot* q = &st->ls[step_slot(mode)];
+      s_run = __ldcg(&q->status) == kRunning;
+      s_par = __ldcg(&q->parity);
+    }
+    __syncthreads();
+  }
+  if ((step && !s_run) || (mode == kModeInit && st->status != kRunning)) {
     mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
     return;
   }
   V2<T>* out = vbuf0;
-  if (mode == kModeStep) out = st->parity ? vbuf0 : vbuf1;
+  if (step) out = s_par ? vbuf0 : vbuf1;
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
   uint32_t ph = 0;
   FieldRed<T> r;
   if (!p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux)) {
-    if (threadIdx.x == 0) st->bad = 2;
+    if (threadIdx.x == 0) {
+      if (step) atomicOr(&st->ls[step_slot(mode)].bad, 1);
+      else st->bad = 2;
+    }
     return;
   }
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&st->dev_bits, (double)r.dev);
-    atomic_max_nonneg(&st->vmax2_bits, (double)r.v2max);
-    if (r.bad) st->bad = 1;
+    if (step) {
+      LoopSlot* q = &st->ls[step_slot(mode)];
+      atomic_max_nonneg(&q->dev_bits, (double)r.dev);
+      atomic_max_nonneg(&q->vmax2_bits, (double)r.v2max);
+      if (r.bad) atomicOr(&q->bad, 1);
+    } else {
+      atomic_max_nonneg(&st->dev_bits, (double)r.dev);
+      atomic_max_nonneg(&st->vmax2_bits, (double)r.v2max);
+      if (r.bad) st->bad = 1;
+    }
   }
   pdl_trigger();
 }
