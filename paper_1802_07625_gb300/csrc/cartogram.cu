@@ -453,7 +453,9 @@ int do_autotune(cg_ctx* c, int reps) {
     if (ms < best_ms[1]) { best_ms[1] = ms; best.cols = W; }
   }
   const StepParams sp = step_params(c);
-  for (int bps = 2; bps <= 32; bps *= 2) {
+  // resident blocks per SM of the step kernel: its 256-thread blocks fit five to an SM at
+  // 48 registers, so the counts around that are tried too
+  for (int bps : {2, 3, 4, 5, 6, 8, 16}) {
     double ms;
     if ((r = timeit([&] {
            cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
