@@ -30,8 +30,8 @@ __device__ __forceinline__ V2<T> interp_v(const V2<T>* __restrict__ v, int Lx, i
     // a cell between four grid points (almost every point): no clamping, no wall factor
     const V2<T>* r0 = v + (iy * Lx + ix);  // Lx * Ly < 2^31
     const V2<T>* r1 = r0 + Lx;
-    const V2<T> a = r0[0], b = r0[1];
-    const V2<T> c = r1[0], d = r1[1];
+    const V2<T> a = __ldg(r0), b = __ldg(r0 + 1);
+    const V2<T> c = __ldg(r1), d = __ldg(r1 + 1);
     return mk2<T>(gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x),
                   gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y));
   }
@@ -40,8 +40,8 @@ __device__ __forceinline__ V2<T> interp_v(const V2<T>* __restrict__ v, int Lx, i
   const int i0 = min(max(ix, 0), Lx - 1), i1 = min(max(ix + 1, 0), Lx - 1);
   const int j0 = min(max(iy, 0), Ly - 1), j1 = min(max(iy + 1, 0), Ly - 1);
   const int r0 = j0 * Lx, r1 = j1 * Lx;
-  const V2<T> a = v[r0 + i0], b = v[r0 + i1];
-  const V2<T> c = v[r1 + i0], d = v[r1 + i1];
+  const V2<T> a = __ldg(v + r0 + i0), b = __ldg(v + r0 + i1);
+  const V2<T> c = __ldg(v + r1 + i0), d = __ldg(v + r1 + i1);
   T ux = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
   T uy = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
   const T x = (T)i + T(0.5) + dx, y = (T)j + T(0.5) + dy;
