@@ -16,6 +16,7 @@ single cartogram has no data-parallel split worth a collective); value sums the
 updates of all ranks over the slowest rank's time.
 
 Besides the headline, the JSON line carries: the FP64 GPU path on the same workload, the
+compensated mixed precision (second transform pass in float-float arithmetic), the
 linear-equalisation flow, the batched workload (64 frames, split between the ranks), the
 differentiation workload (512^2, FP64 gradient), the Tissot and polygon-level distortion
 of the converged map, live per-kernel timings with the roofline of the dominant step
@@ -531,9 +532,8 @@ def run_ours(args):
     e2e_value = replica_throughput(world, e2e_updates, e2e_dt)
 
     # the plain FP64 GPU path on the same workload (one converged cartogram)
-    fp64 = None
-    if args.fp64_steps > 0:
-        f = P.Cartogram(m.Lx, m.Ly, blur, precision="fp64", max_iter=100, use_graph=args.loop_mode)
+    def other_precision(precision, steps):
+        f = P.Cartogram(m.Lx, m.Ly, blur, precision=precision, max_iter=100, use_graph=args.loop_mode)
         f.set_stream(stream)
         P.cartogram_set_regions(f.ctx, d_vals, d_off, d_reg, d_xy)
         f._map = P._Map(m.n_regions, m.n_vertices)
@@ -541,7 +541,7 @@ def run_ours(args):
         f.integrate()
         torch.cuda.synchronize()
         fms, fatt = 0.0, 0
-        for _ in range(args.fp64_steps):
+        for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f.reset()
             a.record(stream)
@@ -550,10 +550,16 @@ def run_ours(args):
             torch.cuda.synchronize()
             fms += a.elapsed_time(b)
             fatt += fs.steps_accepted + fs.steps_rejected
-        fp64 = {"updates_per_s": fatt * m.Lx * m.Ly / (fms / 1e3), "s_per_cartogram": fms / 1e3 / args.fp64_steps,
+        f.close()
+        return {"updates_per_s": fatt * m.Lx * m.Ly / (fms / 1e3), "s_per_cartogram": fms / 1e3 / steps,
                 "iterations": fs.iterations, "attempted_steps": fs.steps_accepted + fs.steps_rejected,
                 "max_area_error": fs.max_area_error}
-        f.close()
+
+    fp64 = other_precision("fp64", args.fp64_steps) if args.fp64_steps > 0 else None
+    # pass 2 in float-float arithmetic: what the compensated mixed precision costs
+    mixed_ff = other_precision("mixed_ff", args.ff_steps) if args.ff_steps > 0 else None
+    if mixed_ff:
+        mixed_ff["precision"] = "mixed, second transform pass in float-float arithmetic"
 
     # the paper's linear-equalisation flow on the same workload (one transform pair per
     # integration, one fused kernel per attempted step)
@@ -618,6 +624,7 @@ def run_ours(args):
             "accepted_steps_per_cartogram": last.steps_accepted, "max_area_error": last.max_area_error,
             "accepted_updates_per_s": value * last.steps_accepted / max(1, last.steps_accepted + last.steps_rejected),
             "fp64_gpu": fp64,
+            "mixed_ff": mixed_ff,
             "mixed_vs_fp64_speedup": (fp64["s_per_cartogram"] / s_per_cartogram) if fp64 else None,
             "linear_flow": linear,
             "distortion": dist,
@@ -656,6 +663,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--ff-steps", type=int, default=2,
+                    help="cartograms timed with pass 2 in float-float arithmetic (0: skip)")
     ap.add_argument("--ref-attempts", type=int, default=20,
                     help="oracle attempted steps per timed step of --impl reference")
     ap.add_argument("--cpu-steps", type=int, default=60)

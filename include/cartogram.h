@@ -55,9 +55,14 @@ enum {
 
 enum {
     CG_PRECISION_FP64 = 0,   /* every field, transform and position in FP64 */
-    CG_PRECISION_MIXED = 1   /* transforms, fields and displacements in FP32; rasterisation,
+    CG_PRECISION_MIXED = 1,  /* transforms, fields and displacements in FP32; rasterisation,
                                 forward transform, polygon areas, the convergence test and
                                 the step-control arithmetic in FP64 */
+    CG_PRECISION_MIXED_FF = 2 /* as CG_PRECISION_MIXED, with the second inverse transform pass
+                                (the column transforms that form rho, grad rho and v) in
+                                float-float arithmetic (about 48 bits on FP32 hardware): FP32
+                                rounding at the scale of a column's largest densities no longer
+                                swamps regions far below them. Not for use_graph = 2 (runs as 1) */
 };
 
 enum {
@@ -70,7 +75,7 @@ enum {
 
 /* Tuning of the method. cartogram_default_options() fills the defaults noted here. */
 typedef struct cg_options {
-    int precision;      /* CG_PRECISION_FP64 (default) or CG_PRECISION_MIXED */
+    int precision;      /* CG_PRECISION_FP64 (default), CG_PRECISION_MIXED or CG_PRECISION_MIXED_FF */
     double dt0;         /* first trial step, diffusion time with D = 1 (1e-2) */
     double atol;        /* accept a step when max ||r_corr - r_pred|| <= atol cells (1e-2) */
     double grow;        /* step factor after an accepted step (1.2) */

@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_ENOCONVERGE", "CG_EFOLD", "CG_ESTEPFAIL", "CG_ETIMEOUT",
-    "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CG_FLOW_DIFFUSION",
+    "CG_ESTATE", "CG_PRECISION_FP64", "CG_PRECISION_MIXED", "CG_PRECISION_MIXED_FF", "CG_FLOW_DIFFUSION",
     "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
@@ -34,7 +34,7 @@ __all__ = [
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOCONVERGE, CG_EFOLD, CG_ESTEPFAIL = 0, -1, -2, -3, -4, -5, -6
 CG_ETIMEOUT, CG_ESTATE = -7, -8
-CG_PRECISION_FP64, CG_PRECISION_MIXED = 0, 1
+CG_PRECISION_FP64, CG_PRECISION_MIXED, CG_PRECISION_MIXED_FF = 0, 1, 2
 CG_FLOW_DIFFUSION, CG_FLOW_LINEAR = 0, 1
 
 _ERRNAMES = {0: "CG_OK", -1: "CG_EINVAL", -2: "CG_ENOMEM", -3: "CG_ECUDA", -4: "CG_ENOCONVERGE",
@@ -451,7 +451,10 @@ class Cartogram:
 
     def __init__(self, Lx, Ly, blur_width=0.0, precision="fp64", flow="diffusion", **options):
         o = cartogram_default_options()
-        o.precision = CG_PRECISION_MIXED if precision == "mixed" else CG_PRECISION_FP64
+        precisions = {"fp64": CG_PRECISION_FP64, "mixed": CG_PRECISION_MIXED, "mixed_ff": CG_PRECISION_MIXED_FF}
+        if precision not in precisions:
+            raise ValueError("precision must be one of %s" % sorted(precisions))
+        o.precision = precisions[precision]
         if flow not in ("diffusion", "linear"):
             raise ValueError("flow must be 'diffusion' or 'linear'")
         o.flow = CG_FLOW_LINEAR if flow == "linear" else CG_FLOW_DIFFUSION

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcartogram.so")
-UNITS = ["cartogram.cu", "spectral_f32.cu", "spectral_f64.cu", "step.cu", "persist.cu", "noalloc.cu"]
+UNITS = ["cartogram.cu", "spectral_f32.cu", "spectral_f64.cu", "spectral_ff.cu", "step.cu", "persist.cu",
+         "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(ROOT, "include")]

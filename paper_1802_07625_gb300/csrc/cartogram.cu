@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/cartogram.h"
+#include "ff.cuh"
 #include "kernels.h"
 
 using cg::DevState;
@@ -60,6 +61,7 @@ struct cg_ctx {
   double blur = 0.0;
   cg_options opt{};
   bool mixed = false;
+  bool ff = false;  // CG_PRECISION_MIXED_FF: pass 2 in float-float arithmetic
   int device = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
@@ -68,6 +70,8 @@ struct cg_ctx {
   // transform tables: inverse roots and quarter-wave factors in the working type,
   // forward (FP64) roots, quarter-wave factors and blur factors
   void *Wx = nullptr, *Wy = nullptr, *Ex = nullptr, *Ey = nullptr;
+  void *Wyff = nullptr, *Eyff = nullptr;  // float-float pass-2 tables (CG_PRECISION_MIXED_FF)
+  int ff_cols_max = 0;                    // largest block of the float-float pass 2
   double2 *Wfx = nullptr, *Wfy = nullptr, *Efx = nullptr, *Efy = nullptr;
   double *bx = nullptr, *by = nullptr;  // blur factors for width blur_tab_sigma
   double blur_tab_sigma = -1.0;           // -1: the tables hold no known width
@@ -249,6 +253,30 @@ int upload_tables(cg_ctx* c, int N, void** Wd, void** Ed, double2** Wfd, double2
   return CG_OK;
 }
 
+// The pass-2 tables of the compensated mixed precision: the same inter-step twiddles and
+// quarter-wave factors as upload_tables, each as the float-float pair nearest the FP64 value.
+int upload_tables_ff(cg_ctx* c, int N, void** Wd, void** Ed) {
+  const int log2N = ilog2(N);
+  const int N1 = 1 << ((log2N + 1) / 2), N2 = N / N1;
+  std::vector<cg::ff2> W(N), E(N);
+  for (int k2 = 0; k2 < N2; ++k2)
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const double a = 2.0 * cg::kPi * (double)((n1 * k2) % N) / N;
+      W[k2 * N1 + n1].x = cg::ff(std::cos(a));
+      W[k2 * N1 + n1].y = cg::ff(std::sin(a));
+    }
+  for (int p = 0; p < N; ++p) {
+    const double b = cg::kPi * (double)p / (2.0 * N);
+    E[p].x = cg::ff(std::cos(b));
+    E[p].y = cg::ff(std::sin(b));
+  }
+  CG_CUDA(c, cudaMalloc(Wd, sizeof(cg::ff2) * N));
+  CG_CUDA(c, cudaMalloc(Ed, sizeof(cg::ff2) * N));
+  CG_CUDA(c, cudaMemcpy(*Wd, W.data(), sizeof(cg::ff2) * N, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(*Ed, E.data(), sizeof(cg::ff2) * N, cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
 // Separable blur factors exp(-(pi m / L)^2 sigma^2 / 2) of both axes, computed on the
 // device by the same kernel the device-side outer iteration uses.
 int set_blur_tables(cg_ctx* c, double sigma) {
@@ -265,6 +293,10 @@ int alloc_fields(cg_ctx* c) {
   if (r) return r;
   r = upload_tables<T>(c, c->Ly, &c->Wy, &c->Ey, &c->Wfy, &c->Efy);
   if (r) return r;
+  if (c->ff) {
+    if ((r = upload_tables_ff(c, c->Ly, &c->Wyff, &c->Eyff))) return r;
+    CG_CUDA(c, cg::prepare_spectral_ff(c->log2Ly, c->Lx, &c->ff_cols_max));
+  }
   CG_CUDA(c, cudaMalloc((void**)&c->bx, sizeof(double) * c->Lx));
   CG_CUDA(c, cudaMalloc((void**)&c->by, sizeof(double) * c->Ly));
   CG_CUDA(c, cudaMalloc((void**)&c->outer, sizeof(cg::OuterState)));
@@ -310,7 +342,8 @@ int alloc_fields(cg_ctx* c) {
                                  cg::inv_cols_cfg(c->log2Ly, c->Lx, sizeof(T), Wc).smem);
     int bps = 0, coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-    if (coop && smem <= 227 * 1024 && cg::prepare_integrate<T>(smem, &bps) == cudaSuccess && bps > 0) {
+    // (the persistent kernel runs the working type's pass 2 only: not for float-float)
+    if (!c->ff && coop && smem <= 227 * 1024 && cg::prepare_integrate<T>(smem, &bps) == cudaSuccess && bps > 0) {
       const int items = std::max(c->Ly / S, c->Lx / Wc);
       c->persist_grid = std::min(bps * cg::sm_count(), std::max(items, cg::sm_count()));
       c->persist_smem = smem;
@@ -324,14 +357,28 @@ int alloc_fields(cg_ctx* c) {
 
 // ---- the kernels of one integration ------------------------------------------
 
+// Pass 2 of the inverse transform with this context's arithmetic (float-float for the
+// compensated mixed precision, the working type otherwise).
+template <typename T>
+void launch_cols(cg_ctx* c, int Wc, const V2<T>* AB, V2<T>* v0, V2<T>* v1, T* rho_out, int mode, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (c->ff) {
+      cg::launch_inv_cols_ff(c->log2Ly, c->Lx, Wc, (const float2*)AB, (float2*)v0, (float2*)v1, (float*)rho_out,
+                             c->Wyff, c->Eyff, c->st, mode, s);
+      return;
+    }
+  }
+  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, Wc, AB, v0, v1, rho_out, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st,
+                         mode, s);
+}
+
 template <typename T>
 void enqueue_field(cg_ctx* c, int mode, double tau, V2<T>* out0, V2<T>* out1, T* rho_out,
                    cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
   cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->specT, (V2<T>*)c->AB,
                          (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, mode, tau, h, use_cond,
                          (unsigned int)c->opt.max_steps + 8u, s);
-  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, out0, out1, rho_out,
-                         (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, mode, s);
+  launch_cols<T>(c, c->tune.cols, (const V2<T>*)c->AB, out0, out1, rho_out, mode, s);
 }
 
 template <typename T>
@@ -365,12 +412,11 @@ void enqueue_init_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, 
   cg::launch_phi_spectrum<T>(c->spec64, (T*)c->phi, c->Lx, c->Ly, s);
   cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->phi, (V2<T>*)c->AB,
                          (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFlux, 0.0, 0, 0, 0u, s);
-  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->flux, nullptr,
-                         nullptr, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFlux, s);
+  launch_cols<T>(c, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->flux, nullptr, nullptr, cg::kModeFlux, s);
   cg::launch_inv_rows<T>(c->log2Lx, c->Ly, c->tune.rows, (const T*)c->specT, (V2<T>*)c->AB,
                          (const V2<T>*)c->Wx, (const V2<T>*)c->Ex, c->st, cg::kModeFixed, 0.0, 0, 0, 0u, s);
-  cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[0], nullptr,
-                         (T*)c->rho0, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
+  launch_cols<T>(c, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[0], nullptr, (T*)c->rho0, cg::kModeFixed,
+                 s);
   cudaMemsetAsync(&c->st->vmax2_bits, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&c->st->dev_bits, 0, sizeof(unsigned long long), s);
   cg::launch_linear_init<T>(c->st, sp, (const V2<T>*)c->flux, (const T*)c->rho0, (V2<T>*)c->vbuf[0],
@@ -441,13 +487,11 @@ int do_autotune(cg_ctx* c, int reps) {
     if (ms < best_ms[0]) { best_ms[0] = ms; best.rows = S; }
   }
   for (int W = 2; W <= 16 && W <= c->Lx; W *= 2) {
-    const cg::LaunchCfg k = cg::inv_cols_cfg(c->log2Ly, c->Lx, esz, W);
-    if (k.smem > 227 * 1024 || k.threads > cols_max) continue;
+    const cg::LaunchCfg k = c->ff ? cg::inv_cols_ff_cfg(c->log2Ly, c->Lx, W) : cg::inv_cols_cfg(c->log2Ly, c->Lx, esz, W);
+    if (k.smem > 227 * 1024 || k.threads > (c->ff ? c->ff_cols_max : cols_max)) continue;
     double ms;
     if ((r = timeit([&] {
-           cg::launch_inv_cols<T>(c->log2Ly, c->Lx, W, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr,
-                                  nullptr, (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st,
-                                  cg::kModeFixed, s);
+           launch_cols<T>(c, W, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr, nullptr, cg::kModeFixed, s);
          }, &ms)))
       return r;
     if (ms < best_ms[1]) { best_ms[1] = ms; best.cols = W; }
@@ -1545,9 +1589,8 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
                                  0, 0, 0u, s);
           break;
         case 1:
-          cg::launch_inv_cols<T>(c->log2Ly, c->Lx, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1],
-                                 nullptr, nullptr,
-                                 (const V2<T>*)c->Wy, (const V2<T>*)c->Ey, c->st, cg::kModeFixed, s);
+          launch_cols<T>(c, c->tune.cols, (const V2<T>*)c->AB, (V2<T>*)c->vbuf[1], nullptr, nullptr,
+                         cg::kModeFixed, s);
           break;
         case 2:
           cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
@@ -1710,7 +1753,8 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   cg_options o;
   cartogram_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED) return CG_EINVAL;
+  if (o.precision != CG_PRECISION_FP64 && o.precision != CG_PRECISION_MIXED && o.precision != CG_PRECISION_MIXED_FF)
+    return CG_EINVAL;
   if (o.use_graph < 0 || o.use_graph > 2) return CG_EINVAL;
   if (o.flow != CG_FLOW_DIFFUSION && o.flow != CG_FLOW_LINEAR) return CG_EINVAL;
   if (!is_finite(o.time_limit) || o.time_limit < 0.0 || o.time_limit > 1e9) return CG_EINVAL;
@@ -1727,7 +1771,8 @@ int cartogram_init(int Lx, int Ly, double blur_width, const cg_options* opt, cg_
   c->log2Ly = ilog2(Ly);
   c->blur = blur_width;
   c->opt = o;
-  c->mixed = o.precision == CG_PRECISION_MIXED;
+  c->mixed = o.precision != CG_PRECISION_FP64;
+  c->ff = o.precision == CG_PRECISION_MIXED_FF;
   int r = CG_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess) r = CG_ECUDA;
   if (!r && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) r = CG_ECUDA;
@@ -2148,7 +2193,7 @@ void cartogram_destroy(cg_ctx* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   free_regions(c);
-  void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
+  void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wyff, c->Eyff, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
                 c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
                 c->rho0, c->diag, c->deadline};

@@ -56,6 +56,20 @@ inline LaunchCfg inv_rows_cfg(int log2Lx, int Ly, size_t esz, int S) {
   return c;
 }
 
+// pass 2 of the inverse transform in float-float arithmetic on FP32 data (the compensated
+// mixed precision): the same block shape, float-float tables and signals in shared memory
+inline LaunchCfg inv_cols_ff_cfg(int log2Ly, int Lx, int Wc) {
+  const int N = 1 << log2Ly, N1 = fft_n1(log2Ly);
+  if (Wc <= 0) Wc = 2;
+  const int S = Wc + Wc / 2;
+  LaunchCfg c;
+  c.per_block = Wc;
+  c.threads = S * N1;
+  c.smem = (size_t)N * 4 * 8 + (size_t)Wc * N * 2 * 4 + (size_t)S * fft_stride(log2Ly) * 2 * 8 + 64 * 4;
+  c.grid = Lx / Wc;
+  return c;
+}
+
 // pass 2 of the inverse transform: Wc columns per block
 inline LaunchCfg inv_cols_cfg(int log2Ly, int Lx, size_t esz, int Wc) {
   const int N = 1 << log2Ly, N1 = fft_n1(log2Ly);
@@ -115,6 +129,13 @@ inline void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem,
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
 }
+
+// Pass 2 in float-float arithmetic (tables W, E: float-float pairs [N]); prepare_spectral_ff
+// allows its shared memory for every column count up to 16 that fits, and reports the
+// largest block it can launch.
+cudaError_t prepare_spectral_ff(int log2Ly, int Lx, int* cols_max_threads);
+void launch_inv_cols_ff(int log2Ly, int Lx, int Wc, const float2* AB, float2* v0, float2* v1, float* rho_out,
+                        const void* W, const void* E, DevState* st, int mode, cudaStream_t s);
 
 // Allow the dynamic shared memory the spectral kernels of this grid need.
 template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);

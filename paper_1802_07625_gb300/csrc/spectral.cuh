@@ -52,11 +52,11 @@ __host__ __device__ constexpr size_t p1_smem(int S) {
   return (size_t)F::N * 4 * sizeof(T) + (size_t)S * F::N * sizeof(T) +
          (size_t)S * F::SSTRIDE * 2 * sizeof(T) + (size_t)(F::N + S) * sizeof(T);
 }
-template <typename T, int LOG2N>
+template <typename T, int LOG2N, typename A = T>
 __host__ __device__ constexpr size_t p2_smem(int Wc) {
   using F = FFTShape<LOG2N>;
-  return (size_t)F::N * 4 * sizeof(T) + (size_t)Wc * F::N * 2 * sizeof(T) +
-         (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(T) + 64 * sizeof(T);
+  return (size_t)F::N * 4 * sizeof(A) + (size_t)Wc * F::N * 2 * sizeof(T) +
+         (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(A) + 64 * sizeof(T);
 }
 
 // Issue the bulk copies of a pass-1 item (thread 0): both tables and the S spectral rows,
@@ -165,6 +165,11 @@ __device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __res
   return p1_finish<T, LOG2N>(ABt, Ly, S, n0, tau, smem, bar, ph);
 }
 
+// A complex value in the arithmetic type A.
+template <typename A, typename T> __device__ __forceinline__ V2<A> to_v2(const V2<T>& v) {
+  return mk2<A>(A(v.x), A(v.y));
+}
+
 // Block-reduced results of a pass-2 item (valid in thread 0).
 template <typename T> struct FieldRed {
   T dev;    // max |rho/rho_bar - 1|
@@ -180,25 +185,25 @@ template <typename T> struct FieldRed {
 // ---------------------------------------------------------------------------
 // Pass-2 copies in two parts on one mbarrier phase (thread 0): the tables, which do not
 // depend on pass 1, and then the Wc columns of ABt that pass 1 wrote.
-template <typename T, int LOG2N>
-__device__ __forceinline__ void p2_issue_tables(const V2<T>* __restrict__ Wg, const V2<T>* __restrict__ Eg,
+template <typename T, int LOG2N, typename A = T>
+__device__ __forceinline__ void p2_issue_tables(const V2<A>* __restrict__ Wg, const V2<A>* __restrict__ Eg,
                                                 int Wc, unsigned char* smem, uint64_t* bar) {
-  using C = V2<T>;
+  using C = V2<A>;
   constexpr int N = 1 << LOG2N;
   C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, (uint32_t)((2 + Wc) * N * sizeof(C)));
+    mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + Wc * N * sizeof(V2<T>)));
     bulk_g2s(W, Wg, N * sizeof(C), bar);
     bulk_g2s(E, Eg, N * sizeof(C), bar);
   }
 }
-template <typename T, int LOG2N>
+template <typename T, int LOG2N, typename A = T>
 __device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int Wc, int c0,
                                               unsigned char* smem, uint64_t* bar) {
   using C = V2<T>;
   constexpr int N = 1 << LOG2N;
-  C* stage = reinterpret_cast<C*>(smem) + 2 * N;
+  C* stage = reinterpret_cast<C*>(reinterpret_cast<V2<A>*>(smem) + 2 * N);
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     for (int cc = 0; cc < Wc; ++cc)
@@ -212,63 +217,65 @@ __device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int
 // by p2_issue_tables and p2_issue_cols have landed.
 // shared: W[N] E[N] (C), stage[Wc*N] (C), buf[(Wc + Wc/2) * SSTRIDE] (C), red[64] (T)
 // ---------------------------------------------------------------------------
-template <typename T, int LOG2N>
+// T: the type of the (A, B) input, of the field written and of the reductions; A: the
+// arithmetic of the packing, the FFT and the velocity (T, or float-float for FP32 data).
+template <typename T, int LOG2N, typename A = T>
 __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict__ rho_out, int Lx,
                                           int Wc, int c0, unsigned char* smem, uint64_t* bar,
                                           uint32_t& ph, FieldRed<T>& res, bool raw = false) {
-  using C = V2<T>;
+  using C = V2<A>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
   C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
-  C* stage = E + N;
-  C* buf = stage + Wc * N;
+  const V2<T>* stage = reinterpret_cast<const V2<T>*>(E + N);
+  C* buf = reinterpret_cast<C*>(const_cast<V2<T>*>(stage) + Wc * N);
   T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::SSTRIDE);
   const bool ok = mbar_wait_bounded(bar, ph, kMbarTries);
   ph ^= 1u;
   if (!__syncthreads_and(ok)) return false;
 
   const int Wp = Wc / 2;
-  const T kd = (T)(kPi / N);
+  const A kd = (A)(kPi / N);
   // N/2 tasks per column pair (no runtime integer division): task m > 0 packs the pair
   // (m, N - m); task 0 packs m = 0 and then (second round) the self-paired m = N/2
   for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
     const int p = task >> (LOG2N - 1);
     int m = task & (N / 2 - 1);
-    const C* s0 = stage + (2 * p) * N;
-    const C* s1 = s0 + N;
+    const V2<T>* s0 = stage + (2 * p) * N;
+    const V2<T>* s1 = s0 + N;
     C* x0 = buf + (2 * p) * F::SSTRIDE;
     C* x1 = x0 + F::SSTRIDE;
     C* x2 = buf + (Wc + p) * F::SSTRIDE;
     if (m == 0) {
-      const C A00 = s0[0], A01 = s1[0];
-      x0[F::pidx(0)] = mk2<T>(A00.x, T(0));
-      x1[F::pidx(0)] = mk2<T>(A01.x, T(0));
-      x2[F::pidx(0)] = mk2<T>(A00.y, A01.y);
+      const C A00 = to_v2<A, T>(s0[0]), A01 = to_v2<A, T>(s1[0]);
+      x0[F::pidx(0)] = mk2<A>(A00.x, A(0));
+      x1[F::pidx(0)] = mk2<A>(A01.x, A(0));
+      x2[F::pidx(0)] = mk2<A>(A00.y, A01.y);
       m = N / 2;
     }
-    const C Am0 = s0[m], Am1 = s1[m];
+    const C Am0 = to_v2<A, T>(s0[m]), Am1 = to_v2<A, T>(s1[m]);
     const int q = N - m;
-    const C Aq0 = s0[q], Aq1 = s1[q];
+    const C Aq0 = to_v2<A, T>(s0[q]), Aq1 = to_v2<A, T>(s1[q]);
     const C em = E[m], eq = E[q];
     {  // (rho', d_y rho) of column c
-      const T am = Am0.x, aq = Aq0.x, bm = -kd * (T)m * am, bq = -kd * (T)q * aq;
-      x0[F::pidx(m)] = cmul(em, mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
-      if (q != m) x0[F::pidx(q)] = cmul(eq, mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+      const A am = Am0.x, aq = Aq0.x, bm = -kd * (A)m * am, bq = -kd * (A)q * aq;
+      x0[F::pidx(m)] = cmul(em, mk2<A>((am + bm) * A(0.5), (bq - aq) * A(0.5)));
+      if (q != m) x0[F::pidx(q)] = cmul(eq, mk2<A>((aq + bq) * A(0.5), (bm - am) * A(0.5)));
     }
     {  // (rho', d_y rho) of column c + 1
-      const T am = Am1.x, aq = Aq1.x, bm = -kd * (T)m * am, bq = -kd * (T)q * aq;
-      x1[F::pidx(m)] = cmul(em, mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
-      if (q != m) x1[F::pidx(q)] = cmul(eq, mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
+      const A am = Am1.x, aq = Aq1.x, bm = -kd * (A)m * am, bq = -kd * (A)q * aq;
+      x1[F::pidx(m)] = cmul(em, mk2<A>((am + bm) * A(0.5), (bq - aq) * A(0.5)));
+      if (q != m) x1[F::pidx(q)] = cmul(eq, mk2<A>((aq + bq) * A(0.5), (bm - am) * A(0.5)));
     }
     {  // d_x rho of columns c (real part) and c + 1 (imaginary part)
-      const T bem = Am0.y, gam = Am1.y, beq = Aq0.y, gaq = Aq1.y;
-      x2[F::pidx(m)] = cmul(em, mk2<T>((bem + gaq) * T(0.5), (gam - beq) * T(0.5)));
-      if (q != m) x2[F::pidx(q)] = cmul(eq, mk2<T>((beq + gam) * T(0.5), (gaq - bem) * T(0.5)));
+      const A bem = Am0.y, gam = Am1.y, beq = Aq0.y, gaq = Aq1.y;
+      x2[F::pidx(m)] = cmul(em, mk2<A>((bem + gaq) * A(0.5), (gam - beq) * A(0.5)));
+      if (q != m) x2[F::pidx(q)] = cmul(eq, mk2<A>((beq + gam) * A(0.5), (gaq - bem) * A(0.5)));
     }
   }
   __syncthreads();
-  block_fft<T, LOG2N, true>(buf, Wc + Wp, W);
+  block_fft<A, LOG2N, true>(buf, Wc + Wp, W);
 
   T dev = T(0), v2max = T(0);
   bool bad = false;
@@ -284,16 +291,16 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const C u1 = buf[(2 * cp + h) * F::SSTRIDE + slot];
-      const T rp = u1.x;
-      const T gy = (j & 1) ? -u1.y : u1.y;
-      const T gx = h ? u2.y : u2.x;
-      const T rho = T(1) + rp;
-      if (!raw) bad |= !(rho > T(0));
-      const T inv = raw ? T(1) : T(1) / rho;
-      const T vx = -gx * inv, vy = -gy * inv;
+      const A rp = u1.x;
+      const A gy = (j & 1) ? -u1.y : u1.y;
+      const A gx = h ? u2.y : u2.x;
+      const A rho = A(1) + rp;
+      if (!raw) bad |= !(rho > A(0));
+      const A inv = raw ? A(1) : A(1) / rho;
+      const T vx = (T)(-gx * inv), vy = (T)(-gy * inv);
       vv[h] = mk2<T>(vx, vy);
-      rr[h] = raw ? rp : rho;  // flux mode: the plain cosine sum
-      dev = max(dev, fabs(rp));
+      rr[h] = (T)(raw ? rp : rho);  // flux mode: the plain cosine sum
+      dev = max(dev, fabs((T)rp));
       v2max = max(v2max, vx * vx + vy * vy);
     }
     const size_t o = (size_t)j * Lx + c0 + 2 * cp;
@@ -407,23 +414,24 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// pass 2 as its own kernel. blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc.
+// pass 2 as its own kernel. blockDim = (Wc + Wc/2) * N1, grid = Lx / Wc. A: the arithmetic
+// (T, or float-float for FP32 data: the compensated mixed precision).
 // ---------------------------------------------------------------------------
-template <typename T, int LOG2N>
+template <typename T, int LOG2N, typename A = T>
 __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<T>* vbuf1,
-                                T* __restrict__ rho_out, const V2<T>* __restrict__ Wg,
-                                const V2<T>* __restrict__ Eg, int Lx, int Wc, DevState* st,
+                                T* __restrict__ rho_out, const V2<A>* __restrict__ Wg,
+                                const V2<A>* __restrict__ Eg, int Lx, int Wc, DevState* st,
                                 int mode) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   const int c0 = blockIdx.x * Wc;
-  p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem_raw, &bar);
+  p2_issue_tables<T, LOG2N, A>(Wg, Eg, Wc, smem_raw, &bar);
   __shared__ int s_run, s_par;
   const bool step = is_step_mode(mode);
   pdl_wait();
-  p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem_raw, &bar);
+  p2_issue_cols<T, LOG2N, A>(ABt, Wc, c0, smem_raw, &bar);
   if (step) {
     // the attempt's state, as pass 1 decided and stored it (read while the copies land)
     if (threadIdx.x == 0) {
@@ -442,7 +450,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
   uint32_t ph = 0;
   FieldRed<T> r;
-  if (!p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux)) {
+  if (!p2_finish<T, LOG2N, A>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux)) {
     if (threadIdx.x == 0) {
       if (step) atomicOr(&st->ls[step_slot(mode)].bad, 1);
       else st->bad = 2;

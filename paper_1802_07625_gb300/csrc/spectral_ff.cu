@@ -1,0 +1,50 @@
+// Pass 2 of the inverse transform in float-float arithmetic on FP32 data (size dispatch).
+#include "ff.cuh"
+#include "kernels.h"
+#include "spectral.cuh"
+
+#define CG_FF_FOR_EACH_LOG2N(X) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
+namespace cg {
+
+cudaError_t prepare_spectral_ff(int log2Ly, int Lx, int* cols_max_threads) {
+  LaunchCfg c = inv_cols_ff_cfg(log2Ly, Lx, 2);
+  for (int W = 2; W <= 16 && W <= Lx; W *= 2) {
+    const LaunchCfg k = inv_cols_ff_cfg(log2Ly, Lx, W);
+    if (k.smem <= 227 * 1024 && k.smem > c.smem) c = k;
+  }
+  cudaError_t e = cudaErrorInvalidValue;
+  cudaFuncAttributes fa;
+  switch (log2Ly) {
+#define CG_CASE(L)                                                                                 \
+  case L:                                                                                          \
+    e = cudaFuncSetAttribute((const void*)inv_cols_kernel<float, L, ff>,                           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);            \
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)inv_cols_kernel<float, L, ff>); \
+    break;
+    CG_FF_FOR_EACH_LOG2N(CG_CASE)
+#undef CG_CASE
+    default: break;
+  }
+  if (e == cudaSuccess && cols_max_threads) *cols_max_threads = fa.maxThreadsPerBlock;
+  return e;
+}
+
+void launch_inv_cols_ff(int log2Ly, int Lx, int Wc, const float2* AB, float2* v0, float2* v1, float* rho_out,
+                        const void* W, const void* E, DevState* st, int mode, cudaStream_t s) {
+  const LaunchCfg c = inv_cols_ff_cfg(log2Ly, Lx, Wc);
+  const ff2* Wf = static_cast<const ff2*>(W);
+  const ff2* Ef = static_cast<const ff2*>(E);
+  switch (log2Ly) {
+#define CG_CASE(L)                                                                                  \
+  case L:                                                                                           \
+    launch_pdl(inv_cols_kernel<float, L, ff>, c.grid, c.threads, c.smem, s, AB, v0, v1, rho_out, Wf, \
+               Ef, Lx, c.per_block, st, mode);                                                      \
+    break;
+    CG_FF_FOR_EACH_LOG2N(CG_CASE)
+#undef CG_CASE
+    default: break;
+  }
+}
+
+}  // namespace cg

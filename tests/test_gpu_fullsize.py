@@ -162,7 +162,8 @@ def test_density_spectrum_field_and_step_at_512(orc, clustered):
     _, _, xcor, ycor, e = orc.heun_step(vx, vy, v1[0], v1[1], x.ravel(), y.ravel(), h)
     # field error bounds relative to the fields' global scale: FP32 transforms ~ eps32
     # log2(N) per value; the FP64 transforms and the oracle's direct sums both ~1e-14
-    for prec, eps, ptol in (("fp64", 1e-12, 1e-9), ("mixed", 2.0 ** -24 * np.log2(m.Lx) * 8, 1e-3)):
+    for prec, eps, ptol in (("fp64", 1e-12, 1e-9), ("mixed", 2.0 ** -24 * np.log2(m.Lx) * 8, 1e-3),
+                            ("mixed_ff", 2.0 ** -24 * np.log2(m.Lx) * 8, 1e-3)):
         with P.Cartogram(m.Lx, m.Ly, blur, precision=prec) as c:
             c.set_map(m)
             rho_gpu = c.density()
@@ -210,10 +211,11 @@ def test_fp64_and_mixed_agree_on_first_integrations_at_512(clustered):
     # drift stays below 1e-3 grid units for 99.9 % of the points and below 3e-3 for all;
     # FP32 displacements alone (FP64 fields) account for 1.4e-4 and the FP32 spectrum
     # alone for 6e-5.
+    # With pass 2 in float-float arithmetic (precision "mixed_ff") every point is within 1e-3.
     m = clustered
     blur = synth.WORKLOADS["clustered300_512"]["blur"]
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_ff"):
         with P.Cartogram(m.Lx, m.Ly, blur, precision=prec, max_iter=2) as c:
             c.set_map(m)
             with pytest.raises(P.CartogramError) as e:
@@ -224,4 +226,8 @@ def test_fp64_and_mixed_agree_on_first_integrations_at_512(clustered):
         d = np.abs(out["fp64"][k] - out["mixed"][k])
         assert np.mean(d > 1e-3) < 1e-3
         assert np.max(d) < 3e-3
+        dff = np.abs(out["fp64"][k] - out["mixed_ff"][k])
+        print("first integrations at 512^2, iteration %d: mixed %.3g, mixed_ff %.3g" % (k, d.max(), dff.max()))
+        assert np.max(dff) < 1e-3
     assert np.max(np.abs(out["fp64"][2] - out["mixed"][2])) < 1e-4
+    assert np.max(np.abs(out["fp64"][2] - out["mixed_ff"][2])) < 1e-4

@@ -8,8 +8,9 @@ in both precisions and is compared with that file:
   - FP64 path: the same number of outer iterations and of accepted / rejected steps,
     every sampled vertex and projected grid point of every iteration within 1e-9 grid
     units, area errors within 1e-9;
-  - mixed path: the same number of outer iterations, sampled vertices within 1e-3 grid
-    units, area errors within 1e-4.
+  - mixed paths (FP32 transforms, and FP32 pass 1 with pass 2 in float-float): the same
+    number of outer iterations, sampled vertices within 1e-3 grid units, area errors within
+    1e-4.
 The 512^2 and 1024^2 workloads are the full configurations of the benchmark.
 """
 import hashlib
@@ -97,5 +98,6 @@ def test_converged_cartogram_matches_stored_oracle(name):
     blur = g["meta"]["blur"]
     st, xy, err, grids = _run(m, blur, "fp64")
     check_fp64(name, g, st, xy, err, grids)
-    st, xy, err, _ = _run(m, blur, "mixed")
-    check_mixed(name, g, st, xy, err)
+    for precision in ("mixed", "mixed_ff"):
+        st, xy, err, _ = _run(m, blur, precision)
+        check_mixed(name, g, st, xy, err)

@@ -66,7 +66,7 @@ def test_spectrum_matches_oracle(orc, precision, tol, shape):
         assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5), ("mixed_ff", 2e-5)])
 @pytest.mark.parametrize("shape", [(64, 64), (16, 64), (128, 32)])
 @pytest.mark.parametrize("t", [0.0, 0.7, 25.0])
 def test_velocity_matches_oracle(orc, precision, tol, shape, t):
@@ -85,7 +85,7 @@ def test_velocity_matches_oracle(orc, precision, tol, shape, t):
     assert np.max(np.abs(v[..., 1] - vy)) < tol * scale * 4
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5), ("mixed_ff", 1e-5)])
 def test_heun_step_matches_oracle(orc, precision, tol):
     m = _small_map()
     Lx, Ly = m.Lx, m.Ly
