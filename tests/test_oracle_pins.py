@@ -284,6 +284,55 @@ def test_x_only_density_gives_one_dimensional_equalising_map(orc):
     assert errs[2] < 0.03
 
 
+def _one_mode_spectrum(orc, Ly=8, Lx=64, a=0.5):
+    x = np.arange(Lx) + 0.5
+    rho0 = (1 + a * np.cos(PI * x / Lx))[None, :] * np.ones((Ly, 1))
+    return orc.forward(rho0, 0.0)
+
+
+def test_heun_is_second_order_in_time(orc):
+    # The predictor-corrector (Eq. rt_diff integrated by Heun's method) on a fixed schedule
+    # of n equal steps to the same end time, against 1024 steps with the same field and
+    # interpolation: halving the step quarters the error (global error O(h^2)). A first-
+    # order slip (e.g. the corrector dropping v(t + h)) would give ratios near 2.
+    spec = _one_mode_spectrum(orc)
+    T = 200.0
+
+    def run(n):
+        return orc.integrate_replay(spec, [T / n] * n)[0]
+
+    ref = run(1024)
+    e = [np.max(np.abs(run(n) - ref)) for n in (8, 16, 32)]
+    for coarse, fine in zip(e, e[1:]):
+        assert 3.7 < coarse / fine < 4.3, e
+
+
+def test_adaptive_error_scales_with_the_step_tolerance(orc):
+    # The step error r_corr - r_pred = (h/2)(u1 - u0) is O(h^2), so with acceptance at
+    # e <= atol the steps scale as atol^(1/2) and the time-integration error (against a
+    # fine fixed schedule to the same end time, same field and interpolation) as atol:
+    # a quarter of atol gives about a quarter of the error.
+    spec = _one_mode_spectrum(orc)
+    errs = []
+    for atol in (4e-2, 1e-2, 2.5e-3):
+        r = orc.integrate(spec, atol=atol, rho_tol=1e-7)
+        assert r.status == 0
+        ref = orc.integrate_replay(spec, [r.t_end / 4096] * 4096)[0]
+        errs.append(np.max(np.abs(r.X - ref)))
+        # the recorded schedule obeys the controller: a rejected step is retried at half
+        # its size, an accepted one grows by at most 1.2 (less where the speed cap holds),
+        # and the accepted steps add up to the end time
+        h, acc = r.sched_h, r.sched_acc.astype(bool)
+        assert np.sum(h[acc]) == pytest.approx(r.t_end, rel=1e-12)
+        for k in range(len(h) - 1):
+            if acc[k]:
+                assert h[k + 1] <= 1.2 * h[k] * (1 + 1e-15)
+            else:
+                assert h[k + 1] == pytest.approx(0.5 * h[k], rel=1e-15)
+    for coarse, fine in zip(errs, errs[1:]):
+        assert 2.5 < coarse / fine < 5.0, errs
+
+
 def test_mirror_symmetry(orc):
     rng = np.random.default_rng(6)
     Ly, Lx = 12, 12
