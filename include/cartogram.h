@@ -284,6 +284,13 @@ int cartogram_set_values(cg_ctx* ctx, const double* target_values);
 /* Number of outer iterations in the history (projected grids stored). */
 int cartogram_history_length(const cg_ctx* ctx);
 
+/* What outer iteration k of the history did (main text, section on benchmarking: the
+ * integration is repeated until the largest relative area error is below 1 %): out[6] =
+ * {max_i |A_i/A^_i - 1| once its vertices were mapped, diffusion time its integration
+ * reached, accepted steps, rejected steps, device time of its step loop in ms, blur width it
+ * used}. out may be host or device memory. Errors: CG_EINVAL (k out of range). */
+int cartogram_iteration_record(cg_ctx* ctx, int k, double* out);
+
 /* Projected grid of history entry k: positions of the Lx*Ly cell centres after
  * integration k, xy_out [Lx*Ly][2] FP64. Errors: CG_EINVAL (k out of range). */
 int cartogram_get_grid(cg_ctx* ctx, int k, double* xy_out);

@@ -23,7 +23,7 @@ __all__ = [
     "CG_FLOW_LINEAR", "CartogramError", "Options", "Stats",
     "library_path", "load", "cartogram_default_options", "cartogram_init", "cartogram_set_stream",
     "cartogram_set_regions", "cartogram_integrate", "cartogram_project", "cartogram_area_errors",
-    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_polygon_measures", "cartogram_autotune", "cartogram_read_bandwidth", "cartogram_profile", "cartogram_history_length", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
+    "cartogram_get_vertices", "cartogram_reset", "cartogram_set_values", "cartogram_polygon_measures", "cartogram_autotune", "cartogram_read_bandwidth", "cartogram_profile", "cartogram_history_length", "cartogram_iteration_record", "cartogram_fold_count", "cartogram_get_grid", "cartogram_density",
     "cartogram_spectrum", "cartogram_velocity", "cartogram_heun_step", "cartogram_integrate_once",
     "cartogram_velocity_noalloc", "cartogram_inverse_project", "cartogram_distortion",
     "cartogram_iteration_gradient", "cartogram_iteration_vjp", "cartogram_last_error",
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "cartogram_area_errors": (i, [_P, _P]),
         "cartogram_get_vertices": (i, [_P, _P]),
         "cartogram_history_length": (i, [_P]),
+        "cartogram_iteration_record": (i, [_P, i, _P]),
         "cartogram_fold_count": (i, [_P, i, ctypes.POINTER(ll), ctypes.POINTER(d)]),
         "cartogram_reset": (i, [_P]),
         "cartogram_set_values": (i, [_P, _P]),
@@ -272,6 +273,18 @@ def cartogram_read_bandwidth(nbytes: int, passes: int = 20) -> float:
 
 def cartogram_history_length(ctx) -> int:
     return load().cartogram_history_length(ctx)
+
+
+ITERATION_RECORD = ("max_area_error", "t_end", "steps_accepted", "steps_rejected", "step_loop_ms", "blur")
+
+
+def cartogram_iteration_record(ctx, k) -> dict:
+    out = np.zeros(len(ITERATION_RECORD))
+    _check(ctx, load().cartogram_iteration_record(ctx, int(k), out.ctypes.data))
+    d = dict(zip(ITERATION_RECORD, out.tolist()))
+    d["steps_accepted"] = int(d["steps_accepted"])
+    d["steps_rejected"] = int(d["steps_rejected"])
+    return d
 
 
 def cartogram_fold_count(ctx, k):
@@ -541,6 +554,12 @@ class Cartogram:
 
     def history_length(self):
         return cartogram_history_length(self.ctx)
+
+    def iteration_record(self, k):
+        return cartogram_iteration_record(self.ctx, k)
+
+    def iteration_history(self):
+        return [cartogram_iteration_record(self.ctx, k) for k in range(self.history_length())]
 
     def fold_count(self, k):
         return cartogram_fold_count(self.ctx, k)

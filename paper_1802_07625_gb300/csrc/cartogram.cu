@@ -787,6 +787,12 @@ int read_info(cg_ctx* c) {
 // integration, a read-back of the outcome and of the areas after each. Runs at most
 // iter_limit iterations; stopping there is CG_ENOCONVERGE only when that is the whole
 // budget (final), else *stopped is set. Counts accumulate into s.
+// Bytes of one history slot: the projected grid's displacements, then its IterRecord.
+template <typename T>
+size_t slot_bytes(const cg_ctx* c) {
+  return sizeof(V2<T>) * (size_t)c->Lx * c->Ly + sizeof(cg::IterRecord);
+}
+
 template <typename T>
 int do_integrate_host(cg_ctx* c, cg_stats& s, int iter_limit, bool final, bool* stopped) {
   int r;
@@ -795,6 +801,7 @@ int do_integrate_host(cg_ctx* c, cg_stats& s, int iter_limit, bool final, bool* 
   double max_err = c->info_h->max_err;
   int status = CG_OK;
   const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
+  const size_t sbytes = slot_bytes<T>(c);
   int it = 0;
   while (!(max_err < c->opt.area_tol)) {
     if (it >= iter_limit) {
@@ -825,7 +832,7 @@ int do_integrate_host(cg_ctx* c, cg_stats& s, int iter_limit, bool final, bool* 
     if (c->opt.autotune && !c->tuned && (r = do_autotune<T>(c, 10))) return r;
     if ((int)c->hist.size() <= c->hist_len) {
       void* p = nullptr;
-      CG_CUDA(c, cudaMalloc(&p, fbytes));
+      CG_CUDA(c, cudaMalloc(&p, sbytes));
       c->hist.push_back(p);
     }
     void* grid = c->hist[c->hist_len];
@@ -833,6 +840,14 @@ int do_integrate_host(cg_ctx* c, cg_stats& s, int iter_limit, bool final, bool* 
     cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)grid, c->Lx, c->Ly, c->stream);
     if ((r = run_areas(c)) || (r = read_info(c))) return r;
     max_err = c->info_h->max_err;
+    cg::IterRecord rec;
+    rec.max_err = max_err;
+    rec.t_end = inf.t_end;
+    rec.blur = c->blur * std::pow(c->opt.blur_decay, (double)c->hist_len);
+    rec.accepted = inf.accepted;
+    rec.rejected = inf.rejected;
+    rec.loop_ns = inf.loop_ns;
+    CG_CUDA(c, cudaMemcpy(static_cast<char*>(grid) + fbytes, &rec, sizeof rec, cudaMemcpyHostToDevice));
     ++it;
     ++c->hist_len;
   }
@@ -847,10 +862,10 @@ constexpr int kSlotChunk = 32;
 
 template <typename T>
 int ensure_slots(cg_ctx* c, int want) {
-  const size_t fbytes = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
+  const size_t sbytes = slot_bytes<T>(c);
   while ((int)c->hist.size() < want) {
     void* p = nullptr;
-    CG_CUDA(c, cudaMalloc(&p, fbytes));
+    CG_CUDA(c, cudaMalloc(&p, sbytes));
     c->hist.push_back(p);
   }
   const int n = (int)c->hist.size();
@@ -897,6 +912,7 @@ int outer_prepare(cg_ctx* c, int budget) {
   o.iterations = 0;
   o.max_iter = budget;
   o.status = cg::kOuterRunning;
+  o.rec_offset = sizeof(V2<T>) * (size_t)c->Lx * c->Ly;
   CG_CUDA(c, cudaMemcpyAsync(c->outer, &o, sizeof o, cudaMemcpyHostToDevice, c->stream));
   CG_CUDA(c, cudaStreamSynchronize(c->stream));
   c->blur_tab_sigma = -1.0;  // the loop rewrites the blur tables
@@ -2069,6 +2085,20 @@ int cartogram_fold_count(cg_ctx* c, int k, long long* n_folded, double* min_area
 }
 
 int cartogram_history_length(const cg_ctx* c) { return c ? c->hist_len : 0; }
+
+int cartogram_iteration_record(cg_ctx* c, int k, double* out) {
+  int r = check_ctx(c, false);
+  if (r) return r;
+  if (k < 0 || k >= c->hist_len || !out) return fail(c, CG_EINVAL, "history entry %d out of range", k);
+  const size_t fbytes = (c->mixed ? sizeof(float2) : sizeof(double2)) * (size_t)c->Lx * c->Ly;
+  cg::IterRecord rec;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  CG_CUDA(c, cudaMemcpy(&rec, static_cast<const char*>(c->hist[k]) + fbytes, sizeof rec, cudaMemcpyDeviceToHost));
+  const double o[6] = {rec.max_err, rec.t_end, (double)rec.accepted, (double)rec.rejected, rec.loop_ns * 1e-6,
+                       rec.blur};
+  CG_CUDA(c, cudaMemcpy(out, o, sizeof o, cudaMemcpyDefault));
+  return CG_OK;
+}
 
 int cartogram_get_grid(cg_ctx* c, int k, double* xy_out) {
   int r = check_ctx(c, false);

@@ -103,6 +103,18 @@ struct IterInfo {
   unsigned long long loop_ns;  // device time of the integration (init to finish)
 };
 
+// What an outer iteration leaves behind with its projected grid (stored after the grid in
+// the iteration's history slot): the largest relative area error once the vertices are
+// mapped, the integration's end time and step counts, its device time and blur width.
+struct IterRecord {
+  double max_err;
+  double t_end;
+  double blur;
+  long long accepted;
+  long long rejected;
+  unsigned long long loop_ns;
+};
+
 // State of the outer iteration when it runs on the device (one CUDA-graph launch runs
 // iterations until the areas converge, the budget ends, an integration fails, or the
 // history has no free slot). Written by the host before a launch, read after it.
@@ -121,6 +133,7 @@ struct OuterState {
   int max_iter;               // iteration budget of this call
   int status;                 // kOuter* below, or a failed integration's status (< 0)
   int pad;
+  unsigned long long rec_offset;  // byte offset of the IterRecord in a history slot
 };
 constexpr int kOuterRunning = 0;
 constexpr int kOuterConverged = 1;

@@ -53,6 +53,13 @@ static __global__ void outer_decide_kernel(OuterState* o, const IterInfo* info, 
     o->t_end = info->t_end;
     o->loop_ns += info->loop_ns;
     if (o->status == kOuterRunning) {
+      IterRecord* rec = reinterpret_cast<IterRecord*>(static_cast<char*>(o->hist[o->k]) + o->rec_offset);
+      rec->max_err = info->max_err;
+      rec->t_end = info->t_end;
+      rec->blur = o->sigma[o->iterations];
+      rec->accepted = info->accepted;
+      rec->rejected = info->rejected;
+      rec->loop_ns = info->loop_ns;
       o->k += 1;
       o->iterations += 1;
     }

@@ -450,3 +450,30 @@ def test_caller_stream_profile_and_autotune():
         assert all(0.0 < v < 100.0 for v in tuned["ms"])
         st2 = c.integrate()  # converged already: no iteration
         assert st2.iterations == 0
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_iteration_records(orc, use_graph):
+    """Per-iteration records of the history (largest area error after the iteration, its
+    end time, step counts, device time, blur width) in both outer-loop modes, against
+    the oracle run for one and two iterations."""
+    m = _small_map()
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph) as c:
+        st = c.integrate()
+        recs = c.iteration_history()
+    assert len(recs) == st.iterations
+    assert recs[-1]["max_area_error"] == pytest.approx(st.max_area_error, rel=1e-12)
+    assert sum(r["steps_accepted"] for r in recs) == st.steps_accepted
+    assert sum(r["steps_rejected"] for r in recs) == st.steps_rejected
+    for k, r in enumerate(recs):
+        assert r["blur"] == pytest.approx(1.0 * 0.5 ** k, rel=1e-15)
+        assert r["step_loop_ms"] > 0 and r["t_end"] > 0
+    for k in (1, 2):
+        ref = orc.cartogram(m, 1.0, keep_grids=False, max_iter=k)
+        assert recs[k - 1]["max_area_error"] == pytest.approx(ref.max_area_error, abs=1e-9)
+        assert sum(r["steps_accepted"] for r in recs[:k]) == ref.steps_accepted
+        assert sum(r["steps_rejected"] for r in recs[:k]) == ref.steps_rejected
+    with _ctx(m, 1.0, "fp64", use_graph=use_graph) as c:
+        with pytest.raises(P.CartogramError) as e:
+            c.iteration_record(0)  # no history yet
+        assert e.value.code == P.CG_EINVAL
