@@ -84,6 +84,7 @@ struct cg_ctx {
   void* AB = nullptr;        // pass-1 output
   void* vbuf[2] = {nullptr, nullptr};
   void* dbuf[2] = {nullptr, nullptr};
+  void* ubuf[2] = {nullptr, nullptr};  // cached predictor velocities, by parity like dbuf
   void* dres = nullptr;      // displacements of the last integration
   void* rho_tmp = nullptr;   // density output of the field entry point
   void* phi = nullptr;       // linear flow: Phi~ = rho~ / (pi^2 k^2) in the working type
@@ -314,6 +315,7 @@ int alloc_fields(cg_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     CG_CUDA(c, cudaMalloc(&c->vbuf[k], sizeof(V2<T>) * N));
     CG_CUDA(c, cudaMalloc(&c->dbuf[k], sizeof(V2<T>) * N));
+    CG_CUDA(c, cudaMalloc(&c->ubuf[k], sizeof(V2<T>) * N));
   }
   CG_CUDA(c, cudaMalloc(&c->dres, sizeof(V2<T>) * N));
   CG_CUDA(c, cudaMemset(c->dres, 0, sizeof(V2<T>) * N));
@@ -387,6 +389,7 @@ void enqueue_init(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStr
   cg::launch_init_state(c->st, sp, s);
   cudaMemsetAsync(c->dbuf[0], 0, sizeof(V2<T>) * (size_t)c->Lx * c->Ly, s);
   enqueue_field<T>(c, cg::kModeInit, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s);
+  cg::launch_gather_u<T>((const V2<T>*)c->vbuf[0], (const V2<T>*)c->dbuf[0], (V2<T>*)c->ubuf[0], c->Lx, c->Ly, s);
   cg::launch_init_finish(c->st, sp, h, use_cond, s);
 }
 
@@ -398,8 +401,8 @@ void enqueue_body(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStr
   const int mode = (k & 1) ? cg::kModeStepOdd : cg::kModeStep;
   enqueue_field<T>(c, mode, 0.0, (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], nullptr, s, h, use_cond);
   cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, mode, 0.0, h,
-                     use_cond, c->tune.heun_bps, s);
+                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], (V2<T>*)c->ubuf[0], (V2<T>*)c->ubuf[1],
+                     c->Lx, c->Ly, mode, 0.0, h, use_cond, c->tune.heun_bps, s);
 }
 
 // Linear flow, once per integration: Phi~, the flux J = -grad Phi and rho0 at the cell
@@ -421,13 +424,14 @@ void enqueue_init_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, 
   cudaMemsetAsync(&c->st->dev_bits, 0, sizeof(unsigned long long), s);
   cg::launch_linear_init<T>(c->st, sp, (const V2<T>*)c->flux, (const T*)c->rho0, (V2<T>*)c->vbuf[0],
                             c->Lx * c->Ly, h, use_cond, s);
+  cg::launch_gather_u<T>((const V2<T>*)c->vbuf[0], (const V2<T>*)c->dbuf[0], (V2<T>*)c->ubuf[0], c->Lx, c->Ly, s);
 }
 
 template <typename T>
 void enqueue_body_linear(cg_ctx* c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   cg::launch_linear_step<T>(c->st, step_params(c), (const V2<T>*)c->flux, (const T*)c->rho0,
                             (V2<T>*)c->vbuf[0], (V2<T>*)c->vbuf[1], (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1],
-                            c->Lx, c->Ly, h, use_cond, (unsigned int)c->opt.max_steps + 8u, c->tune.heun_bps, s);
+                            (V2<T>*)c->ubuf[0], (V2<T>*)c->ubuf[1], c->Lx, c->Ly, h, use_cond, (unsigned int)c->opt.max_steps + 8u, c->tune.heun_bps, s);
 }
 
 template <typename T>
@@ -499,12 +503,13 @@ int do_autotune(cg_ctx* c, int reps) {
   const StepParams sp = step_params(c);
   // resident blocks per SM of the step kernel: its 256-thread blocks fit five to an SM at
   // 48 registers, so the counts around that are tried too
+  cg::launch_gather_u<T>((const V2<T>*)c->vbuf[0], (const V2<T>*)c->dbuf[0], (V2<T>*)c->ubuf[0], c->Lx, c->Ly, s);
   for (int bps : {2, 3, 4, 5, 6, 8, 16}) {
     double ms;
     if ((r = timeit([&] {
            cg::launch_heun<T>(c->st, sp, (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                              (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h,
-                              0, 0, bps, s);
+                              (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], (V2<T>*)c->ubuf[0], (V2<T>*)c->ubuf[1],
+                              c->Lx, c->Ly, cg::kModeFixed, h, 0, 0, bps, s);
          }, &ms)))
       return r;
     if (ms < best_ms[2]) { best_ms[2] = ms; best.heun_bps = bps; }
@@ -1058,9 +1063,12 @@ int do_heun(cg_ctx* c, double t, double h, const double* din, double* dout, doub
   int r = copy_field_in<T>(c, din, c->dbuf[0], 2);
   if (r) return r;
   CG_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  // the step loop's kernel: predictor velocities gathered once, then read from the cache
+  cg::launch_gather_u<T>((const V2<T>*)c->vbuf[0], (const V2<T>*)c->dbuf[0], (V2<T>*)c->ubuf[0], c->Lx, c->Ly,
+                         c->stream);
   cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0,
-                     c->tune.heun_bps, c->stream);
+                     (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], (V2<T>*)c->ubuf[0], (V2<T>*)c->ubuf[1], c->Lx,
+                     c->Ly, cg::kModeFixed, h, 0, 0, c->tune.heun_bps, c->stream);
   CG_CUDA(c, cudaGetLastError());
   if ((r = copy_field_out<T>(c, c->dbuf[1], dout, 2))) return r;
   DevState hs;
@@ -1288,7 +1296,8 @@ void adj_fields(cg_ctx* c, const std::vector<double>& sch, int n0, int m) {
 
 // One predictor-corrector step of all points with the fixed step h (the step kernel).
 void adj_step(cg_ctx* c, const double2* v0, const double2* v1, const double2* din, double2* dout, double h) {
-  cg::launch_heun<double>(c->st, step_params(c), v0, v1, (double2*)din, dout, c->Lx, c->Ly, cg::kModeFixed, h, 0,
+  cg::launch_heun<double>(c->st, step_params(c), v0, v1, (double2*)din, dout, nullptr, nullptr, c->Lx, c->Ly,
+                          cg::kModeFixed, h, 0,
                           0, c->tune.heun_bps, c->stream);
 }
 
@@ -1595,6 +1604,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
   const double t = 1.0, h = 0.5;
   enqueue_field<T>(c, cg::kModeFixed, t, (V2<T>*)c->vbuf[0], nullptr, nullptr, s);
   enqueue_field<T>(c, cg::kModeFixed, t + h, (V2<T>*)c->vbuf[1], nullptr, nullptr, s);
+  cg::launch_gather_u<T>((const V2<T>*)c->vbuf[0], (const V2<T>*)c->dbuf[0], (V2<T>*)c->ubuf[0], c->Lx, c->Ly, s);
   for (int k = 0; k < 6; ++k) {
     CG_CUDA(c, cudaEventRecord(a, s));
     for (int r = 0; r < reps; ++r) {
@@ -1610,8 +1620,8 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
           break;
         case 2:
           cg::launch_heun<T>(c->st, step_params(c), (const V2<T>*)c->vbuf[0], (const V2<T>*)c->vbuf[1],
-                             (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], c->Lx, c->Ly, cg::kModeFixed, h, 0, 0,
-                             c->tune.heun_bps, s);
+                             (V2<T>*)c->dbuf[0], (V2<T>*)c->dbuf[1], (V2<T>*)c->ubuf[0], (V2<T>*)c->ubuf[1],
+                             c->Lx, c->Ly, cg::kModeFixed, h, 0, 0, c->tune.heun_bps, s);
           break;
         case 3:
           run_raster(c);
@@ -2225,7 +2235,7 @@ void cartogram_destroy(cg_ctx* c) {
   free_regions(c);
   void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wyff, c->Eyff, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
-                c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
+                c->ubuf[0], c->ubuf[1], c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
                 c->rho0, c->diag, c->deadline};
   for (void* p : ps)
     if (p) cudaFree(p);

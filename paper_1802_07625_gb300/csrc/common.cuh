@@ -255,6 +255,21 @@ __device__ __forceinline__ LoopSlot loop_decide(const LoopSlot& p, const StepPar
   return n;
 }
 
+// Bit patterns of non-negative values in the working type's own width (they order like
+// the values), so that block reductions convert to FP64 once per block, not per warp:
+// GB300's FP64 pipe is narrow, and every conversion to or from double uses it.
+template <typename T> struct OrdBits;
+template <> struct OrdBits<float> {
+  using U = unsigned int;
+  static __device__ __forceinline__ U of(float v) { return __float_as_uint(v); }
+  static __device__ __forceinline__ double value(U u) { return (double)__uint_as_float(u); }
+};
+template <> struct OrdBits<double> {
+  using U = unsigned long long;
+  static __device__ __forceinline__ U of(double v) { return (U)__double_as_longlong(v); }
+  static __device__ __forceinline__ double value(U u) { return __longlong_as_double((long long)u); }
+};
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   // non-negative doubles order like their bit patterns
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));

@@ -159,10 +159,17 @@ void launch_fwd(int log2Lx, int log2Ly, const double* rho, double* R, double* sp
                 const double2* Wx, const double2* Ex, const double2* Wy, const double2* Ey,
                 const double* bx, const double* by, cudaStream_t s);
 
+// One predictor-corrector step of all grid points. u0, u1 (both null or both set): the
+// cached predictor velocities by parity, read from u[p] and written to u[1 - p] (see
+// heun_kernel); null: the predictor velocities are interpolated.
 template <typename T>
 void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
-                 V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
-                 int use_cond, int blocks_per_sm, cudaStream_t s);
+                 V2<T>* d1, V2<T>* u0, V2<T>* u1, int Lx, int Ly, int mode, double h,
+                 cudaGraphConditionalHandle handle, int use_cond, int blocks_per_sm, cudaStream_t s);
+// u = v interpolated at the grid points displaced by d (the cached predictor velocities
+// at the start of an integration).
+template <typename T>
+void launch_gather_u(const V2<T>* v, const V2<T>* d, V2<T>* u, int Lx, int Ly, cudaStream_t s);
 int sm_count();
 // Read `bytes` (a multiple of 16) of p, `passes` times, bypassing L1.
 void launch_read_bw(const void* p, size_t bytes, int passes, float* sink, cudaStream_t s);
@@ -188,8 +195,9 @@ void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, cons
                         cudaGraphConditionalHandle handle, int use_cond, cudaStream_t s);
 template <typename T>
 void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0,
-                        V2<T>* v1, V2<T>* d0, V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle,
-                        int use_cond, unsigned int max_body, int blocks_per_sm, cudaStream_t s);
+                        V2<T>* v1, V2<T>* d0, V2<T>* d1, V2<T>* u0, V2<T>* u1, int Lx, int Ly,
+                        cudaGraphConditionalHandle handle, int use_cond, unsigned int max_body, int blocks_per_sm,
+                        cudaStream_t s);
 // Outer iteration on the device: blur factors (of o->sigma[o->iterations], or of sigma
 // when o is null), storing an integration's projected grid, and the loop decision.
 void launch_blur_tables(const OuterState* o, double sigma, double* bx, double* by, int Lx, int Ly,

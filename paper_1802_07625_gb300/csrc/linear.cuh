@@ -37,23 +37,39 @@ __global__ void __launch_bounds__(256) linear_velocity_kernel(DevState* st, cons
                                                                V2<T>* vbuf1, int N, int mode,
                                                                cudaGraphConditionalHandle handle, int use_cond,
                                                                unsigned int max_body) {
-  __shared__ unsigned long long s_v2;
+  using OB = OrdBits<T>;
+  __shared__ typename OB::U s_v2;
   __shared__ unsigned int s_warps;
+  __shared__ int s_run, s_par;
+  __shared__ T s_t1;
   if (threadIdx.x == 0) {
-    s_v2 = 0ull;
+    s_v2 = 0;
     s_warps = 0u;
   }
-  __syncthreads();
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const bool step = mode == kModeLinear;
-  if (step && blockIdx.x == 0 && threadIdx.x == 0) {
-    const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
-    if (st->status == kRunning && it > max_body) st->status = kStepFail;
-    if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+  if (threadIdx.x == 0) {
+    // the attempt's end in the working type, converted once per block
+    int run = 1, par = 0;
+    double t1 = 0.0;
+    if (step) {
+      if (blockIdx.x == 0) {
+        const unsigned int it = atomicAdd(&st->body_iters, 1u) + 1u;
+        if (st->status == kRunning && it > max_body) st->status = kStepFail;
+        if (st->status != kRunning && use_cond) cudaGraphSetConditional(handle, 0);
+      }
+      run = st->status == kRunning;
+      par = st->parity;
+      t1 = linear_t1(st->t, st->h);
+    }
+    s_run = run;
+    s_par = par;
+    s_t1 = (T)t1;
   }
-  if (step && st->status != kRunning) return;
-  const T t1 = step ? (T)linear_t1(st->t, st->h) : T(0);
-  V2<T>* out = step ? (st->parity ? vbuf0 : vbuf1) : vbuf0;
+  __syncthreads();
+  if (!s_run) return;
+  const T t1 = s_t1;
+  V2<T>* out = step ? (s_par ? vbuf0 : vbuf1) : vbuf0;
   T v2 = T(0);
   bool bad = false;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
@@ -70,11 +86,11 @@ __global__ void __launch_bounds__(256) linear_velocity_kernel(DevState* st, cons
   bad = __any_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
     if (bad && !step) st->bad = 1;
-    atomicMax(&s_v2, (unsigned long long)__double_as_longlong((double)v2));
+    atomicMax(&s_v2, OB::of(v2));
     __threadfence_block();
     if (atomicAdd(&s_warps, 1u) == (blockDim.x >> 5) - 1) {
       __threadfence_block();
-      atomic_max_nonneg(&st->vmax2_bits, __longlong_as_double((long long)atomicOr(&s_v2, 0ull)));
+      atomic_max_nonneg(&st->vmax2_bits, OB::value(atomicOr(&s_v2, (typename OB::U)0)));
     }
   }
 }

@@ -94,7 +94,8 @@ template <typename T>
 __device__ __noinline__ T heun_pairs_call(const V2<T>* vcur, const V2<T>* vnew, const V2<T>* din,
                                           V2<T>* dout, int Lx, int Ly, int log2Lx, double hd, int q0,
                                           int qstride) {
-  return heun_pairs<T>(vcur, vnew, din, dout, Lx, Ly, log2Lx, hd, q0, qstride);
+  return heun_pairs<T, false>(vcur, vnew, din, dout, nullptr, nullptr, Lx, Ly, log2Lx, (T)hd, (T)(0.5 * hd), q0,
+                             qstride);
 }
 
 template <typename T>

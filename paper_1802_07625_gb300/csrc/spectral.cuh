@@ -79,10 +79,20 @@ __device__ __forceinline__ void p1_issue(const T* __restrict__ spec, const V2<T>
   }
 }
 
-// Rest of a pass-1 item once its copies are issued: damping at tau, packing, FFT,
-// transposed write. All threads call it; false if the copies did not complete.
+// Damping rates of the diffusion time tau in the working type: kx = pi^2 tau / Lx^2,
+// ky = pi^2 tau / Ly^2 (Lx = 2^LOG2N).
 template <typename T, int LOG2N>
-__device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S, int n0, double tau,
+__device__ __forceinline__ void damp_rates(double tau, int Ly, T& kx, T& ky) {
+  constexpr int N = 1 << LOG2N;
+  kx = (T)(kPi * kPi * tau / ((double)N * N));
+  ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
+}
+
+// Rest of a pass-1 item once its copies are issued: damping with the rates kx, ky
+// (damp_rates), packing, FFT, transposed write. All threads call it; false if the
+// copies did not complete.
+template <typename T, int LOG2N>
+__device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S, int n0, T kx, T ky,
                                           unsigned char* smem, uint64_t* bar, uint32_t& ph) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
@@ -93,8 +103,6 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   C* buf = reinterpret_cast<C*>(stage + S * N);
   T* fx = reinterpret_cast<T*>(buf + S * F::SSTRIDE);
   T* fyS = fx + N;
-  const T kx = (T)(kPi * kPi * tau / ((double)N * N));
-  const T ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
   for (int i = threadIdx.x; i < N; i += blockDim.x) fx[i] = texp(-kx * (T)i * (T)i) / (T)N;
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
     const T n = (T)(n0 + s);
@@ -162,7 +170,9 @@ __device__ __forceinline__ bool p1_rows(const T* __restrict__ spec, V2<T>* __res
                                         int Ly, int S, int n0, double tau, unsigned char* smem,
                                         uint64_t* bar, uint32_t& ph) {
   p1_issue<T, LOG2N>(spec, Wg, Eg, S, n0, smem, bar);
-  return p1_finish<T, LOG2N>(ABt, Ly, S, n0, tau, smem, bar, ph);
+  T kx, ky;
+  damp_rates<T, LOG2N>(tau, Ly, kx, ky);
+  return p1_finish<T, LOG2N>(ABt, Ly, S, n0, kx, ky, smem, bar, ph);
 }
 
 // A complex value in the arithmetic type A.
@@ -346,16 +356,19 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   p1_issue<T, LOG2N>(spec, Wg, Eg, S, blockIdx.x * S, smem_raw, &bar);
-  __shared__ double s_tau;
+  __shared__ T s_k[2];
   __shared__ int s_run;
   pdl_wait();
-  double tau = tau_fixed;
-  if (is_step_mode(mode)) {
-    // first kernel of an attempt: the controller's decision on the previous attempt
-    // (every block computes it; block 0 stores it as this attempt's state, ends the
-    // loop when the integration is over or has run more attempts than it allows, and
-    // then also commits the final state)
-    if (threadIdx.x == 0) {
+  // thread 0 takes the attempt's time and the damping rates (FP64 arithmetic, once per
+  // block: GB300's FP64 pipe is narrow)
+  if (threadIdx.x == 0) {
+    double tau = tau_fixed;
+    int run = 1;
+    if (is_step_mode(mode)) {
+      // first kernel of an attempt: the controller's decision on the previous attempt
+      // (every block computes it; block 0 stores it as this attempt's state, ends the
+      // loop when the integration is over or has run more attempts than it allows, and
+      // then also commits the final state)
       const int b = step_slot(mode);
       LoopSlot n = loop_decide(load_slot(&st->ls[b ^ 1]), load_sp(st), blockIdx.x == 0);
       if (blockIdx.x == 0) {
@@ -389,24 +402,25 @@ __global__ void inv_rows_kernel(const T* __restrict__ spec, V2<T>* __restrict__ 
           if (use_cond) cudaGraphSetConditional(handle, 0);
         }
       }
-      s_run = n.status == kRunning;
-      s_tau = n.t + n.h;
+      run = n.status == kRunning;
+      tau = n.t + n.h;
+    } else if (mode == kModeInit) {
+      run = st->status == kRunning;
+      tau = st->t;
     }
-    __syncthreads();
-    if (!s_run) {
-      mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
-      return;
-    }
-    tau = s_tau;
-  } else if (mode == kModeInit) {
-    if (st->status != kRunning) {
-      mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
-      return;
-    }
-    tau = st->t;
+    s_run = run;
+    T kx, ky;
+    damp_rates<T, LOG2N>(tau, Ly, kx, ky);
+    s_k[0] = kx;
+    s_k[1] = ky;
+  }
+  __syncthreads();
+  if (!s_run) {
+    mbar_wait_bounded(&bar, 0, kMbarTries);  // no copy may be left in flight
+    return;
   }
   uint32_t ph = 0;
-  if (!p1_finish<T, LOG2N>(ABt, Ly, S, blockIdx.x * S, tau, smem_raw, &bar, ph) && threadIdx.x == 0) {
+  if (!p1_finish<T, LOG2N>(ABt, Ly, S, blockIdx.x * S, s_k[0], s_k[1], smem_raw, &bar, ph) && threadIdx.x == 0) {
     if (is_step_mode(mode)) atomicOr(&st->ls[step_slot(mode)].bad, 1);
     else st->bad = 2;
   }

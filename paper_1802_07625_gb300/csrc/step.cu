@@ -53,16 +53,28 @@ void launch_read_bw(const void* p, size_t bytes, int passes, float* sink, cudaSt
 
 template <typename T>
 void launch_heun(DevState* st, const StepParams& sp, const V2<T>* v0, const V2<T>* v1, V2<T>* d0,
-                 V2<T>* d1, int Lx, int Ly, int mode, double h, cudaGraphConditionalHandle handle,
-                 int use_cond, int blocks_per_sm, cudaStream_t s) {
+                 V2<T>* d1, V2<T>* u0, V2<T>* u1, int Lx, int Ly, int mode, double h,
+                 cudaGraphConditionalHandle handle, int use_cond, int blocks_per_sm, cudaStream_t s) {
   int log2Lx = 0;
   while ((1 << log2Lx) < Lx) ++log2Lx;
   // a grid-stride loop over point pairs with a few resident blocks per SM keeps the
   // number of same-address atomics of the block reductions small
   const int pairs = Lx * Ly / 2;
   if (blocks_per_sm <= 0) blocks_per_sm = 8;
-  launch_pdl(heun_kernel<T>, blocks_for(pairs, 256, sm_count() * blocks_per_sm), 256, 0, s, st, sp, v0,
-             v1, d0, d1, Lx, Ly, log2Lx, mode, h, handle, use_cond);
+  const int blocks = blocks_for(pairs, 256, sm_count() * blocks_per_sm);
+  if (u0)
+    launch_pdl(heun_kernel<T, true>, blocks, 256, 0, s, st, sp, v0, v1, d0, d1, u0, u1, Lx, Ly, log2Lx, mode, h,
+               handle, use_cond);
+  else
+    launch_pdl(heun_kernel<T, false>, blocks, 256, 0, s, st, sp, v0, v1, d0, d1, (V2<T>*)nullptr,
+               (V2<T>*)nullptr, Lx, Ly, log2Lx, mode, h, handle, use_cond);
+}
+
+template <typename T>
+void launch_gather_u(const V2<T>* v, const V2<T>* d, V2<T>* u, int Lx, int Ly, cudaStream_t s) {
+  int log2Lx = 0;
+  while ((1 << log2Lx) < Lx) ++log2Lx;
+  gather_u_kernel<T><<<blocks_for((long long)Lx * Ly, 256, sm_count() * 8), 256, 0, s>>>(v, d, u, Lx, Ly, log2Lx);
 }
 
 void launch_init_state(DevState* st, const StepParams& sp, cudaStream_t s) {
@@ -131,12 +143,13 @@ void launch_linear_init(DevState* st, const StepParams& sp, const V2<T>* J, cons
 
 template <typename T>
 void launch_linear_step(DevState* st, const StepParams& sp, const V2<T>* J, const T* rho0, V2<T>* v0,
-                        V2<T>* v1, V2<T>* d0, V2<T>* d1, int Lx, int Ly, cudaGraphConditionalHandle handle,
-                        int use_cond, unsigned int max_body, int blocks_per_sm, cudaStream_t s) {
+                        V2<T>* v1, V2<T>* d0, V2<T>* d1, V2<T>* u0, V2<T>* u1, int Lx, int Ly,
+                        cudaGraphConditionalHandle handle, int use_cond, unsigned int max_body, int blocks_per_sm,
+                        cudaStream_t s) {
   const int N = Lx * Ly;
   launch_pdl(linear_velocity_kernel<T>, blocks_for(N, 256, sm_count() * 8), 256, 0, s, st, J, rho0, v0, v1, N,
              (int)kModeLinear, handle, use_cond, max_body);
-  launch_heun<T>(st, sp, v0, v1, d0, d1, Lx, Ly, kModeLinear, 0.0, handle, use_cond, blocks_per_sm, s);
+  launch_heun<T>(st, sp, v0, v1, d0, d1, u0, u1, Lx, Ly, kModeLinear, 0.0, handle, use_cond, blocks_per_sm, s);
 }
 
 void launch_blur_tables(const OuterState* o, double sigma, double* bx, double* by, int Lx, int Ly,
@@ -271,8 +284,9 @@ void launch_map_adjoint(const double2* xy_pre, const double2* g, double* lamD, i
 
 #define CG_INSTANTIATE_STEP(T)                                                                      \
   template void launch_heun<T>(DevState*, const StepParams&, const V2<T>*, const V2<T>*, V2<T>*,    \
-                               V2<T>*, int, int, int, double, cudaGraphConditionalHandle, int, int, \
-                               cudaStream_t);                                                       \
+                               V2<T>*, V2<T>*, V2<T>*, int, int, int, double,                       \
+                               cudaGraphConditionalHandle, int, int, cudaStream_t);                 \
+  template void launch_gather_u<T>(const V2<T>*, const V2<T>*, V2<T>*, int, int, cudaStream_t);     \
   template void launch_snapshot<T>(const DevState*, const V2<T>*, const V2<T>*, V2<T>*, int,        \
                                    cudaStream_t);                                                   \
   template void launch_map_points<T>(const double2*, double2*, long long, const V2<T>*, int, int,   \
@@ -287,8 +301,8 @@ void launch_map_adjoint(const double2* xy_pre, const double2* g, double* lamD, i
   template void launch_linear_init<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
                                       int, cudaGraphConditionalHandle, int, cudaStream_t);          \
   template void launch_linear_step<T>(DevState*, const StepParams&, const V2<T>*, const T*, V2<T>*, \
-                                      V2<T>*, V2<T>*, V2<T>*, int, int, cudaGraphConditionalHandle, \
-                                      int, unsigned int, int, cudaStream_t);
+                                      V2<T>*, V2<T>*, V2<T>*, V2<T>*, V2<T>*, int, int,             \
+                                      cudaGraphConditionalHandle, int, unsigned int, int, cudaStream_t);
 CG_INSTANTIATE_STEP(float)
 CG_INSTANTIATE_STEP(double)
 
