@@ -203,8 +203,22 @@ void stamp_deadline(cg_ctx* c, bool limited = true) {
   cg::launch_deadline(c->deadline, ns > 0.0 ? (unsigned long long)ns + 1ull : 0ull, c->stream);
 }
 
+// Bit pattern of the largest x >= 0 with sqrt(x) <= atol (double arithmetic; sqrt is
+// correctly rounded on host and device alike): the step controller's accept test on the
+// squared error.
+unsigned long long err2_accept_bits(double atol) {
+  double x = atol * atol;
+  for (int k = 0; k < 64 && x < HUGE_VAL && std::sqrt(std::nextafter(x, HUGE_VAL)) <= atol; ++k)
+    x = std::nextafter(x, HUGE_VAL);
+  for (int k = 0; k < 64 && x > 0.0 && std::sqrt(x) > atol; ++k) x = std::nextafter(x, 0.0);
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+}
+
 StepParams step_params(const cg_ctx* c) {
   StepParams sp;
+  sp.err2_accept_bits = err2_accept_bits(c->opt.atol);
   sp.dt0 = c->opt.dt0;
   sp.atol = c->opt.atol;
   sp.grow = c->opt.grow;

@@ -31,6 +31,10 @@ constexpr double kPi = 3.14159265358979323846;
 struct StepParams {
   double dt0, atol, grow, shrink, cfl, rho_tol, h_min;
   long long max_steps;
+  // bit pattern of the largest x >= 0 with sqrt(x) <= atol in double arithmetic (the
+  // square root is correctly rounded and monotone), so that the accept test on the
+  // squared error needs no FP64 square root: sqrt(e2) <= atol  <=>  bits(e2) <= this
+  unsigned long long err2_accept_bits;
   double* sched;  // if not null: (t, h) of every accepted step, [max_steps][2]
   // if not null: device-clock deadline of the call in ns (0: none), written at its start
   const unsigned long long* deadline;
@@ -198,6 +202,7 @@ __device__ __forceinline__ StepParams load_sp(const DevState* st) {
   r.rho_tol = __ldcg(&st->sp.rho_tol);
   r.h_min = __ldcg(&st->sp.h_min);
   r.max_steps = __ldcg(&st->sp.max_steps);
+  r.err2_accept_bits = __ldcg(&st->sp.err2_accept_bits);
   r.sched = (double*)__ldcg((const long long*)&st->sp.sched);
   r.deadline = (const unsigned long long*)__ldcg((const long long*)&st->sp.deadline);
   return r;
@@ -222,14 +227,16 @@ __device__ __forceinline__ LoopSlot loop_decide(const LoopSlot& p, const StepPar
   if (p.status != kRunning) return n;
   n.pending = 1;
   if (!p.pending) return n;  // the integration's first attempt
-  const double e = sqrt(__longlong_as_double((long long)p.err2_bits));
-  const double vmax_new = sqrt(__longlong_as_double((long long)p.vmax2_bits));
-  const double dev_new = __longlong_as_double((long long)p.dev_bits);
+  // The decision is on the critical path of every attempt and GB300's FP64 pipe is
+  // narrow: the accept and stop tests compare bit patterns of non-negative doubles
+  // (ordered like their values), and the new field's speed (a square root) is taken
+  // only on acceptance. The outcome is that of the plain formulas: accept iff
+  // sqrt(err2) <= atol; done iff dev <= rho_tol; cap h at cfl / vmax.
   int status = kRunning;
   double h = p.h;
   if (p.bad & 1) {
     status = kStepFail;
-  } else if (e <= sp.atol) {
+  } else if (p.err2_bits <= sp.err2_accept_bits) {
     if (record && sp.sched) {
       sp.sched[2 * p.accepted] = p.t;
       sp.sched[2 * p.accepted + 1] = h;
@@ -237,8 +244,8 @@ __device__ __forceinline__ LoopSlot loop_decide(const LoopSlot& p, const StepPar
     n.parity = p.parity ^ 1;
     n.t = p.t + h;
     n.accepted = p.accepted + 1;
-    n.vmax = vmax_new;
-    if (dev_new <= sp.rho_tol) status = kDone;
+    n.vmax = sqrt(__longlong_as_double((long long)p.vmax2_bits));
+    if (p.dev_bits <= (unsigned long long)__double_as_longlong(sp.rho_tol)) status = kDone;
     else h *= sp.grow;
   } else {
     n.rejected = p.rejected + 1;

@@ -81,11 +81,14 @@ __device__ __forceinline__ void p1_issue(const T* __restrict__ spec, const V2<T>
 
 // Damping rates of the diffusion time tau in the working type: kx = pi^2 tau / Lx^2,
 // ky = pi^2 tau / Ly^2 (Lx = 2^LOG2N).
+// The divisions by the squared sizes (powers of two) are exact, so they are taken as
+// multiplications by the exact reciprocals (FP64 division is slow on GB300).
 template <typename T, int LOG2N>
 __device__ __forceinline__ void damp_rates(double tau, int Ly, T& kx, T& ky) {
-  constexpr int N = 1 << LOG2N;
-  kx = (T)(kPi * kPi * tau / ((double)N * N));
-  ky = (T)(kPi * kPi * tau / ((double)Ly * Ly));
+  const double pt = kPi * kPi * tau;
+  const int log2Ly = __ffs(Ly) - 1;
+  kx = (T)(pt * __longlong_as_double((long long)(1023 - 2 * LOG2N) << 52));
+  ky = (T)(pt * __longlong_as_double((long long)(1023 - 2 * log2Ly) << 52));
 }
 
 // Rest of a pass-1 item once its copies are issued: damping with the rates kx, ky
