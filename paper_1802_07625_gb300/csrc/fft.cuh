@@ -12,9 +12,11 @@
 // The register DFTs are radix-2 decimation in time with every twiddle a compile-time
 // constant: cos and sin of 2 pi j / n are evaluated at compile time from their Taylor
 // series after an exact integer reduction to the first quadrant; multiplications by
-// 1 and by +-i are elided.
+// 1 and by +-i are elided, and the other butterflies take their sum and difference by
+// fused multiply-adds (u + w v directly, u - w v as 2u - (u + w v)).
 #pragma once
 
+#include <type_traits>
 #include <utility>
 
 #include "common.cuh"
@@ -71,6 +73,18 @@ __device__ __forceinline__ void butterfly(C (&a)[R]) {
     if constexpr (4 * J == 2 * HALF) {
       // multiply by +i (inverse) or -i (forward)
       v = INV ? mk2<T>(-v.y, v.x) : mk2<T>(v.y, -v.x);
+    } else if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) {
+      // u + w v by two fused multiply-adds per component, u - w v as 2u - (u + w v):
+      // six instructions instead of a complex product and two complex additions
+      constexpr double wr = cos2pi(J, 2 * HALF);
+      constexpr double wi = (INV ? 1.0 : -1.0) * sin2pi(J, 2 * HALF);
+      const T r = (T)wr, i = (T)wi;
+      const C u = a[U];
+      const T px = fma(-v.y, i, fma(v.x, r, u.x));
+      const T py = fma(v.y, r, fma(v.x, i, u.y));
+      a[U] = mk2<T>(px, py);
+      a[U + HALF] = mk2<T>(fma(T(2), u.x, -px), fma(T(2), u.y, -py));
+      return;
     } else {
       constexpr double wr = cos2pi(J, 2 * HALF);
       constexpr double wi = (INV ? 1.0 : -1.0) * sin2pi(J, 2 * HALF);

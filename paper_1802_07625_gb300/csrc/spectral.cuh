@@ -41,6 +41,12 @@ __device__ __forceinline__ void st_two(double* p, double a, double b) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
+// 1 / x, correctly rounded (the FP32 one by the reciprocal instruction rather than a
+// general division).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+template <typename A> __device__ __forceinline__ A recip(A x) { return A(1) / x; }
+
 // Output index i of a cosine sum -> index of the complex DFT output that holds it.
 __device__ __forceinline__ int dct3_src(int i, int N) { return (i & 1) ? (N - 1 - (i >> 1)) : (i >> 1); }
 
@@ -309,7 +315,7 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
       const A gx = h ? u2.y : u2.x;
       const A rho = A(1) + rp;
       if (!raw) bad |= !(rho > A(0));
-      const A inv = raw ? A(1) : A(1) / rho;
+      const A inv = raw ? A(1) : recip(rho);
       const T vx = (T)(-gx * inv), vy = (T)(-gy * inv);
       vv[h] = mk2<T>(vx, vy);
       rr[h] = (T)(raw ? rp : rho);  // flux mode: the plain cosine sum
