@@ -185,12 +185,12 @@ def read_bandwidths(P):
 
 def launches_per_cartogram(iterations, attempted):
     """Kernels the library launches for one cartogram_integrate call on the device-side
-    outer loop: initial areas (3) and loop decision (1); per iteration rasterise (2), blur
+    outer loop: initial areas (4) and loop decision (1); per iteration rasterise (2), blur
     factors (1), forward transform (2), integration init (5: state, pass 1, pass 2,
     predictor velocities at the grid points, finish), the step-loop body (3 kernels per attempted step, 8 attempts per body, so
     on average 10.5 launches of finished attempts per integration that return at once),
-    snapshot and outcome (2), history store (1), vertex map (1), areas (3), decision (1)."""
-    return int(round(4 + iterations * (2 + 1 + 2 + 5 + 10.5 + 2 + 1 + 1 + 3 + 1) + 3 * attempted))
+    snapshot and outcome (2), history store (1), vertex map (1), areas (4), decision (1)."""
+    return int(round(5 + iterations * (2 + 1 + 2 + 5 + 10.5 + 2 + 1 + 1 + 4 + 1) + 3 * attempted))
 
 
 def bytes_per_point(esz):

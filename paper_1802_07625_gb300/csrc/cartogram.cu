@@ -104,6 +104,10 @@ struct cg_ctx {
   long long* ring_off = nullptr;
   int* reg_off = nullptr;
   int* reg_rings = nullptr;
+  int* chunk_ring = nullptr;      // area sums: the ring of every vertex chunk
+  int* ring_chunk_off = nullptr;  // ring k's chunks are [ring_chunk_off[k], ring_chunk_off[k+1])
+  double* chunk_sum = nullptr;    // one shoelace partial sum per chunk
+  long long n_chunks = 0;
   int* next = nullptr;
   int* vreg = nullptr;
   double2* xy = nullptr;
@@ -214,6 +218,15 @@ unsigned long long err2_accept_bits(double atol) {
   unsigned long long b;
   memcpy(&b, &x, sizeof b);
   return b;
+}
+
+cg::AreaChunks area_chunks(const cg_ctx* c) {
+  cg::AreaChunks ch;
+  ch.chunk_ring = c->chunk_ring;
+  ch.ring_chunk_off = c->ring_chunk_off;
+  ch.n_chunks = c->n_chunks;
+  ch.chunk_sum = c->chunk_sum;
+  return ch;
 }
 
 StepParams step_params(const cg_ctx* c) {
@@ -620,7 +633,7 @@ cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaS
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, 0);
   if (e != cudaSuccess) return e;
   cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings, c->values, c->R_n,
-                   c->area, c->err_d, c->w, c->info, cs);
+                   c->area, c->err_d, c->w, c->info, area_chunks(c), cs);
   cg::launch_outer_decide(c->outer, c->info, ho, 0, cs);
   const int N = c->Lx * c->Ly;
   return capture_while(cs, bs, ho, [&](cudaStream_t s) {
@@ -634,7 +647,7 @@ cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaS
     cg::launch_outer_commit<T>(c->outer, c->info, (const V2<T>*)c->dres, N, s);
     cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s, &c->outer->status);
     cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings, c->values, c->R_n,
-                     c->area, c->err_d, c->w, c->info, s);
+                     c->area, c->err_d, c->w, c->info, area_chunks(c), s);
     cg::launch_outer_decide(c->outer, c->info, ho, 1, s);
     return cudaGetLastError();
   });
@@ -791,7 +804,7 @@ int run_raster(cg_ctx* c) {
 
 int run_areas(cg_ctx* c) {
   cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings,
-                   c->values, c->R_n, c->area, c->err_d, c->w, c->info, c->stream);
+                   c->values, c->R_n, c->area, c->err_d, c->w, c->info, area_chunks(c), c->stream);
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;
 }
@@ -1453,7 +1466,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
     decay[k] = std::pow(c->opt.blur_decay, (double)(c->hist_len + k));
     sigma[k] = blur * decay[k];
     cg::launch_areas(a->X[k], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R,
-                     c->area, c->err_d, c->w, c->info, s);
+                     c->area, c->err_d, c->w, c->info, area_chunks(c), s);
     CG_CUDA(c, cudaMemcpyAsync(A[k].data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
     CG_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(double) * N, s));
     cg::launch_raster(a->X[k], c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, nv, s);
@@ -1494,7 +1507,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
   c->blur_tab_sigma = -1.0;
   // the loss on the final vertices
   cg::launch_areas(a->X[K], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R, c->area,
-                   c->err_d, c->w, c->info, s);
+                   c->err_d, c->w, c->info, area_chunks(c), s);
   std::vector<double> A1(R);
   std::vector<double2> X0(nv), X1(nv);
   CG_CUDA(c, cudaMemcpyAsync(A1.data(), c->area, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
@@ -1568,7 +1581,7 @@ int do_iteration_gradient(cg_ctx* c, const double* values_in, double blur, doubl
                                   (const double2*)c->Wy, (const double2*)c->Ey, c->st, cg::kModeFlux, s);
       // the iteration's region weights again (for the coverage adjoint of its vertices)
       cg::launch_areas(a->X[k], c->ring_off, c->area_sums, c->reg_off, c->reg_rings, a->vals, R,
-                       c->area, c->err_d, c->w, c->info, s);
+                       c->area, c->err_d, c->w, c->info, area_chunks(c), s);
       if (k > 0)
         cg::launch_vertex_map_coverage(a->X[k], c->next, c->vreg, c->w, a->dens, a->Dk, lamX, lamX2, c->Lx, c->Ly,
                                        nv, s);
@@ -1648,7 +1661,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
         default:
           cg::launch_map_points<T>(c->xy0, c->pts, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s);
           cg::launch_areas(c->xy, c->ring_off, c->area_sums, c->reg_off, c->reg_rings,
-                           c->values, c->R_n, c->area, c->err_d, c->w, c->info, s);
+                           c->values, c->R_n, c->area, c->err_d, c->w, c->info, area_chunks(c), s);
           break;
       }
     }
@@ -1674,9 +1687,11 @@ void free_regions(cg_ctx* c) {
   c->prev = nullptr;
   c->scheds.clear();
   void* ps[] = {c->values, c->ring_off, c->reg_off, c->reg_rings, c->next, c->vreg,
-                c->xy, c->xy0, c->area_sums, c->area, c->err_d, c->w};
+                c->xy, c->xy0, c->area_sums, c->area, c->err_d, c->w, c->chunk_ring, c->ring_chunk_off,
+                c->chunk_sum};
   for (void* p : ps)
     if (p) cudaFree(p);
+  c->chunk_ring = nullptr; c->ring_chunk_off = nullptr; c->chunk_sum = nullptr; c->n_chunks = 0;
   c->values = nullptr; c->ring_off = nullptr; c->reg_off = nullptr; c->reg_rings = nullptr;
   c->next = nullptr; c->vreg = nullptr; c->xy = nullptr; c->xy0 = nullptr;
   c->area_sums = nullptr; c->area = nullptr; c->err_d = nullptr; c->w = nullptr;
@@ -1938,6 +1953,23 @@ int cartogram_set_regions(cg_ctx* c, int n_regions, const double* target_values,
   CG_CUDA(c, cudaMemcpy(c->reg_rings, reg_rings.data(), sizeof(int) * n_rings, cudaMemcpyHostToDevice));
   CG_CUDA(c, cudaMemcpy(c->next, next.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
   CG_CUDA(c, cudaMemcpy(c->vreg, vreg.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+  {
+    // the area sums' chunks: up to kAreaChunk consecutive vertices of one ring
+    std::vector<int> ring_chunk_off(n_rings + 1, 0), chunk_ring;
+    for (long long k = 0; k < n_rings; ++k) {
+      const long long nk = (off[k + 1] - off[k] + cg::kAreaChunk - 1) / cg::kAreaChunk;
+      ring_chunk_off[k + 1] = ring_chunk_off[k] + (int)nk;
+      for (long long q = 0; q < nk; ++q) chunk_ring.push_back((int)k);
+    }
+    c->n_chunks = (long long)chunk_ring.size();
+    CG_CUDA(c, cudaMalloc((void**)&c->ring_chunk_off, sizeof(int) * (n_rings + 1)));
+    CG_CUDA(c, cudaMalloc((void**)&c->chunk_ring, sizeof(int) * std::max<long long>(1, c->n_chunks)));
+    CG_CUDA(c, cudaMalloc((void**)&c->chunk_sum, sizeof(double) * std::max<long long>(1, c->n_chunks)));
+    CG_CUDA(c, cudaMemcpy(c->ring_chunk_off, ring_chunk_off.data(), sizeof(int) * (n_rings + 1),
+                          cudaMemcpyHostToDevice));
+    if (c->n_chunks > 0)
+      CG_CUDA(c, cudaMemcpy(c->chunk_ring, chunk_ring.data(), sizeof(int) * c->n_chunks, cudaMemcpyHostToDevice));
+  }
   {
     std::vector<int> prev(nv);
     for (long long v = 0; v < nv; ++v) prev[next[v]] = (int)v;

@@ -97,6 +97,18 @@ constexpr int kStepFail = -6;
 constexpr int kTimeout = -7;
 
 // Per-iteration results read back by the host in one copy.
+// Fixed-size chunks of the rings' vertices for the shoelace area sums (built with the
+// map): chunk c covers up to kAreaChunk consecutive vertices of ring chunk_ring[c]; ring
+// k's chunks are [ring_chunk_off[k], ring_chunk_off[k+1]); chunk_sum holds one partial
+// sum per chunk.
+constexpr int kAreaChunk = 64;
+struct AreaChunks {
+  const int* chunk_ring;
+  const int* ring_chunk_off;
+  long long n_chunks;
+  double* chunk_sum;
+};
+
 struct IterInfo {
   double max_err;       // max_i |A_i / A^_i - 1|
   double t_end;         // diffusion time reached by the integration

@@ -141,47 +141,65 @@ __global__ void row_scan_kernel(double* __restrict__ acc, int Lx) {
 
 // ---------------------------------------------------------------------------
 // Areas: per region the signed sum of its rings' shoelace areas (each ring relative to
-// its first vertex), one warp per region; then sum(A) and sum(V) in one block (a fixed
-// order, so the result does not vary from run to run); then per region the relative
+// its first vertex); then sum(A) and sum(V) in one block; then per region the relative
 // error err_r = A_r / A^_r - 1 with A^_r = V_r sum(A) / sum(V), the rasterisation weight
-// w_r = A^_r / A_r - 1 and the largest |err_r|. GB300's FP64 rate bounds these kernels:
-// the division-heavy last step is spread over many blocks.
+// w_r = A^_r / A_r - 1 and the largest |err_r|. Every sum runs in a fixed order, so the
+// results do not vary from run to run. The shoelace sums are split into chunks of at most
+// kAreaChunk vertices of one ring (one warp each), so that a region with a long boundary
+// does not hold up the whole launch; each region then adds its rings' chunk sums in
+// order. GB300's FP64 rate bounds these kernels: the division-heavy last step is spread
+// over many blocks.
 // ---------------------------------------------------------------------------
-__global__ void region_area_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
-                                   const int* __restrict__ reg_off, const int* __restrict__ reg_rings,
-                                   int R, double* __restrict__ area) {
-  const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+__global__ void ring_chunk_kernel(const double2* __restrict__ xy, const long long* __restrict__ off,
+                                  const int* __restrict__ chunk_ring, const int* __restrict__ ring_chunk_off,
+                                  long long n_chunks, double* __restrict__ chunk_sum) {
+  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= R) return;  // whole warps leave together
-  double A = 0.0;
-  for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) {
-    const int ring = reg_rings[k];
-    const long long a = off[ring], b = off[ring + 1];
-    const double2 o = xy[a];
-    double s = 0.0;
-    for (long long c = a; c < b; c += 32) {
-      // lane l holds the offset of vertex c + l from o; its successor's comes from lane
-      // l + 1, lane 31 loads it (the successor of the last vertex is o: offset 0)
-      const long long v = c + lane;
-      double2 d = make_double2(0.0, 0.0);
-      if (v < b) {
-        const double2 p = xy[v];
-        d = make_double2(p.x - o.x, p.y - o.y);
-      }
-      double2 e = make_double2(__shfl_down_sync(0xffffffffu, d.x, 1), __shfl_down_sync(0xffffffffu, d.y, 1));
-      if (lane == 31) {
-        e = make_double2(0.0, 0.0);
-        if (v + 1 < b) {
-          const double2 q = xy[v + 1];
-          e = make_double2(q.x - o.x, q.y - o.y);
-        }
-      }
-      s += d.x * e.y - e.x * d.y;
+  if (c >= n_chunks) return;  // whole warps leave together
+  const int ring = chunk_ring[c];
+  const long long a = off[ring], b = off[ring + 1];
+  const long long start = a + (c - ring_chunk_off[ring]) * (long long)kAreaChunk;
+  const long long end = min(start + (long long)kAreaChunk, b);
+  const double2 o = xy[a];
+  double s = 0.0;
+  for (long long c0 = start; c0 < end; c0 += 32) {
+    // lane l holds the offset of vertex c0 + l from o; its successor's comes from lane
+    // l + 1 inside the chunk, and the chunk's last vertex loads it (the successor of the
+    // ring's last vertex is o: offset 0)
+    const long long v = c0 + lane;
+    double2 d = make_double2(0.0, 0.0);
+    if (v < end) {
+      const double2 p = xy[v];
+      d = make_double2(p.x - o.x, p.y - o.y);
     }
-    s = warp_sum(s);
-    A += 0.5 * s;
+    double2 e = make_double2(__shfl_down_sync(0xffffffffu, d.x, 1), __shfl_down_sync(0xffffffffu, d.y, 1));
+    if (v < end && (lane == 31 || v + 1 == end)) {
+      e = make_double2(0.0, 0.0);
+      if (v + 1 < b) {
+        const double2 q = xy[v + 1];
+        e = make_double2(q.x - o.x, q.y - o.y);
+      }
+    }
+    s += d.x * e.y - e.x * d.y;
   }
-  if (lane == 0) area[r] = A;
+  s = warp_sum(s);
+  if (lane == 0) chunk_sum[c] = s;
+}
+
+// A_r = sum over the region's rings of half their chunk sums (one thread per region).
+__global__ void region_area_kernel(const int* __restrict__ reg_off, const int* __restrict__ reg_rings,
+                                   const int* __restrict__ ring_chunk_off, const double* __restrict__ chunk_sum,
+                                   int R, double* __restrict__ area) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    double A = 0.0;
+    for (int k = reg_off[r]; k < reg_off[r + 1]; ++k) {
+      const int ring = reg_rings[k];
+      double s = 0.0;
+      for (int c = ring_chunk_off[ring]; c < ring_chunk_off[ring + 1]; ++c) s += chunk_sum[c];
+      A += 0.5 * s;
+    }
+    area[r] = A;
+  }
 }
 
 __device__ __forceinline__ double block_sum_det(double v, double* red) {

@@ -273,7 +273,7 @@ void launch_raster(const double2* xy, const int* next, const int* vreg, const do
 // rasterisation weights and the largest |error| into info->max_err.
 void launch_areas(const double2* xy, const long long* ring_off, double* sums, const int* reg_off,
                   const int* reg_rings, const double* values, int R, double* area, double* err, double* w,
-                  IterInfo* info, cudaStream_t s);
+                  IterInfo* info, const AreaChunks& ch, cudaStream_t s);
 void launch_collect(const DevState* st, IterInfo* info, cudaStream_t s);
 
 }  // namespace cg

@@ -110,9 +110,12 @@ void launch_raster(const double2* xy, const int* next, const int* vreg, const do
 
 void launch_areas(const double2* xy, const long long* ring_off, double* sums, const int* reg_off,
                   const int* reg_rings, const double* values, int R, double* area, double* err, double* w,
-                  IterInfo* info, cudaStream_t s) {
-  region_area_kernel<<<blocks_for((long long)R * 32, 256, 1 << 20), 256, 0, s>>>(xy, ring_off, reg_off,
-                                                                                reg_rings, R, area);
+                  IterInfo* info, const AreaChunks& ch, cudaStream_t s) {
+  if (ch.n_chunks > 0)
+    ring_chunk_kernel<<<blocks_for(ch.n_chunks * 32, 256, 1 << 20), 256, 0, s>>>(
+        xy, ring_off, ch.chunk_ring, ch.ring_chunk_off, ch.n_chunks, ch.chunk_sum);
+  region_area_kernel<<<blocks_for(R, 128, 1 << 16), 128, 0, s>>>(reg_off, reg_rings, ch.ring_chunk_off,
+                                                                  ch.chunk_sum, R, area);
   area_sums_kernel<<<1, 1024, 0, s>>>(area, values, R, sums, info);
   region_error_kernel<<<blocks_for(R, 32, sm_count()), 32, 0, s>>>(area, values, R, sums, err, w, info);
 }
