@@ -326,9 +326,22 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     st_two(out + o, vv[0], vv[1]);
     if (rho_out) st_two(rho_out + o, rr[0], rr[1]);
   }
+  // both maxima and the flag with one barrier (valid in thread 0)
+  dev = warp_max(dev);
+  v2max = warp_max(v2max);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp] = dev;
+    red[32 + warp] = v2max;
+  }
   res.bad = __syncthreads_or(bad);
-  res.dev = block_max(dev, red);
-  res.v2max = block_max(v2max, red + 32);
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    dev = warp_max(lane < nw ? red[lane] : T(0));
+    v2max = warp_max(lane < nw ? red[32 + lane] : T(0));
+  }
+  res.dev = dev;
+  res.v2max = v2max;
   __syncthreads();
   return true;
 }
