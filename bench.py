@@ -509,6 +509,12 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     achieved = bpp[dominant] * m.Lx * m.Ly / (prof[dominant] * 1e-3) / 1e9
     traffic = _traffic(dominant)
+    # the same figures for each of the three kernels of an attempted step
+    per_kernel = {k: {"us": prof[k] * 1e3, "bytes_per_launch": bpp[k] * m.Lx * m.Ly,
+                      "achieved_gbs": bpp[k] * m.Lx * m.Ly / (prof[k] * 1e-3) / 1e9} for k in bpp}
+    for k in per_kernel:
+        per_kernel[k]["frac"] = per_kernel[k]["achieved_gbs"] / peaks["hbm_gbs"]
+        per_kernel[k]["traffic"] = _traffic(k)
     bw = read_bandwidths(P)
 
     # end to end through the C-ABI with host buffers: pinned host -> set_regions ->
@@ -638,6 +644,7 @@ def run_ours(args):
                          "peak_kind": peak_kind + " (copy bandwidth)",
                          "bytes_per_launch": bpp[dominant] * m.Lx * m.Ly,
                          "l2_read_gbs": bw["l2_read_gbs"], "l2_frac": achieved / bw["l2_read_gbs"],
+                         "step_kernels": per_kernel,
                          "hbm_read_gbs": bw["hbm_read_gbs"],
                          "note": "the step loop's working set (~50 MB) stays in L2: l2_frac is against the read "
                                  "bandwidth of a 32 MiB L2-resident buffer measured live (library probe kernel, "
