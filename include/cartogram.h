@@ -384,7 +384,8 @@ int cartogram_read_bandwidth(int64_t bytes, int passes, double* gbs_out);
  * transform tables and a reduction state) is one array in device memory created when
  * the library is loaded onto a GPU and kept until the process exits. The first call on
  * a device, with that device current, looks up the array's device address and sets
- * the kernels' shared-memory limits. Every call on a device shares the array and
+ * the kernels' shared-memory limits; make that first call before any stream capture
+ * begins on the device. Every call on a device shares the array and
  * leaves its contents behind (the reduction state is cleared by each call): calls
  * whose work overlaps on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. The call is asynchronous, so a failure inside the kernels
