@@ -149,20 +149,21 @@ struct FFTShape {
   }
 };
 
-// In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N).
-// TW[k2*N1 + n1] = exp(s 2 pi i n1 k2 / N) holds the inter-step twiddles (shared
-// memory; consecutive threads read consecutive entries). Unnormalised. Ends with
-// __syncthreads().
-template <typename T, int LOG2N, bool INV>
-__device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ TW) {
+// DFT of S signals into buf[s*SSTRIDE + pidx(p)], p in [0, N): step A takes its inputs
+// from load(s, n1, a), which fills a[n2] with element n1 + N1*n2 of signal s (so a pass can
+// form its signals on the fly instead of staging them in buf first), and leaves its results
+// in buf, where step B finishes in place. TW[k2*N1 + n1] = exp(s 2 pi i n1 k2 / N) holds the
+// inter-step twiddles (shared memory; consecutive threads read consecutive entries).
+// Unnormalised. Ends with __syncthreads().
+template <typename T, int LOG2N, bool INV, typename Load>
+__device__ __forceinline__ void block_fft_from(V2<T>* buf, int S, const V2<T>* __restrict__ TW, Load&& load) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
   for (int task = threadIdx.x; task < S * F::N1; task += blockDim.x) {
     const int s = task >> F::L1, n1 = task & (F::N1 - 1);
     C* x = buf + s * F::SSTRIDE;
     C a[F::N2];
-#pragma unroll
-    for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
+    load(s, n1, a);
     reg_dft<C, F::N2, INV>(a);
 #pragma unroll
     for (int k2 = 1; k2 < F::N2; ++k2) a[k2] = cmul(a[k2], TW[k2 * F::N1 + n1]);
@@ -181,6 +182,19 @@ __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __rest
     for (int k1 = 0; k1 < F::N1; ++k1) x[F::pidx(k1 + F::N1 * k2)] = a[k1];
   }
   __syncthreads();
+}
+
+// In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N) (see
+// block_fft_from). Ends with __syncthreads().
+template <typename T, int LOG2N, bool INV>
+__device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ TW) {
+  using C = V2<T>;
+  using F = FFTShape<LOG2N>;
+  block_fft_from<T, LOG2N, INV>(buf, S, TW, [&](int s, int n1, C (&a)[F::N2]) {
+    const C* x = buf + s * F::SSTRIDE;
+#pragma unroll
+    for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
+  });
 }
 
 }  // namespace cg

@@ -123,31 +123,23 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   if (!__syncthreads_and(ok)) return false;
 
   const T kd = (T)(kPi / N);
-  // N/2 tasks per row (no runtime integer division): task m > 0 packs the pair (m, N - m);
-  // task 0 packs m = 0 and the self-paired m = N/2
-  for (int task = threadIdx.x; task < S * (N / 2); task += blockDim.x) {
-    const int s = task >> (LOG2N - 1), m = task & (N / 2 - 1);
+  // The packed signal of each row, formed by the FFT's first step as it reads its inputs
+  // (no staging pass): element m > 0 of row s is E[m] ((a_m + b_m)/2, (b_q - a_q)/2), q = N - m,
+  // with a_m = spec[m] fx[m] fy and b_m = -(pi m / N) a_m (the DCT-III and DST-III
+  // coefficients sharing one complex DFT); element 0 is (a_0, 0).
+  block_fft_from<T, LOG2N, true>(buf, S, W, [&](int s, int n1, C (&a)[F::N2]) {
     const T* row = stage + s * N;
-    C* x = buf + s * F::SSTRIDE;
     const T f = fyS[s];
-    if (m == 0) {
-      x[F::pidx(0)] = mk2<T>(row[0] * fx[0] * f, T(0));
-      constexpr int h = N / 2;
-      const T ah = row[h] * fx[h] * f;
-      const T bh = -kd * (T)h * ah;
-      x[F::pidx(h)] = cmul(E[h], mk2<T>((ah + bh) * T(0.5), (bh - ah) * T(0.5)));
-      continue;
+#pragma unroll
+    for (int n2 = 0; n2 < F::N2; ++n2) {
+      const int m = n1 + F::N1 * n2, q = (N - m) & (N - 1);
+      const T am = row[m] * fx[m] * f;
+      const T aq = row[q] * fx[q] * f;
+      const T bm = -kd * (T)m * am;
+      const T bq = -kd * (T)q * aq;
+      a[n2] = (m == 0) ? mk2<T>(am, T(0)) : cmul(E[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
     }
-    const T am = row[m] * fx[m] * f;
-    const T bm = -kd * (T)m * am;
-    const int q = N - m;
-    const T aq = row[q] * fx[q] * f;
-    const T bq = -kd * (T)q * aq;
-    x[F::pidx(m)] = cmul(E[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
-    x[F::pidx(q)] = cmul(E[q], mk2<T>((aq + bq) * T(0.5), (bm - am) * T(0.5)));
-  }
-  __syncthreads();
-  block_fft<T, LOG2N, true>(buf, S, W);
+  });
   // S is a power of two: a runtime integer division here costs as much as the FFT. Two
   // adjacent rows per task (one output slot, one vector store)
   const int ls = __ffs(S) - 1;
