@@ -41,9 +41,10 @@ __device__ __forceinline__ void st_two(double* p, double a, double b) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
-// 1 / x, correctly rounded (the FP32 one by the reciprocal instruction rather than a
-// general division).
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// 1 / x of the velocity v = -grad rho / rho. In FP32 the hardware's approximate reciprocal
+// (within 2 ulp for the positive normal densities here, far inside the error of the FP32
+// transforms that produce rho); in FP64 and float-float a division.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <typename A> __device__ __forceinline__ A recip(A x) { return A(1) / x; }
 
