@@ -25,6 +25,12 @@ __global__ void phi_spectrum_kernel(const double* __restrict__ spec, T* __restri
   }
 }
 
+// 1 / rho: in FP32 the hardware's approximate reciprocal (within 2 ulp for the positive
+// normal densities here, far inside the error of the FP32 transforms that produce rho0 and
+// J), in FP64 a division.
+__device__ __forceinline__ float lin_recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double lin_recip(double x) { return 1.0 / x; }
+
 // v = J / ((1 - t) rho0 + t) at every grid point, and max |v|^2 into st->vmax2_bits.
 // Init mode (kModeInit): t = 0 into vbuf0 (the field at the start, parity 0), a
 // non-positive rho0 flagged. Step mode (kModeLinear): the end t1 = min(t + h, 1) of the
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(256) linear_velocity_kernel(DevState* st, cons
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     const T r0 = rho0[p];
     bad |= !(r0 > T(0));
-    const T inv = T(1) / ((T(1) - t1) * r0 + t1);
+    const T inv = lin_recip((T(1) - t1) * r0 + t1);
     const V2<T> j = J[p];
     const V2<T> v = mk2<T>(j.x * inv, j.y * inv);
     out[p] = v;
