@@ -131,13 +131,15 @@ __device__ __forceinline__ bool p1_finish(V2<T>* __restrict__ ABt, int Ly, int S
   block_fft_from<T, LOG2N, true>(buf, S, W, [&](int s, int n1, C (&a)[F::N2]) {
     const T* row = stage + s * N;
     const T f = fyS[s];
+    const T fn1 = (T)n1;  // m and N - m as values by exact adds, not a conversion each
 #pragma unroll
     for (int n2 = 0; n2 < F::N2; ++n2) {
       const int m = n1 + F::N1 * n2, q = (N - m) & (N - 1);
+      const T fm = fn1 + T(F::N1 * n2), fq = T(N) - fm;
       const T am = row[m] * fx[m] * f;
       const T aq = row[q] * fx[q] * f;
-      const T bm = -kd * (T)m * am;
-      const T bq = -kd * (T)q * aq;
+      const T bm = -kd * fm * am;
+      const T bq = -kd * fq * aq;
       a[n2] = (m == 0) ? mk2<T>(am, T(0)) : cmul(E[m], mk2<T>((am + bm) * T(0.5), (bq - aq) * T(0.5)));
     }
   });
