@@ -30,12 +30,6 @@ __device__ __forceinline__ unsigned floor_parts(double x, double& fl) {
   fl = min(max(floor(x), -4194304.0), 4194304.0);
   return (unsigned)(int)fl;
 }
-// (T)i for 0 <= i < 2^22, FP32 again by the same bit pattern instead of a conversion.
-__device__ __forceinline__ float int_to(int i, float) {
-  return __fsub_rn(__int_as_float(0x4B400000 + i), 12582912.0f);
-}
-__device__ __forceinline__ double int_to(int i, double) { return (double)i; }
-
 // Cell of the interpolation lattice that holds the grid point (i, j) displaced by
 // (dx, dy): lower-left grid point (ix, iy) and the fractions (fx, fy).
 template <typename T> struct Cell {

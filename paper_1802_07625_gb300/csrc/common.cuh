@@ -27,6 +27,13 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// (T)i for 0 <= i < 2^22. FP32 takes the bit pattern of 1.5 * 2^23 + i and one exact add
+// instead of the conversion unit; other types convert.
+__device__ __forceinline__ float int_to(int i, float) {
+  return __fsub_rn(__int_as_float(0x4B400000 + i), 12582912.0f);
+}
+template <typename A> __device__ __forceinline__ A int_to(int i, A) { return A(i); }
+
 // Step-control constants passed by value to the kernels that need them.
 struct StepParams {
   double dt0, atol, grow, shrink, cfl, rho_tol, h_min;

@@ -41,6 +41,11 @@ __device__ __forceinline__ void st_two(double* p, double a, double b) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
+// a * b + c, with one rounding in FP32 and FP64
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }
+template <typename A> __device__ __forceinline__ A madd(A a, A b, A c) { return a * b + c; }
+
 // 1 / x of the velocity v = -grad rho / rho. In FP32 the hardware's approximate reciprocal
 // (within 2 ulp for the positive normal densities here, far inside the error of the FP32
 // transforms that produce rho); in FP64 and float-float a division.
@@ -250,9 +255,11 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
   if (!__syncthreads_and(ok)) return false;
 
   const int Wp = Wc / 2;
-  const A kd = (A)(kPi / N);
+  const A kh = (A)(0.5 * kPi / N);
   // N/2 tasks per column pair (no runtime integer division): task m > 0 packs the pair
-  // (m, N - m); task 0 packs m = 0 and then (second round) the self-paired m = N/2
+  // (m, N - m); task 0 packs m = 0 and then (second round) the self-paired m = N/2.
+  // With b_m = -(pi m/N) a_m, (a_m + b_m)/2 = a_m g_m and (b_m - a_m)/2 = a_m h_m, where
+  // g_m = 1/2 - (pi/(2N)) m and h_m = -1/2 - (pi/(2N)) m.
   for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
     const int p = task >> (LOG2N - 1);
     int m = task & (N / 2 - 1);
@@ -272,15 +279,18 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     const int q = N - m;
     const C Aq0 = to_v2<A, T>(s0[q]), Aq1 = to_v2<A, T>(s1[q]);
     const C em = E[m], eq = E[q];
+    const A fm = int_to(m, A(0)), fq = A(N) - fm;
+    const A gm = madd(-kh, fm, A(0.5)), hm = madd(-kh, fm, A(-0.5));
+    const A gq = madd(-kh, fq, A(0.5)), hq = madd(-kh, fq, A(-0.5));
     {  // (rho', d_y rho) of column c
-      const A am = Am0.x, aq = Aq0.x, bm = -kd * (A)m * am, bq = -kd * (A)q * aq;
-      x0[F::pidx(m)] = cmul(em, mk2<A>((am + bm) * A(0.5), (bq - aq) * A(0.5)));
-      if (q != m) x0[F::pidx(q)] = cmul(eq, mk2<A>((aq + bq) * A(0.5), (bm - am) * A(0.5)));
+      const A am = Am0.x, aq = Aq0.x;
+      x0[F::pidx(m)] = cmul(em, mk2<A>(am * gm, aq * hq));
+      if (q != m) x0[F::pidx(q)] = cmul(eq, mk2<A>(aq * gq, am * hm));
     }
     {  // (rho', d_y rho) of column c + 1
-      const A am = Am1.x, aq = Aq1.x, bm = -kd * (A)m * am, bq = -kd * (A)q * aq;
-      x1[F::pidx(m)] = cmul(em, mk2<A>((am + bm) * A(0.5), (bq - aq) * A(0.5)));
-      if (q != m) x1[F::pidx(q)] = cmul(eq, mk2<A>((aq + bq) * A(0.5), (bm - am) * A(0.5)));
+      const A am = Am1.x, aq = Aq1.x;
+      x1[F::pidx(m)] = cmul(em, mk2<A>(am * gm, aq * hq));
+      if (q != m) x1[F::pidx(q)] = cmul(eq, mk2<A>(aq * gq, am * hm));
     }
     {  // d_x rho of columns c (real part) and c + 1 (imaginary part)
       const A bem = Am0.y, gam = Am1.y, beq = Aq0.y, gaq = Aq1.y;
