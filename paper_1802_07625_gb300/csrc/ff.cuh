@@ -1,9 +1,12 @@
-// Float-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers with
-// |lo| <= ulp(hi)/2, which carries about 48 significant bits. Sums use the error-free
-// two-sum of two floats (Knuth), products the error-free product by fused multiply-add;
-// each result is renormalised. Used for the mixed path's compensated second transform pass,
-// where FP32 rounding at the scale of a line's largest values would swamp densities far
-// below it.
+// Float-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers, which
+// carries about 48 significant bits. Sums use the error-free two-sum of the high parts
+// (Knuth) and add the low parts in FP32; products take the error-free product of the high
+// parts by fused multiply-add plus the two cross terms. Results are not renormalised: lo
+// may exceed ulp(hi)/2 by a small factor, and after a cancellation of the high parts it may
+// hold most of the value, which is then tiny against the operands. Every error stays within
+// a small multiple of 2^-44 of the operands' magnitudes, the bound a transform's error
+// analysis uses. Used for the mixed path's compensated second transform pass, where FP32
+// rounding at the scale of a line's largest values would swamp densities far below it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,22 +43,25 @@ __device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
 }
 
 // The sum's error is within a small multiple of 2^-44 (|a| + |b|): relative to the size of
-// the operands, which is the bound a transform's error analysis uses (a sum that cancels
-// keeps the absolute error of its operands).
+// the operands (a sum that cancels keeps the absolute error of its operands).
 __device__ __forceinline__ ff operator+(ff a, ff b) {
   const ff s = ff_two_sum(a.hi, b.hi);
-  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  return ff(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
 __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+// The product drops a.lo * b.lo, which is below 2^-44 |a| |b| while the low parts are small;
+// where a cancellation left a low part as large as its high part, the value is itself below
+// 2^-22 of the operands that formed it, and the dropped term is as small in absolute terms.
 __device__ __forceinline__ ff operator*(ff a, ff b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);  // p + e = a.hi * b.hi exactly
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return ff_fast_two_sum(p, e);
+  return ff(p, e);
 }
 __device__ __forceinline__ ff operator/(ff a, ff b) {
+  b = ff_two_sum(b.hi, b.lo);  // normalised divisor: q2 below divides by b.hi alone
   const float q1 = __fdiv_rn(a.hi, b.hi);
   const ff r = a - b * ff(q1, 0.0f);
   const float q2 = __fdiv_rn(__fadd_rn(r.hi, r.lo), b.hi);
@@ -63,7 +69,11 @@ __device__ __forceinline__ ff operator/(ff a, ff b) {
 }
 __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
 __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
-__device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+// by the sign of the difference (the parts of an unnormalised value do not order it)
+__device__ __forceinline__ bool operator>(ff a, ff b) {
+  const ff d = a - b;
+  return __fadd_rn(d.hi, d.lo) > 0.0f;
+}
 
 struct ff2 {
   ff x, y;
