@@ -186,15 +186,42 @@ __device__ __forceinline__ void block_fft_from(V2<T>* buf, int S, const V2<T>* _
 
 // In-place DFT of S signals stored at buf[s*SSTRIDE + pidx(p)], p in [0, N) (see
 // block_fft_from). Ends with __syncthreads().
-template <typename T, int LOG2N, bool INV>
+// COMPACT (where N1 = N2): both steps run one copy of the register DFT in a loop over the
+// two steps, with the element positions n + N1 k (step A) or N1 n + k (step B) taken at run
+// time: the same arithmetic in the same order, in half the code. For the float-float type,
+// whose unrolled register DFT is large, the two inlined copies overflow the instruction
+// cache.
+template <typename T, int LOG2N, bool INV, bool COMPACT = false>
 __device__ __forceinline__ void block_fft(V2<T>* buf, int S, const V2<T>* __restrict__ TW) {
   using C = V2<T>;
   using F = FFTShape<LOG2N>;
-  block_fft_from<T, LOG2N, INV>(buf, S, TW, [&](int s, int n1, C (&a)[F::N2]) {
-    const C* x = buf + s * F::SSTRIDE;
+  if constexpr (COMPACT && F::N1 == F::N2) {
+#pragma unroll 1
+    for (int step = 0; step < 2; ++step) {
+      for (int task = threadIdx.x; task < S * F::N1; task += blockDim.x) {
+        const int s = task >> F::L1, n = task & (F::N1 - 1);
+        C* x = buf + s * F::SSTRIDE;
+        const int base = step ? F::N1 * n : n, stride = step ? 1 : F::N1;
+        C a[F::N1];
 #pragma unroll
-    for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
-  });
+        for (int k = 0; k < F::N1; ++k) a[k] = x[F::pidx(base + stride * k)];
+        reg_dft<C, F::N1, INV>(a);
+        if (step == 0) {
+#pragma unroll
+          for (int k2 = 1; k2 < F::N2; ++k2) a[k2] = cmul(a[k2], TW[k2 * F::N1 + n]);
+        }
+#pragma unroll
+        for (int k = 0; k < F::N1; ++k) x[F::pidx(base + stride * k)] = a[k];
+      }
+      __syncthreads();
+    }
+  } else {
+    block_fft_from<T, LOG2N, INV>(buf, S, TW, [&](int s, int n1, C (&a)[F::N2]) {
+      const C* x = buf + s * F::SSTRIDE;
+#pragma unroll
+      for (int n2 = 0; n2 < F::N2; ++n2) a[n2] = x[F::pidx(n1 + F::N1 * n2)];
+    });
+  }
 }
 
 }  // namespace cg

@@ -19,6 +19,8 @@
 // parts).
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
 #include "tma.cuh"
 
@@ -299,7 +301,7 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     }
   }
   __syncthreads();
-  block_fft<A, LOG2N, true>(buf, Wc + Wp, W);
+  block_fft<A, LOG2N, true, !std::is_same<A, T>::value>(buf, Wc + Wp, W);
 
   T dev = T(0), v2max = T(0);
   bool bad = false;
