@@ -333,6 +333,50 @@ def test_adaptive_error_scales_with_the_step_tolerance(orc):
         assert 2.5 < coarse / fine < 5.0, errs
 
 
+def test_adaptive_heun_follows_a_brute_force_rk4_trajectory(orc):
+    # Brute force on an 8x8 grid: every grid point's trajectory dr/dt = v(r, t) (main text
+    # Eq. rt_diff) integrated by classical RK4 with 400 equal steps to the adaptive
+    # integration's own end time, through the same fields and interpolation. The RK4
+    # solution is converged (200 against 400 steps agree to ~1e-6), so the difference is
+    # the adaptive predictor-corrector's time-integration error: within about atol, and
+    # falling with it. A slip in the step, the controller or the time bookkeeping (a
+    # stage at the wrong time, an accepted step whose time is not advanced) shows here.
+    L = 8
+    c = np.arange(L) + 0.5
+    X0, Y0 = np.meshgrid(c, c)
+    rho = (1 + 0.4 * np.cos(PI * X0 / L) * np.cos(PI * Y0 / L) + 0.25 * np.cos(2 * PI * Y0 / L)
+           + 0.2 * np.cos(3 * PI * X0 / L))
+    spec = orc.forward(rho, 0.0)
+
+    def vel(t, px, py):
+        vx, vy, _ = orc.velocity(*orc.fields(spec, t))
+        u = np.array([orc.interp(vx, vy, a, b) for a, b in zip(px, py)])
+        return u[:, 0], u[:, 1]
+
+    def rk4(T, n):
+        px, py, h = X0.ravel().copy(), Y0.ravel().copy(), T / n
+        for k in range(n):
+            t = k * h
+            k1 = vel(t, px, py)
+            k2 = vel(t + h / 2, px + h / 2 * k1[0], py + h / 2 * k1[1])
+            k3 = vel(t + h / 2, px + h / 2 * k2[0], py + h / 2 * k2[1])
+            k4 = vel(t + h, px + h * k3[0], py + h * k3[1])
+            px = px + h / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+            py = py + h / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+        return px.reshape(L, L), py.reshape(L, L)
+
+    errs = []
+    for atol in (1e-2, 1e-3, 1e-4):
+        r = orc.integrate(spec, atol=atol, rho_tol=1e-4)
+        assert r.status == 0
+        xr, yr = rk4(r.t_end, 400)
+        assert np.max(np.abs(xr - X0)) > 0.3  # the points do move
+        e = max(np.max(np.abs(r.X - xr)), np.max(np.abs(r.Y - yr)))
+        assert e < 1.5 * atol, (atol, e)
+        errs.append(e)
+    assert errs[0] > 3 * errs[1] > 9 * errs[2]
+
+
 def test_mirror_symmetry(orc):
     rng = np.random.default_rng(6)
     Ly, Lx = 12, 12
