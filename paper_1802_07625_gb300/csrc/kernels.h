@@ -93,7 +93,7 @@ inline LaunchCfg fwd_rows_cfg(int log2Lx, int Ly) {
   LaunchCfg c;
   c.per_block = S;
   c.threads = (S / 2) * N1;
-  c.smem = (size_t)N * 16 + (size_t)(S / 2) * fft_stride(log2Lx) * 16;
+  c.smem = (size_t)N * 32 + (size_t)(S / 2) * fft_stride(log2Lx) * 16;
   c.grid = Ly / S;
   return c;
 }
@@ -106,7 +106,7 @@ inline LaunchCfg fwd_cols_cfg(int log2Ly, int Lx) {
   LaunchCfg c;
   c.per_block = Wc;
   c.threads = (Wc / 2) * N1;
-  c.smem = (size_t)N * 16 + (size_t)(Wc / 2) * fft_stride(log2Ly) * 16;
+  c.smem = (size_t)N * 32 + (size_t)(Wc / 2) * fft_stride(log2Ly) * 16;
   c.grid = Lx / Wc;
   return c;
 }

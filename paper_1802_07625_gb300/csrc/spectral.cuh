@@ -518,7 +518,11 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
 // ---------------------------------------------------------------------------
 // forward pass 1: DCT-II along x of row pairs. S rows per block (even),
 // blockDim = (S/2) * N1, grid = Ly / S. R[j][m] = sum_i rho[j][i] cos(pi m x_i/Lx).
-// shared: W[N] (C, forward roots), buf[(S/2) * STRIDE] (C)
+// The two real rows of a signal come out of its DFT V as R[m] = Re(conj(E[m]) (V[m] +
+// conj V[N-m]) / 2) and Re(conj(E[m]) (V[m] - conj V[N-m]) / (2i)); outputs m and N - m
+// share the sums and differences of V[m] and V[N-m], so one task forms both, with the halves
+// folded into a per-block table E/2 (exact).
+// shared: W[N] (C, forward roots), buf[(S/2) * STRIDE] (C), Eh[N] (C)
 // ---------------------------------------------------------------------------
 template <int LOG2N>
 __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restrict__ R,
@@ -530,9 +534,14 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* W = reinterpret_cast<C*>(smem_raw);
   C* buf = W + N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
   const int r0 = blockIdx.x * S;
   const int S2 = S / 2;
+  C* Eh = buf + S2 * F::SSTRIDE;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    W[i] = Wg[i];
+    const C e = Eg[i];
+    Eh[i] = mk2<double>(0.5 * e.x, 0.5 * e.y);
+  }
   for (int task = threadIdx.x; task < S2 * (N / 2); task += blockDim.x) {
     const int s = task / (N / 2), k = task - s * (N / 2);
     const double2 e = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s) * N + 2 * k);
@@ -543,17 +552,29 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
   }
   __syncthreads();
   block_fft<double, LOG2N, false>(buf, S2, W);
-  for (int task = threadIdx.x; task < S2 * N; task += blockDim.x) {
-    const int s = task >> LOG2N, m = task & (N - 1);
+  for (int task = threadIdx.x; task < S2 * (N / 2); task += blockDim.x) {
+    const int s = task >> (LOG2N - 1), k = task & (N / 2 - 1);
     const C* x = buf + s * F::SSTRIDE;
-    const C Vm = x[F::out_slot(m)];
-    const C Vq = x[F::out_slot((N - m) & (N - 1))];
-    const C em = Eg[m];
-    // V1 = (Vm + conj Vq)/2, V2 = (Vm - conj Vq)/(2i); X = Re(conj(e) V)
-    const C V1 = mk2<double>(0.5 * (Vm.x + Vq.x), 0.5 * (Vm.y - Vq.y));
-    const C V2 = mk2<double>(0.5 * (Vm.y + Vq.y), -0.5 * (Vm.x - Vq.x));
-    R[(size_t)(r0 + 2 * s) * N + m] = em.x * V1.x + em.y * V1.y;
-    R[(size_t)(r0 + 2 * s + 1) * N + m] = em.x * V2.x + em.y * V2.y;
+    double* R0 = R + (size_t)(r0 + 2 * s) * N;
+    double* R1 = R0 + N;
+    if (k == 0) {
+      // the self-paired outputs 0 and N/2 (E[0] = 1)
+      const C V0 = x[F::out_slot(0)], Vh = x[F::out_slot(N / 2)];
+      const double eh = Eh[N / 2].x;
+      R0[0] = V0.x;
+      R1[0] = V0.y;
+      R0[N / 2] = eh * (Vh.x + Vh.x);
+      R1[N / 2] = eh * (Vh.y + Vh.y);
+    } else {
+      const int q = N - k;
+      const C Vm = x[F::out_slot(k)], Vq = x[F::out_slot(q)];
+      const double u = Vm.x + Vq.x, v = Vm.y - Vq.y, w = Vm.y + Vq.y, z = Vm.x - Vq.x;
+      const C em = Eh[k], eq = Eh[q];
+      R0[k] = em.x * u + em.y * v;
+      R1[k] = em.x * w - em.y * z;
+      R0[q] = eq.x * u - eq.y * v;
+      R1[q] = eq.x * w + eq.y * z;
+    }
   }
 }
 
@@ -561,7 +582,10 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
 // forward pass 2: DCT-II along y of column pairs, times the coefficient weights
 // 4/((1+d_m0)(1+d_n0)) and the separable blur factors; the (0,0) coefficient (the
 // mean, which the velocity handles separately) is set to zero.
-// Wc columns per block (even), blockDim = (Wc/2) * N1, grid = Lx / Wc.
+// Wc columns per block (even), blockDim = (Wc/2) * N1, grid = Lx / Wc. As in pass 1 one task
+// forms outputs n and N - n; the halves and the row weights (1 + d_n0)^-1 2 by[n] are folded
+// into a per-block table Ew[n] = E[n] (n == 0 ? 1/2 : 1) by[n].
+// shared: W[N] (C), buf[(Wc/2) * SSTRIDE] (C), Ew[N] (C)
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2N>
 __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict__ spec64,
@@ -574,10 +598,16 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* W = reinterpret_cast<C*>(smem_raw);
   C* buf = W + N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) W[i] = Wg[i];
   const int c0 = blockIdx.x * Wc;
   const int Wp = Wc / 2;
   const int lp = __ffs(Wp) - 1;  // Wp is a power of two
+  C* Ew = buf + Wp * F::SSTRIDE;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    W[i] = Wg[i];
+    const C e = Eg[i];
+    const double f = (i == 0 ? 0.5 : 1.0) * (by ? by[i] : 1.0);
+    Ew[i] = mk2<double>(e.x * f, e.y * f);
+  }
   for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
     const int k = task >> lp, p = task & (Wp - 1);
     const double2 e = *reinterpret_cast<const double2*>(R + (size_t)(2 * k) * Lx + c0 + 2 * p);
@@ -588,25 +618,34 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   }
   __syncthreads();
   block_fft<double, LOG2N, false>(buf, Wp, W);
-  for (int task = threadIdx.x; task < N * Wp; task += blockDim.x) {
-    const int n = task >> lp, p = task & (Wp - 1);
-    const C* x = buf + p * F::SSTRIDE;
-    const C Vn = x[F::out_slot(n)];
-    const C Vq = x[F::out_slot((N - n) & (N - 1))];
-    const C en = Eg[n];
-    const C V1 = mk2<double>(0.5 * (Vn.x + Vq.x), 0.5 * (Vn.y - Vq.y));
-    const C V2 = mk2<double>(0.5 * (Vn.y + Vq.y), -0.5 * (Vn.x - Vq.x));
-    const int m = c0 + 2 * p;
-    const double wn = (n == 0 ? 1.0 : 2.0) * (by ? by[n] : 1.0);
-    double s0 = (en.x * V1.x + en.y * V1.y) * wn * (m == 0 ? 1.0 : 2.0) * (bx ? bx[m] : 1.0);
-    double s1 = (en.x * V2.x + en.y * V2.y) * wn * 2.0 * (bx ? bx[m + 1] : 1.0);
-    if (m == 0 && n == 0) s0 = 0.0;
+  auto put = [&](int n, int m, double s0, double s1) {
     const size_t o = (size_t)n * Lx + m;
     spec64[o] = s0;
     spec64[o + 1] = s1;
     if (specT) {
       specT[o] = (T)s0;
       specT[o + 1] = (T)s1;
+    }
+  };
+  for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
+    const int k = task >> lp, p = task & (Wp - 1);
+    const C* x = buf + p * F::SSTRIDE;
+    const int m = c0 + 2 * p;
+    // column weights (1 + d_m0)^-1 2 bx[m]
+    const double wm0 = (m == 0 ? 1.0 : 2.0) * (bx ? bx[m] : 1.0), wm1 = 2.0 * (bx ? bx[m + 1] : 1.0);
+    if (k == 0) {
+      // the self-paired outputs 0 and N/2; the (0,0) coefficient is zero
+      const C V0 = x[F::out_slot(0)], Vh = x[F::out_slot(N / 2)];
+      const double e0 = Ew[0].x, eh = Ew[N / 2].x;
+      put(0, m, m == 0 ? 0.0 : e0 * (V0.x + V0.x) * wm0, e0 * (V0.y + V0.y) * wm1);
+      put(N / 2, m, eh * (Vh.x + Vh.x) * wm0, eh * (Vh.y + Vh.y) * wm1);
+    } else {
+      const int q = N - k;
+      const C Vn = x[F::out_slot(k)], Vq = x[F::out_slot(q)];
+      const double u = Vn.x + Vq.x, v = Vn.y - Vq.y, w = Vn.y + Vq.y, z = Vn.x - Vq.x;
+      const C en = Ew[k], eq = Ew[q];
+      put(k, m, (en.x * u + en.y * v) * wm0, (en.x * w - en.y * z) * wm1);
+      put(q, m, (eq.x * u - eq.y * v) * wm0, (eq.x * w + eq.y * z) * wm1);
     }
   }
 }
