@@ -78,8 +78,10 @@ inline LaunchCfg inv_cols_cfg(int log2Ly, int Lx, size_t esz, int Wc) {
   LaunchCfg c;
   c.per_block = Wc;
   c.threads = S * N1;
-  c.smem = (size_t)N * 4 * esz + (size_t)Wc * N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz +
-           64 * esz;
+  // FP64 reads its columns and quarter-wave factors from global memory (p2_staged)
+  c.smem = esz == 8 ? (size_t)N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz + 64 * esz
+                    : (size_t)N * 4 * esz + (size_t)Wc * N * 2 * esz + (size_t)S * fft_stride(log2Ly) * 2 * esz +
+                          64 * esz;
   c.grid = Lx / Wc;
   return c;
 }

@@ -66,12 +66,21 @@ __host__ __device__ constexpr size_t p1_smem(int S) {
   return (size_t)F::N * 4 * sizeof(T) + (size_t)S * F::N * sizeof(T) +
          (size_t)S * F::SSTRIDE * 2 * sizeof(T) + (size_t)(F::N + S) * sizeof(T);
 }
+// Pass 2 stages its columns and quarter-wave factors in shared memory except in FP64, whose
+// 16-byte elements would leave one block (three warps) per SM: there it reads both from
+// global memory (L2 and L1) and fits three blocks per SM.
+template <typename T> __host__ __device__ constexpr bool p2_staged() { return !std::is_same<T, double>::value; }
 template <typename T, int LOG2N, typename A = T>
 __host__ __device__ constexpr size_t p2_smem(int Wc) {
   using F = FFTShape<LOG2N>;
-  return (size_t)F::N * 4 * sizeof(A) + (size_t)Wc * F::N * 2 * sizeof(T) +
-         (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(A) + 64 * sizeof(T);
+  return p2_staged<T>()
+             ? (size_t)F::N * 4 * sizeof(A) + (size_t)Wc * F::N * 2 * sizeof(T) +
+                   (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(A) + 64 * sizeof(T)
+             : (size_t)F::N * 2 * sizeof(A) + (size_t)(Wc + Wc / 2) * F::SSTRIDE * 2 * sizeof(A) + 64 * sizeof(T);
 }
+
+// A read-only table entry.
+template <typename C> __device__ __forceinline__ C ld_table(const C* p) { return __ldg(p); }
 
 // Issue the bulk copies of a pass-1 item (thread 0): both tables and the S spectral rows,
 // none of which depend on the previous kernel of the step loop.
@@ -214,9 +223,14 @@ __device__ __forceinline__ void p2_issue_tables(const V2<A>* __restrict__ Wg, co
   C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + Wc * N * sizeof(V2<T>)));
-    bulk_g2s(W, Wg, N * sizeof(C), bar);
-    bulk_g2s(E, Eg, N * sizeof(C), bar);
+    if constexpr (p2_staged<T>()) {
+      mbar_expect_tx(bar, (uint32_t)(2 * N * sizeof(C) + Wc * N * sizeof(V2<T>)));
+      bulk_g2s(W, Wg, N * sizeof(C), bar);
+      bulk_g2s(E, Eg, N * sizeof(C), bar);
+    } else {
+      mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)));
+      bulk_g2s(W, Wg, N * sizeof(C), bar);
+    }
   }
 }
 template <typename T, int LOG2N, typename A = T>
@@ -225,6 +239,7 @@ __device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int
   using C = V2<T>;
   constexpr int N = 1 << LOG2N;
   C* stage = reinterpret_cast<C*>(reinterpret_cast<V2<A>*>(smem) + 2 * N);
+  if constexpr (!p2_staged<T>()) return;  // read in place by p2_finish
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     for (int cc = 0; cc < Wc; ++cc)
@@ -240,18 +255,30 @@ __device__ __forceinline__ void p2_issue_cols(const V2<T>* __restrict__ ABt, int
 // ---------------------------------------------------------------------------
 // T: the type of the (A, B) input, of the field written and of the reductions; A: the
 // arithmetic of the packing, the FFT and the velocity (T, or float-float for FP32 data).
+// ABt and Eg: the columns and the quarter-wave factors in global memory, read there where
+// pass 2 does not stage them (p2_staged).
 template <typename T, int LOG2N, typename A = T>
 __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict__ rho_out, int Lx,
                                           int Wc, int c0, unsigned char* smem, uint64_t* bar,
-                                          uint32_t& ph, FieldRed<T>& res, bool raw = false) {
+                                          uint32_t& ph, FieldRed<T>& res, bool raw,
+                                          const V2<T>* __restrict__ ABt, const V2<A>* __restrict__ Eg) {
   using C = V2<A>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
+  constexpr bool kStaged = p2_staged<T>();
   C* W = reinterpret_cast<C*>(smem);
   C* E = W + N;
-  const V2<T>* stage = reinterpret_cast<const V2<T>*>(E + N);
-  C* buf = reinterpret_cast<C*>(const_cast<V2<T>*>(stage) + Wc * N);
+  const V2<T>* stage = kStaged ? reinterpret_cast<const V2<T>*>(E + N) : ABt + (size_t)c0 * N;
+  C* buf = kStaged ? reinterpret_cast<C*>(reinterpret_cast<V2<T>*>(E + N) + Wc * N) : E;
   T* red = reinterpret_cast<T*>(buf + (Wc + Wc / 2) * F::SSTRIDE);
+  auto ld_in = [&](const V2<T>* p) -> C {
+    if constexpr (kStaged) return to_v2<A, T>(*p);
+    else return to_v2<A, T>(__ldcg(p));  // written by pass 1 (L2)
+  };
+  auto ld_e = [&](int m) -> C {
+    if constexpr (kStaged) return E[m];
+    else return ld_table(Eg + m);
+  };
   const bool ok = mbar_wait_bounded(bar, ph, kMbarTries);
   ph ^= 1u;
   if (!__syncthreads_and(ok)) return false;
@@ -271,16 +298,16 @@ __device__ __forceinline__ bool p2_finish(V2<T>* __restrict__ out, T* __restrict
     C* x1 = x0 + F::SSTRIDE;
     C* x2 = buf + (Wc + p) * F::SSTRIDE;
     if (m == 0) {
-      const C A00 = to_v2<A, T>(s0[0]), A01 = to_v2<A, T>(s1[0]);
+      const C A00 = ld_in(s0), A01 = ld_in(s1);
       x0[F::pidx(0)] = mk2<A>(A00.x, A(0));
       x1[F::pidx(0)] = mk2<A>(A01.x, A(0));
       x2[F::pidx(0)] = mk2<A>(A00.y, A01.y);
       m = N / 2;
     }
-    const C Am0 = to_v2<A, T>(s0[m]), Am1 = to_v2<A, T>(s1[m]);
+    const C Am0 = ld_in(s0 + m), Am1 = ld_in(s1 + m);
     const int q = N - m;
-    const C Aq0 = to_v2<A, T>(s0[q]), Aq1 = to_v2<A, T>(s1[q]);
-    const C em = E[m], eq = E[q];
+    const C Aq0 = ld_in(s0 + q), Aq1 = ld_in(s1 + q);
+    const C em = ld_e(m), eq = ld_e(q);
     const A fm = int_to(m, A(0)), fq = A(N) - fm;
     const A gm = madd(-kh, fm, A(0.5)), hm = madd(-kh, fm, A(-0.5));
     const A gq = madd(-kh, fq, A(0.5)), hq = madd(-kh, fq, A(-0.5));
@@ -361,7 +388,7 @@ __device__ __forceinline__ bool p2_cols(const V2<T>* __restrict__ ABt, V2<T>* __
                                         FieldRed<T>& res) {
   p2_issue_tables<T, LOG2N>(Wg, Eg, Wc, smem, bar);
   p2_issue_cols<T, LOG2N>(ABt, Wc, c0, smem, bar);
-  return p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem, bar, ph, res);
+  return p2_finish<T, LOG2N>(out, rho_out, Lx, Wc, c0, smem, bar, ph, res, false, ABt, Eg);
 }
 
 // Programmatic dependent launch: let the next kernel of the step loop start its
@@ -493,7 +520,7 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
   else if (mode == kModeInit) out = st->parity ? vbuf1 : vbuf0;
   uint32_t ph = 0;
   FieldRed<T> r;
-  if (!p2_finish<T, LOG2N, A>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux)) {
+  if (!p2_finish<T, LOG2N, A>(out, rho_out, Lx, Wc, c0, smem_raw, &bar, ph, r, mode == kModeFlux, ABt, Eg)) {
     if (threadIdx.x == 0) {
       if (step) atomicOr(&st->ls[step_slot(mode)].bad, 1);
       else st->bad = 2;
