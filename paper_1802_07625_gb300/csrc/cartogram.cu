@@ -71,6 +71,9 @@ struct cg_ctx {
   // forward (FP64) roots, quarter-wave factors and blur factors
   void *Wx = nullptr, *Wy = nullptr, *Ex = nullptr, *Ey = nullptr;
   void *Wyff = nullptr, *Eyff = nullptr;  // float-float pass-2 tables (CG_PRECISION_MIXED_FF)
+  // float-float forward roots and quarter-wave factors of both axes (the mixed precisions'
+  // forward transform)
+  void *Wfxff = nullptr, *Efxff = nullptr, *Wfyff = nullptr, *Efyff = nullptr;
   int ff_cols_max = 0;                    // largest block of the float-float pass 2
   double2 *Wfx = nullptr, *Wfy = nullptr, *Efx = nullptr, *Efy = nullptr;
   double *bx = nullptr, *by = nullptr;  // blur factors for width blur_tab_sigma
@@ -305,6 +308,31 @@ int upload_tables_ff(cg_ctx* c, int N, void** Wd, void** Ed) {
   return CG_OK;
 }
 
+// The forward-transform tables of the mixed precisions: the forward roots exp(-2 pi i n1 k2 /
+// N) and the quarter-wave factors exp(i pi m / (2N)), each as the float-float pair nearest the
+// FP64 value.
+int upload_fwd_tables_ff(cg_ctx* c, int N, void** Wd, void** Ed) {
+  const int log2N = ilog2(N);
+  const int N1 = 1 << ((log2N + 1) / 2), N2 = N / N1;
+  std::vector<cg::ff2> W(N), E(N);
+  for (int k2 = 0; k2 < N2; ++k2)
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const double a = 2.0 * cg::kPi * (double)((n1 * k2) % N) / N;
+      W[k2 * N1 + n1].x = cg::ff(std::cos(a));
+      W[k2 * N1 + n1].y = cg::ff(-std::sin(a));
+    }
+  for (int p = 0; p < N; ++p) {
+    const double b = cg::kPi * (double)p / (2.0 * N);
+    E[p].x = cg::ff(std::cos(b));
+    E[p].y = cg::ff(std::sin(b));
+  }
+  CG_CUDA(c, cudaMalloc(Wd, sizeof(cg::ff2) * N));
+  CG_CUDA(c, cudaMalloc(Ed, sizeof(cg::ff2) * N));
+  CG_CUDA(c, cudaMemcpy(*Wd, W.data(), sizeof(cg::ff2) * N, cudaMemcpyHostToDevice));
+  CG_CUDA(c, cudaMemcpy(*Ed, E.data(), sizeof(cg::ff2) * N, cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
 // Separable blur factors exp(-(pi m / L)^2 sigma^2 / 2) of both axes, computed on the
 // device by the same kernel the device-side outer iteration uses.
 int set_blur_tables(cg_ctx* c, double sigma) {
@@ -312,6 +340,18 @@ int set_blur_tables(cg_ctx* c, double sigma) {
   CG_CUDA(c, cudaGetLastError());
   c->blur_tab_sigma = sigma;
   return CG_OK;
+}
+
+// The forward transform of the rasterised density c->acc into the spectrum (FP64, and its FP32
+// copy for the mixed precisions, whose forward transform runs in float-float arithmetic).
+template <typename T>
+void launch_forward(cg_ctx* c, const double* bx, const double* by, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    cg::launch_fwd_ff(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, (float*)c->specT, c->Wfxff, c->Efxff,
+                      c->Wfyff, c->Efyff, bx, by, s);
+  else
+    cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
+                      bx, by, s);
 }
 
 template <typename T>
@@ -324,6 +364,11 @@ int alloc_fields(cg_ctx* c) {
   if (c->ff) {
     if ((r = upload_tables_ff(c, c->Ly, &c->Wyff, &c->Eyff))) return r;
     CG_CUDA(c, cg::prepare_spectral_ff(c->log2Ly, c->Lx, &c->ff_cols_max));
+  }
+  if constexpr (sizeof(T) == 4) {
+    if ((r = upload_fwd_tables_ff(c, c->Lx, &c->Wfxff, &c->Efxff))) return r;
+    if ((r = upload_fwd_tables_ff(c, c->Ly, &c->Wfyff, &c->Efyff))) return r;
+    CG_CUDA(c, cg::prepare_forward_ff(c->log2Lx, c->log2Ly));
   }
   CG_CUDA(c, cudaMalloc((void**)&c->bx, sizeof(double) * c->Lx));
   CG_CUDA(c, cudaMalloc((void**)&c->by, sizeof(double) * c->Ly));
@@ -641,8 +686,7 @@ cudaError_t capture_cartogram(cg_ctx* c, cudaStream_t cs, cudaStream_t bs, cudaS
     if (eb != cudaSuccess) return eb;
     cg::launch_raster(c->xy, c->next, c->vreg, c->w, c->acc, c->Lx, c->Ly, (int)c->n_vert, s);
     cg::launch_blur_tables(c->outer, 0.0, c->bx, c->by, c->Lx, c->Ly, s);
-    cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64, sizeof(T) == 4 ? (T*)c->specT : nullptr,
-                      c->Wfx, c->Efx, c->Wfy, c->Efy, c->bx, c->by, s);
+    launch_forward<T>(c, c->bx, c->by, s);
     if ((eb = capture_integration<T>(c, s, bs2, nullptr)) != cudaSuccess) return eb;
     cg::launch_outer_commit<T>(c->outer, c->info, (const V2<T>*)c->dres, N, s);
     cg::launch_map_points<T>(c->xy, c->xy, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s, &c->outer->status);
@@ -787,9 +831,7 @@ int run_forward(cg_ctx* c) {
     int r = set_blur_tables(c, sigma);
     if (r) return r;
   }
-  cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
-                    sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
-                    blur ? c->bx : nullptr, blur ? c->by : nullptr, c->stream);
+  launch_forward<T>(c, blur ? c->bx : nullptr, blur ? c->by : nullptr, c->stream);
   c->have_spectrum = true;
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;
@@ -1654,9 +1696,7 @@ int do_profile(cg_ctx* c, int reps, double* ms_out) {
           run_raster(c);
           break;
         case 4:
-          cg::launch_fwd<T>(c->log2Lx, c->log2Ly, c->acc, c->R, c->spec64,
-                            sizeof(T) == 4 ? (T*)c->specT : nullptr, c->Wfx, c->Efx, c->Wfy, c->Efy,
-                            c->bx, c->by, s);  // timing only
+          launch_forward<T>(c, c->bx, c->by, s);  // timing only
           break;
         default:
           cg::launch_map_points<T>(c->xy0, c->pts, c->n_vert, (const V2<T>*)c->dres, c->Lx, c->Ly, s);
@@ -2279,7 +2319,7 @@ void cartogram_destroy(cg_ctx* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   free_regions(c);
-  void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wyff, c->Eyff, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
+  void* ps[] = {c->Wx, c->Wy, c->Ex, c->Ey, c->Wyff, c->Eyff, c->Wfxff, c->Efxff, c->Wfyff, c->Efyff, c->Wfx, c->Wfy, c->Efx, c->Efy, c->bx, c->by,
                 c->acc, c->R, c->spec64, c->AB, c->vbuf[0], c->vbuf[1], c->dbuf[0], c->dbuf[1],
                 c->ubuf[0], c->ubuf[1], c->dres, c->rho_tmp, c->st, c->info, c->pts, c->gb, c->acc2, c->phi, c->flux,
                 c->rho0, c->diag, c->deadline};

@@ -138,6 +138,12 @@ inline void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem,
 cudaError_t prepare_spectral_ff(int log2Ly, int Lx, int* cols_max_threads);
 void launch_inv_cols_ff(int log2Ly, int Lx, int Wc, const float2* AB, float2* v0, float2* v1, float* rho_out,
                         const void* W, const void* E, DevState* st, int mode, cudaStream_t s);
+// The forward transform of the mixed precisions in float-float arithmetic (FP64 input and
+// output; tables: float-float forward roots and quarter-wave factors [N] of each axis).
+cudaError_t prepare_forward_ff(int log2Lx, int log2Ly);
+void launch_fwd_ff(int log2Lx, int log2Ly, const double* rho, double* R, double* spec64, float* specT,
+                   const void* Wx, const void* Ex, const void* Wy, const void* Ey, const double* bx,
+                   const double* by, cudaStream_t s);
 
 // Allow the dynamic shared memory the spectral kernels of this grid need.
 template <typename T> cudaError_t prepare_spectral(int log2Lx, int log2Ly);

@@ -551,11 +551,12 @@ __global__ void inv_cols_kernel(const V2<T>* __restrict__ ABt, V2<T>* vbuf0, V2<
 // folded into a per-block table E/2 (exact).
 // shared: W[N] (C, forward roots), buf[(S/2) * STRIDE] (C), Eh[N] (C)
 // ---------------------------------------------------------------------------
-template <int LOG2N>
+// A: the arithmetic (FP64, or float-float for the mixed precisions); input and output FP64.
+template <int LOG2N, typename A = double>
 __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restrict__ R,
-                                const double2* __restrict__ Wg, const double2* __restrict__ Eg,
+                                const V2<A>* __restrict__ Wg, const V2<A>* __restrict__ Eg,
                                 int S) {
-  using C = double2;
+  using C = V2<A>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -567,18 +568,18 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     W[i] = Wg[i];
     const C e = Eg[i];
-    Eh[i] = mk2<double>(0.5 * e.x, 0.5 * e.y);
+    Eh[i] = mk2<A>(A(0.5) * e.x, A(0.5) * e.y);
   }
   for (int task = threadIdx.x; task < S2 * (N / 2); task += blockDim.x) {
     const int s = task / (N / 2), k = task - s * (N / 2);
     const double2 e = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s) * N + 2 * k);
     const double2 o = *reinterpret_cast<const double2*>(rho + (size_t)(r0 + 2 * s + 1) * N + 2 * k);
     C* x = buf + s * F::SSTRIDE;
-    x[F::pidx(k)] = mk2<double>(e.x, o.x);
-    x[F::pidx(N - 1 - k)] = mk2<double>(e.y, o.y);
+    x[F::pidx(k)] = mk2<A>(A(e.x), A(o.x));
+    x[F::pidx(N - 1 - k)] = mk2<A>(A(e.y), A(o.y));
   }
   __syncthreads();
-  block_fft<double, LOG2N, false>(buf, S2, W);
+  block_fft<A, LOG2N, false, !std::is_same<A, double>::value>(buf, S2, W);
   for (int task = threadIdx.x; task < S2 * (N / 2); task += blockDim.x) {
     const int s = task >> (LOG2N - 1), k = task & (N / 2 - 1);
     const C* x = buf + s * F::SSTRIDE;
@@ -587,20 +588,20 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
     if (k == 0) {
       // the self-paired outputs 0 and N/2 (E[0] = 1)
       const C V0 = x[F::out_slot(0)], Vh = x[F::out_slot(N / 2)];
-      const double eh = Eh[N / 2].x;
-      R0[0] = V0.x;
-      R1[0] = V0.y;
-      R0[N / 2] = eh * (Vh.x + Vh.x);
-      R1[N / 2] = eh * (Vh.y + Vh.y);
+      const A eh = Eh[N / 2].x;
+      R0[0] = (double)V0.x;
+      R1[0] = (double)V0.y;
+      R0[N / 2] = (double)(eh * (Vh.x + Vh.x));
+      R1[N / 2] = (double)(eh * (Vh.y + Vh.y));
     } else {
       const int q = N - k;
       const C Vm = x[F::out_slot(k)], Vq = x[F::out_slot(q)];
-      const double u = Vm.x + Vq.x, v = Vm.y - Vq.y, w = Vm.y + Vq.y, z = Vm.x - Vq.x;
+      const A u = Vm.x + Vq.x, v = Vm.y - Vq.y, w = Vm.y + Vq.y, z = Vm.x - Vq.x;
       const C em = Eh[k], eq = Eh[q];
-      R0[k] = em.x * u + em.y * v;
-      R1[k] = em.x * w - em.y * z;
-      R0[q] = eq.x * u - eq.y * v;
-      R1[q] = eq.x * w + eq.y * z;
+      R0[k] = (double)(em.x * u + em.y * v);
+      R1[k] = (double)(em.x * w - em.y * z);
+      R0[q] = (double)(eq.x * u - eq.y * v);
+      R1[q] = (double)(eq.x * w + eq.y * z);
     }
   }
 }
@@ -613,13 +614,14 @@ __global__ void fwd_rows_kernel(const double* __restrict__ rho, double* __restri
 // forms outputs n and N - n; the halves and the row weights (1 + d_n0)^-1 2 by[n] are folded
 // into a per-block table Ew[n] = E[n] (n == 0 ? 1/2 : 1) by[n].
 // shared: W[N] (C), buf[(Wc/2) * SSTRIDE] (C), Ew[N] (C)
+// A: the arithmetic (FP64, or float-float for the mixed precisions); input and output FP64.
 // ---------------------------------------------------------------------------
-template <typename T, int LOG2N>
+template <typename T, int LOG2N, typename A = double>
 __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict__ spec64,
-                                T* __restrict__ specT, const double2* __restrict__ Wg,
-                                const double2* __restrict__ Eg, const double* __restrict__ bx,
+                                T* __restrict__ specT, const V2<A>* __restrict__ Wg,
+                                const V2<A>* __restrict__ Eg, const double* __restrict__ bx,
                                 const double* __restrict__ by, int Lx, int Wc) {
-  using C = double2;
+  using C = V2<A>;
   using F = FFTShape<LOG2N>;
   constexpr int N = F::N;  // = Ly
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -632,20 +634,21 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     W[i] = Wg[i];
     const C e = Eg[i];
-    const double f = (i == 0 ? 0.5 : 1.0) * (by ? by[i] : 1.0);
-    Ew[i] = mk2<double>(e.x * f, e.y * f);
+    const A f = A((i == 0 ? 0.5 : 1.0) * (by ? by[i] : 1.0));
+    Ew[i] = mk2<A>(e.x * f, e.y * f);
   }
   for (int task = threadIdx.x; task < (N / 2) * Wp; task += blockDim.x) {
     const int k = task >> lp, p = task & (Wp - 1);
     const double2 e = *reinterpret_cast<const double2*>(R + (size_t)(2 * k) * Lx + c0 + 2 * p);
     const double2 o = *reinterpret_cast<const double2*>(R + (size_t)(2 * k + 1) * Lx + c0 + 2 * p);
     C* x = buf + p * F::SSTRIDE;
-    x[F::pidx(k)] = e;
-    x[F::pidx(N - 1 - k)] = o;
+    x[F::pidx(k)] = mk2<A>(A(e.x), A(e.y));
+    x[F::pidx(N - 1 - k)] = mk2<A>(A(o.x), A(o.y));
   }
   __syncthreads();
-  block_fft<double, LOG2N, false>(buf, Wp, W);
-  auto put = [&](int n, int m, double s0, double s1) {
+  block_fft<A, LOG2N, false, !std::is_same<A, double>::value>(buf, Wp, W);
+  auto put = [&](int n, int m, A a0, A a1) {
+    const double s0 = (double)a0, s1 = (double)a1;
     const size_t o = (size_t)n * Lx + m;
     spec64[o] = s0;
     spec64[o + 1] = s1;
@@ -659,17 +662,17 @@ __global__ void fwd_cols_kernel(const double* __restrict__ R, double* __restrict
     const C* x = buf + p * F::SSTRIDE;
     const int m = c0 + 2 * p;
     // column weights (1 + d_m0)^-1 2 bx[m]
-    const double wm0 = (m == 0 ? 1.0 : 2.0) * (bx ? bx[m] : 1.0), wm1 = 2.0 * (bx ? bx[m + 1] : 1.0);
+    const A wm0 = A((m == 0 ? 1.0 : 2.0) * (bx ? bx[m] : 1.0)), wm1 = A(2.0 * (bx ? bx[m + 1] : 1.0));
     if (k == 0) {
       // the self-paired outputs 0 and N/2; the (0,0) coefficient is zero
       const C V0 = x[F::out_slot(0)], Vh = x[F::out_slot(N / 2)];
-      const double e0 = Ew[0].x, eh = Ew[N / 2].x;
-      put(0, m, m == 0 ? 0.0 : e0 * (V0.x + V0.x) * wm0, e0 * (V0.y + V0.y) * wm1);
+      const A e0 = Ew[0].x, eh = Ew[N / 2].x;
+      put(0, m, m == 0 ? A(0.0) : e0 * (V0.x + V0.x) * wm0, e0 * (V0.y + V0.y) * wm1);
       put(N / 2, m, eh * (Vh.x + Vh.x) * wm0, eh * (Vh.y + Vh.y) * wm1);
     } else {
       const int q = N - k;
       const C Vn = x[F::out_slot(k)], Vq = x[F::out_slot(q)];
-      const double u = Vn.x + Vq.x, v = Vn.y - Vq.y, w = Vn.y + Vq.y, z = Vn.x - Vq.x;
+      const A u = Vn.x + Vq.x, v = Vn.y - Vq.y, w = Vn.y + Vq.y, z = Vn.x - Vq.x;
       const C en = Ew[k], eq = Ew[q];
       put(k, m, (en.x * u + en.y * v) * wm0, (en.x * w - en.y * z) * wm1);
       put(q, m, (eq.x * u - eq.y * v) * wm0, (eq.x * w + eq.y * z) * wm1);
