@@ -55,9 +55,10 @@ enum {
 
 enum {
     CG_PRECISION_FP64 = 0,   /* every field, transform and position in FP64 */
-    CG_PRECISION_MIXED = 1,  /* transforms, fields and displacements in FP32; rasterisation,
-                                forward transform, polygon areas, the convergence test and
-                                the step-control arithmetic in FP64 */
+    CG_PRECISION_MIXED = 1,  /* inverse transforms, fields and displacements in FP32; the
+                                forward transform in float-float arithmetic (about 48 bits,
+                                FP64 input and spectrum); rasterisation, polygon areas, the
+                                convergence test and the step-control arithmetic in FP64 */
     CG_PRECISION_MIXED_FF = 2 /* as CG_PRECISION_MIXED, with the second inverse transform pass
                                 (the column transforms that form rho, grad rho and v) in
                                 float-float arithmetic (about 48 bits on FP32 hardware): FP32
